@@ -1,0 +1,240 @@
+/*
+ * tg.h — exact typed 3- and 4-node graphlet counting on one NVIDIA GB300
+ * (sm_103a).  C ABI: plain pointers and sizes, no C++ or framework types.
+ *
+ * Method: Rossi et al., "Heterogeneous Network Motifs" (arXiv 1901.10026).
+ * Problem statement: an undirected graph G = (V, E) with a node-type map
+ * phi : V -> {0..L-1} (Def. "Heterogeneous network"); for every edge (i, j)
+ * count the connected induced 3- and 4-node subgraphs containing it, keyed by
+ * graphlet (or edge orbit, Table 2) and by the multiset of node types
+ * (Def. "Typed Graphlet Instance"); global counts are the per-edge sums
+ * divided by the graphlet's edge count (Eq. C = x^T e / |E(H)|).
+ *
+ * Conventions shared by every call:
+ *   - Return value: TG_OK (0) or a negative TG_E* code.  On error no partial
+ *     state is left behind (outputs may have been written partially).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is ordered on it; calls that return results in
+ *     host memory synchronise the stream before returning.
+ *   - Pointers marked "host or device" may point to either; the library tells
+ *     them apart through unified addressing.
+ *   - The library allocates its own device memory (stream-ordered) for graphs
+ *     and scratch; see tg_set_allocator to route that through a caller's
+ *     allocator.
+ *   - A tg_graph is read-only after tg_build_csr; concurrent counting calls on
+ *     one graph from several host threads are safe.
+ *
+ * Per-edge row layout (slot s of row e).  P = L(L+1)/2 unordered type pairs
+ * (t, t'), t <= t', in lexicographic order.  Orbit level (k = 4):
+ *     [g1: L][g2: L][g3: P][g4: P][g5: P] ... [g12: P]     2L + 10P slots
+ * graphlet level (k = 4):
+ *     [h1: L][h2: L][h3: P][h4: P] ... [h8: P]              2L + 6P slots
+ * k = 3 keeps the first 2L slots.  A 3-node slot t holds the subgraphs whose
+ * third node has type t; a 4-node slot (t, t') those whose two other nodes
+ * have types {t, t'}.  Orbits (Table 2): g1 3-path, g2 triangle, g3 4-path
+ * end edge, g4 4-path centre edge, g5 4-star, g6 4-cycle, g7 tailed-triangle
+ * tail edge, g8 tailed-triangle centre (triangle edge opposite the degree-3
+ * node), g9 tailed-triangle tri-edge (triangle edge at the degree-3 node),
+ * g10 chordal-cycle outer edge, g11 chordal-cycle chord, g12 4-clique.
+ * Graphlets (Sec. "From Typed Orbits to Graphlets"): h1 3-path, h2 triangle,
+ * h3 4-path (g3+g4), h4 4-star (g5), h5 4-cycle (g6), h6 tailed triangle
+ * (g7+g8+g9), h7 chordal cycle (g10+g11), h8 4-clique (g12).
+ *
+ * Global layout: [edges: C(L+1,2)][h1: C(L+2,3)][h2: C(L+2,3)] followed, for
+ * k = 4, by [h3..h8: C(L+3,4) each].  Inside a block the entry for the sorted
+ * type multiset c_1 <= ... <= c_m is tg_config_rank(c, m) (colex order).
+ *
+ * Canonical edge order: the simplified graph's edges (u, v), u < v, in
+ * ascending (u, v) order of the ORIGINAL node ids; row e of every per-edge
+ * output belongs to the e-th edge of tg_edge_list.
+ */
+#ifndef TG_H
+#define TG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status ---- */
+#define TG_OK 0
+#define TG_EINVAL (-1)       /* an argument is out of range or inconsistent   */
+#define TG_ENOMEM (-2)       /* a device or host allocation failed            */
+#define TG_ECUDA (-3)        /* a CUDA runtime call failed                    */
+#define TG_EOVERFLOW (-4)    /* a count could exceed its integer width        */
+#define TG_EINTERNAL (-5)    /* a device-side consistency check failed        */
+#define TG_EBUSY (-6)        /* server queue full                              */
+#define TG_ENOMEM_ADMIT (-7) /* request can never fit the server's memory cap */
+#define TG_ETIMEDOUT (-8)    /* a bounded wait ran out                         */
+#define TG_ENOTFOUND (-9)    /* unknown server ticket                          */
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char *tg_strerror(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int tg_version(void);
+
+/* ----------------------------------------------------------- graphs ----- */
+typedef struct tg_graph tg_graph;
+
+/* tg_build_csr flags */
+#define TG_INPUT_DEVICE 1u /* src, dst, type are device pointers (else host) */
+
+/* Limits checked by tg_build_csr. */
+#define TG_MAX_TYPES 16
+#define TG_MAX_NODES (1 << 28)
+
+/*
+ * Build the resident, read-only graph used by every counting call
+ * (Def. "Heterogeneous network", Def. "Typed Neighborhood"): self-loops are
+ * dropped, duplicate and reversed pairs merged, nodes relabelled by degree
+ * (descending, ties by original id), and every adjacency list sorted by
+ * (neighbour type, neighbour id) so that each typed neighbourhood Gamma_v^t
+ * is one contiguous range.
+ *
+ *   n     number of nodes, 1 <= n <= TG_MAX_NODES; ids are 0..n-1
+ *   m     number of input pairs (src[e], dst[e]), m >= 0
+ *   src, dst  int32 node ids, host or device per TG_INPUT_DEVICE
+ *   type  uint8 node types, length n, each < L
+ *   L     number of node types, 1 <= L <= TG_MAX_TYPES
+ *   out   receives the graph; the library owns it until tg_free_graph
+ *
+ * The caller keeps ownership of src, dst and type; they are read during the
+ * call only (the call synchronises `stream` before returning).
+ * Errors: TG_EINVAL (n, m, L out of range; an id outside [0, n); a type >= L;
+ * out == NULL), TG_ENOMEM, TG_ECUDA.
+ */
+int tg_build_csr(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                 const uint8_t *type, int32_t L, uint32_t flags, void *stream,
+                 tg_graph **out);
+
+/* Release a graph and its device memory (NULL is a no-op). */
+int tg_free_graph(tg_graph *g);
+
+typedef struct {
+    int64_t n;             /* nodes                                      */
+    int64_t m_input;       /* input pairs given to tg_build_csr          */
+    int64_t M;             /* undirected edges after simplification      */
+    int64_t n_nonisolated; /* nodes with degree >= 1                     */
+    int64_t max_degree;    /* Delta                                      */
+    int64_t device_bytes;  /* device memory held by the graph            */
+    int32_t L;             /* node types                                 */
+    int32_t reserved;
+} tg_info;
+
+int tg_graph_info(const tg_graph *g, tg_info *info);
+
+/*
+ * Canonical edge list: u[e] < v[e], original ids, ascending (u, v).  u and v
+ * hold M entries each, host or device.  Synchronises `stream`.
+ */
+int tg_edge_list(const tg_graph *g, int32_t *u, int32_t *v, void *stream);
+
+/* ----------------------------------------------------------- layout ----- */
+#define TG_GRAPHLET 0
+#define TG_ORBIT 1
+
+/* Slots per per-edge row: 2L (k = 3) or 2L + {6|10}*L(L+1)/2 (k = 4). */
+int64_t tg_slots(int32_t L, int32_t k, int32_t level);
+
+/* Entries of the global histogram for (L, k); see the global layout above. */
+int64_t tg_global_len(int32_t L, int32_t k);
+
+/* Number of typed configurations of one k-node graphlet: C(L+k-1, k)
+ * (Eq. "number of typed motifs", Table 1). */
+int64_t tg_config_count(int32_t L, int32_t k);
+
+/* Colex rank of a sorted type multiset: sum_m C(c_m + m - 1, m), m = 1..k.
+ * `types` need not be sorted (it is sorted internally); returns -1 when k is
+ * not in 1..4 or a type is negative. */
+int64_t tg_config_rank(const int32_t *types, int32_t k);
+
+/* Inverse of tg_config_rank for k in 1..4: writes the sorted multiset. */
+int tg_config_unrank(int64_t rank, int32_t k, int32_t *types);
+
+/*
+ * Typed motif hash of Sec. "Typed Motif Hash Functions":
+ *   F = g*10^4 + t1*10^3 + t2*10^2 + t3*10 + t4      (L < 10)
+ *   F = g*10^8 + t1*10^6 + t2*10^4 + t3*10^2 + t4    (L >= 10)
+ * with the k node types shifted to 1..L, sorted ascending (every ordering of
+ * the types maps to the same value), and padded with 0 for k < 4.  g is the
+ * caller's motif or orbit number.  Returns 0 on invalid input.
+ */
+uint64_t tg_paper_hash(int32_t g, const int32_t *types, int32_t k, int32_t L);
+
+/* Per-edge slot -> (orbit or graphlet id, sorted config of all k nodes).
+ * phi_i, phi_j are the edge's endpoint types; writes `k_out` (3 or 4) types. */
+int tg_slot_config(int32_t L, int32_t k, int32_t level, int32_t phi_i, int32_t phi_j,
+                   int64_t slot, int32_t *motif, int32_t *types, int32_t *k_out);
+
+/* ----------------------------------------------------------- counting --- */
+/*
+ * Global typed graphlet counts (Sec. "Global Typed Graphlet Counts").
+ *   k    3 or 4 (k = 4 also fills the 2- and 3-node blocks)
+ *   out  tg_global_len(L, k) uint64 entries, host or device
+ * Runs Alg. 1-3 and the closed forms per edge on the GPU, reduces into a
+ * per-configuration histogram and divides by |E(H)|.  Errors: TG_EINVAL,
+ * TG_EOVERFLOW (the graph is too large for the 32-bit per-edge counters:
+ * 2M >= 2^31), TG_EINTERNAL (a sum not divisible by |E(H)|), TG_ENOMEM,
+ * TG_ECUDA.
+ */
+int tg_count_global(const tg_graph *g, int32_t k, uint64_t *out, void *stream);
+
+/*
+ * Per-edge typed counts (Def. "Local Typed Graphlet Counting").
+ *   level  TG_GRAPHLET or TG_ORBIT
+ *   rows   M x tg_slots(L, k, level) uint64, row-major, canonical edge order,
+ *          host or device
+ */
+int tg_count_per_edge(const tg_graph *g, int32_t k, int32_t level, uint64_t *rows,
+                      void *stream);
+
+/*
+ * Undivided per-configuration sums over the canonical edge range [e0, e1):
+ * sum over those edges of the per-edge graphlet counts, in the global layout.
+ * Summing the outputs of disjoint ranges that cover [0, M) and passing the
+ * total to tg_global_finalize gives tg_count_global's result; this is the
+ * unit of work one rank does when the edges are sharded across GPUs.
+ *   sums  tg_global_len(L, k) uint64, host or device
+ */
+int tg_count_range(const tg_graph *g, int32_t k, int64_t e0, int64_t e1, uint64_t *sums,
+                   void *stream);
+
+/*
+ * Divide undivided sums by |E(H)| (1 for edges, 2 for h1, 3 for h2, then
+ * 3, 3, 4, 4, 5, 6 for h3..h8) on the host.  Returns TG_EINTERNAL if a sum is
+ * not divisible.  `sums` and `out` are host arrays of tg_global_len(L, k)
+ * entries (they may alias).
+ */
+int tg_global_finalize(int32_t L, int32_t k, const uint64_t *sums, uint64_t *out);
+
+/*
+ * Paper work model of the count (Thm. "time complexity for all 3 and 4-node
+ * typed graphlet orbits"): for every edge (i, j), 2 d_i + d_j adjacency
+ * entries for Alg. 1 (d_i <= d_j) plus sum over w in S_i u S_j u T_ij of d_w
+ * for Alg. 2-3.  Writes the total entry count; computed on the GPU.
+ */
+int tg_work_model(const tg_graph *g, uint64_t *entries, void *stream);
+
+/* ------------------------------------------------------- allocation ----- */
+/*
+ * Route the library's device allocations through caller functions (for
+ * example a framework's caching allocator).  alloc returns NULL on failure.
+ * Pass NULLs to restore the default (cudaMallocAsync / cudaFreeAsync).
+ * Not thread-safe with respect to calls in flight; set it once at start-up.
+ */
+typedef void *(*tg_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*tg_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int tg_set_allocator(tg_alloc_fn alloc, tg_free_fn free_fn, void *ctx);
+
+/* Failure injection for tests: make the n-th device allocation from now on
+ * fail (n >= 1), or disable with n = 0.  Host-side only: the allocation is
+ * refused before any CUDA call is made. */
+int tg_debug_fail_alloc(int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TG_H */

@@ -1,0 +1,288 @@
+"""Python binding of the typed-graphlet C ABI (include/tg.h).
+
+Argument marshalling only: every step of the counting path runs in the CUDA
+library ``libtg.so`` built in-tree by ``build.build()``.  Importing this
+module never computes anything on the host; if the library is missing the
+first call raises instead of falling back to anything else.
+
+Arrays: numpy arrays are host memory; torch CUDA tensors (or anything with a
+``data_ptr()`` on the device) are device memory.  ``stream`` is a
+``torch.cuda.Stream`` or a raw ``cudaStream_t`` integer (None: torch's current
+stream when torch is loaded, else the legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import sys
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "TGError", "Graph", "lib", "tg_build_csr", "tg_free_graph", "tg_graph_info", "tg_edge_list",
+    "tg_count_global", "tg_count_per_edge", "tg_count_range", "tg_global_finalize",
+    "tg_work_model", "tg_slots", "tg_global_len", "tg_config_count", "tg_config_rank",
+    "tg_config_unrank", "tg_paper_hash", "tg_slot_config", "tg_strerror", "tg_version",
+    "tg_debug_fail_alloc", "TG_GRAPHLET", "TG_ORBIT",
+]
+
+TG_OK = 0
+TG_EINVAL = -1
+TG_ENOMEM = -2
+TG_ECUDA = -3
+TG_EOVERFLOW = -4
+TG_EINTERNAL = -5
+TG_EBUSY = -6
+TG_ENOMEM_ADMIT = -7
+TG_ETIMEDOUT = -8
+TG_ENOTFOUND = -9
+TG_INPUT_DEVICE = 1
+TG_GRAPHLET = 0
+TG_ORBIT = 1
+
+_lib = None
+
+
+class TGError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {tg_strerror(status)} ({status})" if what else tg_strerror(status))
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m_input", ctypes.c_int64), ("M", ctypes.c_int64),
+                ("n_nonisolated", ctypes.c_int64), ("max_degree", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("L", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def lib():
+    """The loaded libtg.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise ImportError(f"libtg.so not built ({_build.LIB}); run __graft_entry__.build()")
+        L = ctypes.CDLL(_build.LIB)
+        vp, i64, i32, u32, u64 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32,
+                                  ctypes.c_uint64)
+        sig = {
+            "tg_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+            "tg_version": (ctypes.c_int, []),
+            "tg_build_csr": (ctypes.c_int, [i64, i64, vp, vp, vp, i32, u32, vp, ctypes.POINTER(vp)]),
+            "tg_free_graph": (ctypes.c_int, [vp]),
+            "tg_graph_info": (ctypes.c_int, [vp, ctypes.POINTER(_Info)]),
+            "tg_edge_list": (ctypes.c_int, [vp, vp, vp, vp]),
+            "tg_slots": (i64, [i32, i32, i32]),
+            "tg_global_len": (i64, [i32, i32]),
+            "tg_config_count": (i64, [i32, i32]),
+            "tg_config_rank": (i64, [vp, i32]),
+            "tg_config_unrank": (ctypes.c_int, [i64, i32, vp]),
+            "tg_paper_hash": (u64, [i32, vp, i32, i32]),
+            "tg_slot_config": (ctypes.c_int, [i32, i32, i32, i32, i32, i64, vp, vp, vp]),
+            "tg_count_global": (ctypes.c_int, [vp, i32, vp, vp]),
+            "tg_count_per_edge": (ctypes.c_int, [vp, i32, i32, vp, vp]),
+            "tg_count_range": (ctypes.c_int, [vp, i32, i64, i64, vp, vp]),
+            "tg_global_finalize": (ctypes.c_int, [i32, i32, vp, vp]),
+            "tg_work_model": (ctypes.c_int, [vp, vp, vp]),
+            "tg_set_allocator": (ctypes.c_int, [vp, vp, vp]),
+            "tg_debug_fail_alloc": (ctypes.c_int, [i64]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------- marshalling --
+def _is_device(x) -> bool:
+    dev = getattr(x, "is_cuda", None)
+    return bool(dev)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_contiguous") and not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    raise TypeError(f"unsupported buffer type {type(x)!r}")
+
+
+def _stream(stream):
+    if stream is None:
+        torch = sys.modules.get("torch")
+        if torch is not None and torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check(rc: int, what: str):
+    if rc != TG_OK:
+        raise TGError(rc, what)
+
+
+def tg_strerror(status: int) -> str:
+    return lib().tg_strerror(status).decode()
+
+
+def tg_version() -> int:
+    return lib().tg_version()
+
+
+# --------------------------------------------------------------- graphs -----
+class Graph:
+    """Owner of a ``tg_graph*``; freed with the object (or ``close()``)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+        info = _Info()
+        _check(lib().tg_graph_info(self._h, ctypes.byref(info)), "tg_graph_info")
+        self.n, self.m_input, self.M = info.n, info.m_input, info.M
+        self.n_nonisolated, self.max_degree = info.n_nonisolated, info.max_degree
+        self.device_bytes, self.L = info.device_bytes, info.L
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("graph is closed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().tg_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        return dict(n=self.n, m_input=self.m_input, M=self.M, n_nonisolated=self.n_nonisolated,
+                    max_degree=self.max_degree, device_bytes=self.device_bytes, L=self.L)
+
+
+def tg_build_csr(n: int, src, dst, types, L: int, stream=None) -> Graph:
+    """Build the resident typed CSR (host numpy or device tensors)."""
+    dev = _is_device(src)
+    if dev != _is_device(dst) or dev != _is_device(types):
+        raise ValueError("src, dst and types must all be host arrays or all device tensors")
+    if not dev:
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        types = np.ascontiguousarray(types, dtype=np.uint8)
+    m = int(src.shape[0])
+    if int(dst.shape[0]) != m or int(types.shape[0]) != int(n):
+        raise ValueError("length mismatch")
+    h = ctypes.c_void_p()
+    rc = lib().tg_build_csr(int(n), m, _ptr(src), _ptr(dst), _ptr(types), int(L),
+                            TG_INPUT_DEVICE if dev else 0, _stream(stream), ctypes.byref(h))
+    _check(rc, "tg_build_csr")
+    return Graph(h)
+
+
+def tg_free_graph(g: Graph) -> None:
+    g.close()
+
+
+def tg_graph_info(g: Graph) -> dict:
+    return g.info()
+
+
+def tg_edge_list(g: Graph, stream=None):
+    u = np.empty(g.M, np.int32)
+    v = np.empty(g.M, np.int32)
+    _check(lib().tg_edge_list(g.handle, _ptr(u), _ptr(v), _stream(stream)), "tg_edge_list")
+    return u, v
+
+
+# --------------------------------------------------------------- layout -----
+def tg_slots(L: int, k: int = 4, level: int = TG_GRAPHLET) -> int:
+    return int(lib().tg_slots(L, k, level))
+
+
+def tg_global_len(L: int, k: int = 4) -> int:
+    return int(lib().tg_global_len(L, k))
+
+
+def tg_config_count(L: int, k: int) -> int:
+    return int(lib().tg_config_count(L, k))
+
+
+def tg_config_rank(types) -> int:
+    a = np.ascontiguousarray(types, dtype=np.int32)
+    return int(lib().tg_config_rank(_ptr(a), a.shape[0]))
+
+
+def tg_config_unrank(rank: int, k: int):
+    a = np.zeros(k, np.int32)
+    _check(lib().tg_config_unrank(int(rank), k, _ptr(a)), "tg_config_unrank")
+    return tuple(int(x) for x in a)
+
+
+def tg_paper_hash(g: int, types, L: int) -> int:
+    a = np.ascontiguousarray(types, dtype=np.int32)
+    return int(lib().tg_paper_hash(g, _ptr(a), a.shape[0], L))
+
+
+def tg_slot_config(L: int, k: int, level: int, phi_i: int, phi_j: int, slot: int):
+    motif = ctypes.c_int32()
+    kk = ctypes.c_int32()
+    t = np.zeros(4, np.int32)
+    _check(lib().tg_slot_config(L, k, level, phi_i, phi_j, slot, ctypes.byref(motif), _ptr(t),
+                                ctypes.byref(kk)), "tg_slot_config")
+    return int(motif.value), tuple(int(x) for x in t[: kk.value])
+
+
+# -------------------------------------------------------------- counting ----
+def tg_count_global(g: Graph, k: int = 4, out=None, stream=None):
+    """Global typed counts; ``out`` (host array or device tensor) or a new numpy array."""
+    if out is None:
+        out = np.zeros(tg_global_len(g.L, k), np.uint64)
+    _check(lib().tg_count_global(g.handle, k, _ptr(out), _stream(stream)), "tg_count_global")
+    return out
+
+
+def tg_count_per_edge(g: Graph, k: int = 4, level: int = TG_GRAPHLET, rows=None, stream=None):
+    if rows is None:
+        rows = np.zeros((g.M, tg_slots(g.L, k, level)), np.uint64)
+    _check(lib().tg_count_per_edge(g.handle, k, level, _ptr(rows), _stream(stream)),
+           "tg_count_per_edge")
+    return rows
+
+
+def tg_count_range(g: Graph, k: int, e0: int, e1: int, sums=None, stream=None):
+    if sums is None:
+        sums = np.zeros(tg_global_len(g.L, k), np.uint64)
+    _check(lib().tg_count_range(g.handle, k, int(e0), int(e1), _ptr(sums), _stream(stream)),
+           "tg_count_range")
+    return sums
+
+
+def tg_global_finalize(L: int, k: int, sums) -> np.ndarray:
+    s = np.ascontiguousarray(sums, dtype=np.uint64)
+    out = np.zeros_like(s)
+    _check(lib().tg_global_finalize(L, k, _ptr(s), _ptr(out)), "tg_global_finalize")
+    return out
+
+
+def tg_work_model(g: Graph, stream=None) -> int:
+    v = np.zeros(1, np.uint64)
+    _check(lib().tg_work_model(g.handle, _ptr(v), _stream(stream)), "tg_work_model")
+    return int(v[0])
+
+
+def tg_debug_fail_alloc(n: int) -> None:
+    _check(lib().tg_debug_fail_alloc(int(n)), "tg_debug_fail_alloc")

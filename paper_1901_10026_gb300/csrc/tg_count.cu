@@ -1,0 +1,712 @@
+// Per-edge typed graphlet counting (Alg. 1-3, the closed forms of Sec.
+// "Combinatorial Relationships", Sec. "From Typed Orbits to Graphlets") and
+// the global reduction of Sec. "Global Typed Graphlet Counts".
+//
+// One warp owns one edge (i, j) at a time; i is the endpoint with the larger
+// new id, so d_i <= d_j.
+//   Phase A/B (Alg. 1): classify Gamma_i \ {j} into T_ij / S_i and
+//     Gamma_j \ {i} into T_ij / S_j, counting |T^t|, |S_i^t|, |S_j^t|.
+//   Phase C (Alg. 2 and 3): for every w_k in S_i u S_j u T_ij and every w_r
+//     in Gamma_{w_k}, classify w_r and update the enumerated orbits.  The
+//     unmarked case (w_r in I, orbits g3 and g8) is not touched per w_r:
+//     each w_k adds its typed degree vector d_{w_k}^{t'} (minus the entries
+//     for i and j) once, and every marked w_r subtracts one.  This is the
+//     same count as the per-w_r increments of Alg. 2-3.
+//   Phase D: closed forms per type pair t <= t', then either the per-edge
+//     row or warp-aggregated updates of a per-CTA histogram indexed by the
+//     colex rank of the sorted type multiset.
+// Membership of a neighbour w in Gamma_i or Gamma_j is a binary search inside
+// the typed range Gamma_i^{phi(w)} (lists are sorted by (type, id)).
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "tg_internal.cuh"
+
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kBlock = kWarps * 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// enumerated-orbit counter rows (per warp)
+enum { C_G3 = 0, C_G6 = 1, C_G7 = 2, C_G8 = 3, C_G10 = 4, C_G12 = 5, C_NUM = 6 };
+// classes of a node relative to the edge (bit 0: in Gamma_i, bit 1: in Gamma_j)
+enum { CLS_I = 0, CLS_SI = 1, CLS_SJ = 2, CLS_T = 3 };
+
+struct CountParams {
+    const int64_t *rowptr;
+    const uint32_t *adj;
+    const int32_t *toff;
+    const uint8_t *ntype;
+    const int2 *edges;
+    const int64_t *order;  // processing order (edge ids); NULL -> e0 + item
+    int64_t e0;
+    int64_t count;
+    int32_t L, P, k, level;
+    unsigned long long *queue;
+    uint64_t *rows;  // per-edge output, row (e - e0)
+    int64_t width;
+    unsigned long long *hist;  // undivided global sums
+    int64_t hist_len;
+    int32_t hist_smem;
+    int64_t off1, off2, off4, n4;
+};
+
+__device__ __forceinline__ int pair_index(int L, int a, int b) {
+    if (a > b) {
+        int t = a;
+        a = b;
+        b = t;
+    }
+    return a * L - (a * (a - 1)) / 2 + (b - a);
+}
+
+__device__ __forceinline__ void unpair(int L, int p, int &t, int &u) {
+    t = 0;
+    while (p >= L - t) {
+        p -= L - t;
+        ++t;
+    }
+    u = t + p;
+}
+
+__device__ __forceinline__ uint64_t c2(uint64_t x) { return x < 2 ? 0 : x * (x - 1) / 2; }
+
+__device__ __forceinline__ int64_t colex3(int a, int b, int c) {
+    // a <= b <= c
+    return (int64_t)a + (int64_t)(b + 1) * b / 2 + (int64_t)(c + 2) * (c + 1) * c / 6;
+}
+__device__ __forceinline__ int64_t colex4(int a, int b, int c, int d) {
+    return colex3(a, b, c) + (int64_t)(d + 3) * (d + 2) * (d + 1) * d / 24;
+}
+__device__ __forceinline__ void sort2(int &a, int &b) {
+    if (a > b) {
+        int t = a;
+        a = b;
+        b = t;
+    }
+}
+
+// Is the packed entry w in the list at adj + base?  `to` holds the list's type
+// offsets, so only the typed range Gamma^{type(w)} is searched.
+__device__ __forceinline__ bool contains(const uint32_t *__restrict__ adj, int64_t base,
+                                         const int32_t *__restrict__ to, uint32_t w) {
+    int t = (int)(w >> TG_TSHIFT);
+    int lo = __ldg(to + t), hi = __ldg(to + t + 1);
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        uint32_t x = __ldg(adj + base + mid);
+        if (x < w)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo < __ldg(to + t + 1) && __ldg(adj + base + lo) == w;
+}
+
+__device__ __forceinline__ void hist_add(const CountParams &p, unsigned long long *shist,
+                                         int64_t x, unsigned long long v) {
+    if (!v) return;
+    if (p.hist_smem)
+        atomicAdd(shist + x, v);
+    else
+        atomicAdd(p.hist + x, v);
+}
+
+__global__ void __launch_bounds__(kBlock) k_count_warp(CountParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int L = p.L, P = p.P;
+    size_t hist_bytes = p.hist_smem ? (((size_t)p.hist_len * 8 + 15) & ~(size_t)15) : 0;
+    size_t wbytes = ((size_t)C_NUM * P * 4 + 3 * 16 * 4 + 32 * 4 + 15) & ~(size_t)15;
+    unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);
+    unsigned char *wb = smem + hist_bytes + warp * wbytes;
+    int *cnt = reinterpret_cast<int *>(wb);
+    unsigned *Tn = reinterpret_cast<unsigned *>(wb + (size_t)C_NUM * P * 4);
+    unsigned *Si = Tn + 16;
+    unsigned *Sj = Si + 16;
+    int *pos2owner = reinterpret_cast<int *>(Sj + 16);
+
+    if (p.hist_smem) {
+        for (int64_t x = threadIdx.x; x < p.hist_len; x += blockDim.x) shist[x] = 0;
+        __syncthreads();
+    }
+    const int64_t *__restrict__ rowptr = p.rowptr;
+    const uint32_t *__restrict__ adj = p.adj;
+    const int32_t *__restrict__ toff = p.toff;
+
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(p.queue, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= (unsigned long long)p.count) break;
+        const int64_t e = p.order ? p.order[item] : p.e0 + (int64_t)item;
+
+        const int2 ab = p.edges[e];
+        const int j = ab.x < ab.y ? ab.x : ab.y;  // larger degree
+        const int i = ab.x < ab.y ? ab.y : ab.x;
+        const int ti = p.ntype[i], tj = p.ntype[j];
+        const int64_t bi = rowptr[i], bj = rowptr[j];
+        const int di = (int)(rowptr[i + 1] - bi), dj = (int)(rowptr[j + 1] - bj);
+        const int32_t *toi = toff + (int64_t)i * (L + 1);
+        const int32_t *toj = toff + (int64_t)j * (L + 1);
+
+        for (int x = lane; x < C_NUM * P; x += 32) cnt[x] = 0;
+        if (lane < 16) {
+            Tn[lane] = 0;
+            Si[lane] = 0;
+            Sj[lane] = 0;
+        }
+        __syncwarp();
+
+        // ---- Alg. 1: T_ij and S_i from Gamma_i, S_j from Gamma_j ----------
+        for (int x = lane; x < di; x += 32) {
+            uint32_t w = __ldg(adj + bi + x);
+            if ((int)(w & TG_IDMASK) == j) continue;
+            bool inJ = contains(adj, bj, toj, w);
+            atomicAdd(inJ ? &Tn[w >> TG_TSHIFT] : &Si[w >> TG_TSHIFT], 1u);
+        }
+        for (int x = lane; x < dj; x += 32) {
+            uint32_t w = __ldg(adj + bj + x);
+            if ((int)(w & TG_IDMASK) == i) continue;
+            if (!contains(adj, bi, toi, w)) atomicAdd(&Sj[w >> TG_TSHIFT], 1u);
+        }
+        __syncwarp();
+
+        // ---- Alg. 2 and 3 ------------------------------------------------
+        if (p.k == 4) {
+            for (int side = 0; side < 2; ++side) {
+                const int64_t sb = side == 0 ? bi : bj;
+                const int sd = side == 0 ? di : dj;
+                for (int c0 = 0; c0 < sd; c0 += 32) {
+                    const int x = c0 + lane;
+                    bool act = x < sd;
+                    uint32_t wk = act ? __ldg(adj + sb + x) : 0u;
+                    const int kid = (int)(wk & TG_IDMASK), kt = (int)(wk >> TG_TSHIFT);
+                    int cls = CLS_I;
+                    if (act) {
+                        if (side == 0) {
+                            if (kid == j)
+                                act = false;
+                            else
+                                cls = contains(adj, bj, toj, wk) ? CLS_T : CLS_SI;
+                        } else {
+                            if (kid == i || contains(adj, bi, toi, wk))
+                                act = false;  // T members are enumerated from Gamma_i
+                            else
+                                cls = CLS_SJ;
+                        }
+                    }
+                    int64_t kb = 0;
+                    int dk = 0;
+                    if (act) {
+                        kb = rowptr[kid];
+                        dk = (int)(rowptr[kid + 1] - kb);
+                        const int32_t *tk = toff + (int64_t)kid * (L + 1);
+                        const int gI = cls == CLS_T ? C_G8 : C_G3;
+                        for (int t2 = 0; t2 < L; ++t2) {
+                            int c = __ldg(tk + t2 + 1) - __ldg(tk + t2);
+                            if ((cls & 1) && t2 == ti) --c;  // w_r = i
+                            if ((cls & 2) && t2 == tj) --c;  // w_r = j
+                            if (c) atomicAdd(&cnt[gI * P + pair_index(L, kt, t2)], c);
+                        }
+                    }
+                    // flattened walk over the (up to 32) lists Gamma_{w_k}
+                    int incl = dk;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        int y = __shfl_up_sync(kFull, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const int excl = incl - dk;
+                    const int total = __shfl_sync(kFull, incl, 31);
+                    int carry = 0;
+                    for (int base = 0; base < total; base += 32) {
+                        const int srel = excl - base;
+                        const bool starts = dk > 0 && srel >= 0 && srel < 32;
+                        const unsigned smask = __reduce_or_sync(kFull, starts ? (1u << srel) : 0u);
+                        if (starts) pos2owner[srel] = lane;
+                        __syncwarp();
+                        const unsigned below =
+                            smask & (lane == 31 ? kFull : ((2u << lane) - 1u));
+                        const int owner = below ? pos2owner[31 - __clz(below)] : carry;
+                        carry = __shfl_sync(kFull, owner, 31);
+                        __syncwarp();
+                        const int64_t ob = __shfl_sync(kFull, kb, owner);
+                        const int oex = __shfl_sync(kFull, excl, owner);
+                        const int ocls = __shfl_sync(kFull, cls, owner);
+                        const int okt = __shfl_sync(kFull, kt, owner);
+                        const int okid = __shfl_sync(kFull, kid, owner);
+                        const int pos = base + lane;
+                        if (pos < total) {
+                            const uint32_t wr = __ldg(adj + ob + (pos - oex));
+                            const int rid = (int)(wr & TG_IDMASK);
+                            if (rid != i && rid != j) {
+                                const int rcls = (contains(adj, bi, toi, wr) ? 1 : 0) |
+                                                 (contains(adj, bj, toj, wr) ? 2 : 0);
+                                if (rcls != CLS_I) {
+                                    const int pr = pair_index(L, okt, (int)(wr >> TG_TSHIFT));
+                                    atomicAdd(&cnt[(ocls == CLS_T ? C_G8 : C_G3) * P + pr], -1);
+                                    if (ocls == CLS_SI) {
+                                        if (rcls == CLS_SI && rid < okid)
+                                            atomicAdd(&cnt[C_G7 * P + pr], 1);
+                                    } else if (ocls == CLS_SJ) {
+                                        if (rcls == CLS_SJ && rid < okid)
+                                            atomicAdd(&cnt[C_G7 * P + pr], 1);
+                                        else if (rcls == CLS_SI)
+                                            atomicAdd(&cnt[C_G6 * P + pr], 1);
+                                    } else {
+                                        if (rcls == CLS_T) {
+                                            if (rid < okid) atomicAdd(&cnt[C_G12 * P + pr], 1);
+                                        } else {
+                                            atomicAdd(&cnt[C_G10 * P + pr], 1);
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+
+        // ---- closed forms and output --------------------------------------
+        if (p.rows) {
+            uint64_t *row = p.rows + (e - p.e0) * p.width;
+            for (int t = lane; t < L; t += 32) {
+                row[t] = (uint64_t)Si[t] + Sj[t];
+                row[L + t] = Tn[t];
+            }
+        } else {
+            if (lane == 0) {
+                int a = ti, b = tj;
+                sort2(a, b);
+                hist_add(p, shist, (int64_t)a + (int64_t)(b + 1) * b / 2, 1ull);
+            }
+            for (int t = lane; t < L; t += 32) {
+                int a = ti, b = tj, c = t;
+                sort2(a, b);
+                sort2(b, c);
+                sort2(a, b);
+                const int64_t r = colex3(a, b, c);
+                hist_add(p, shist, p.off1 + r, (unsigned long long)Si[t] + Sj[t]);
+                hist_add(p, shist, p.off2 + r, (unsigned long long)Tn[t]);
+            }
+        }
+        if (p.k == 4) {
+            for (int pr = lane; pr < P; pr += 32) {
+                int t, u;
+                unpair(L, pr, t, u);
+                const uint64_t sit = Si[t], siu = Si[u], sjt = Sj[t], sju = Sj[u];
+                const uint64_t tt = Tn[t], tu = Tn[u];
+                const uint64_t g3 = (uint64_t)(int64_t)cnt[C_G3 * P + pr];
+                const uint64_t g6 = (uint64_t)(int64_t)cnt[C_G6 * P + pr];
+                const uint64_t g7 = (uint64_t)(int64_t)cnt[C_G7 * P + pr];
+                const uint64_t g8 = (uint64_t)(int64_t)cnt[C_G8 * P + pr];
+                const uint64_t g10 = (uint64_t)(int64_t)cnt[C_G10 * P + pr];
+                const uint64_t g12 = (uint64_t)(int64_t)cnt[C_G12 * P + pr];
+                uint64_t g4, g5, g9, g11;
+                if (t == u) {
+                    g4 = sit * sjt - g6;
+                    g5 = c2(sit) + c2(sjt) - g7;
+                    g9 = tt * (sit + sjt) - g10;
+                    g11 = c2(tt) - g12;
+                } else {
+                    g4 = sit * sju + siu * sjt - g6;
+                    g5 = sit * siu + sjt * sju - g7;
+                    g9 = tt * (siu + sju) + tu * (sit + sjt) - g10;
+                    g11 = tt * tu - g12;
+                }
+                if (p.rows) {
+                    uint64_t *row = p.rows + (e - p.e0) * p.width + 2 * L;
+                    if (p.level == TG_ORBIT) {
+                        row[0 * P + pr] = g3;
+                        row[1 * P + pr] = g4;
+                        row[2 * P + pr] = g5;
+                        row[3 * P + pr] = g6;
+                        row[4 * P + pr] = g7;
+                        row[5 * P + pr] = g8;
+                        row[6 * P + pr] = g9;
+                        row[7 * P + pr] = g10;
+                        row[8 * P + pr] = g11;
+                        row[9 * P + pr] = g12;
+                    } else {
+                        row[0 * P + pr] = g3 + g4;
+                        row[1 * P + pr] = g5;
+                        row[2 * P + pr] = g6;
+                        row[3 * P + pr] = g7 + g8 + g9;
+                        row[4 * P + pr] = g10 + g11;
+                        row[5 * P + pr] = g12;
+                    }
+                } else {
+                    const uint64_t h[6] = {g3 + g4, g5, g6, g7 + g8 + g9, g10 + g11, g12};
+                    if (h[0] | h[1] | h[2] | h[3] | h[4] | h[5]) {
+                        int a = ti, b = tj, c = t, d = u;
+                        sort2(a, b);
+                        sort2(c, d);
+                        sort2(a, c);
+                        sort2(b, d);
+                        sort2(b, c);
+                        const int64_t r = colex4(a, b, c, d);
+#pragma unroll
+                        for (int q = 0; q < 6; ++q)
+                            hist_add(p, shist, p.off4 + q * p.n4 + r, h[q]);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+
+    if (p.hist_smem) {
+        __syncthreads();
+        for (int64_t x = threadIdx.x; x < p.hist_len; x += blockDim.x)
+            if (shist[x]) atomicAdd(p.hist + x, shist[x]);
+    }
+}
+
+// |E(H)| per global entry: divide and check.
+__global__ void k_finalize(const unsigned long long *sums, uint64_t *out, int64_t len,
+                           int64_t off1, int64_t off2, int64_t off4, int64_t n4,
+                           unsigned *err) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < len;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t d = 1;
+        if (x >= off4) {
+            const uint64_t eh[6] = {3, 3, 4, 4, 5, 6};
+            d = eh[(x - off4) / n4];
+        } else if (x >= off2) {
+            d = 3;
+        } else if (x >= off1) {
+            d = 2;
+        }
+        uint64_t v = sums[x];
+        if (v % d) atomicOr(err, TG_DERR_DIVISIBLE);
+        out[x] = v / d;
+    }
+}
+
+// s_v = sum of neighbour degrees (for the work model and the schedule).
+__global__ void k_neighbor_degree_sum(const int64_t *rowptr, const uint32_t *adj, int64_t n,
+                                      unsigned long long *s) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = wid; v < n; v += nw) {
+        unsigned long long acc = 0;
+        for (int64_t x = rowptr[v] + lane; x < rowptr[v + 1]; x += 32) {
+            uint32_t w = adj[x] & TG_IDMASK;
+            acc += (unsigned long long)(rowptr[w + 1] - rowptr[w]);
+        }
+        for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+        if (lane == 0) s[v] = acc;
+    }
+}
+
+// Paper work model per edge: 2 d_i + d_j + sum_{w in S_i u S_j u T} d_w.
+__global__ void k_work_model(const int64_t *rowptr, const uint32_t *adj, const int32_t *toff,
+                             const int2 *edges, int64_t M, int32_t L,
+                             const unsigned long long *s, unsigned long long *total,
+                             unsigned long long *edge_cost) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long acc_total = 0;
+    for (int64_t e = wid; e < M; e += nw) {
+        const int2 ab = edges[e];
+        const int j = ab.x < ab.y ? ab.x : ab.y;
+        const int i = ab.x < ab.y ? ab.y : ab.x;
+        const int64_t bi = rowptr[i], bj = rowptr[j];
+        const int64_t di = rowptr[i + 1] - bi, dj = rowptr[j + 1] - bj;
+        const int32_t *toj = toff + (int64_t)j * (L + 1);
+        unsigned long long tsum = 0;
+        for (int64_t x = lane; x < di; x += 32) {
+            uint32_t w = adj[bi + x];
+            int id = (int)(w & TG_IDMASK);
+            if (id == j) continue;
+            if (contains(adj, bj, toj, w)) tsum += (unsigned long long)(rowptr[id + 1] - rowptr[id]);
+        }
+        for (int o = 16; o; o >>= 1) tsum += __shfl_down_sync(kFull, tsum, o);
+        if (lane == 0) {
+            unsigned long long c = 2ull * di + dj + (s[i] - dj) + (s[j] - di) - tsum;
+            if (edge_cost) edge_cost[e] = c;
+            acc_total += c;
+        }
+    }
+    if (lane == 0 && acc_total) atomicAdd(total, acc_total);
+}
+
+// Schedule keys: most expensive edges first (cost = s_i + s_j), ties by id.
+__global__ void k_sched_keys(const int2 *edges, int64_t M, const unsigned long long *s,
+                             int ebits, int cbits, uint64_t *key) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < M;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int2 ab = edges[e];
+        unsigned long long c = s[ab.x] + s[ab.y];
+        int lb = 64 - __clzll((long long)(c | 1ull));
+        // log-scale bucket (8 sub-steps per octave), descending
+        unsigned long long bucket = (unsigned long long)lb * 8ull +
+                                    ((lb > 3) ? ((c >> (lb - 4)) & 7ull) : 0ull);
+        unsigned long long maxb = (1ull << cbits) - 1ull;
+        if (bucket > maxb) bucket = maxb;
+        key[e] = ((maxb - bucket) << ebits) | (uint64_t)e;
+    }
+}
+
+__global__ void k_sched_unpack(const uint64_t *key, int64_t M, uint64_t emask, int64_t *order) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < M;
+         x += (int64_t)gridDim.x * blockDim.x)
+        order[x] = (int64_t)(key[x] & emask);
+}
+
+inline unsigned grid_for(int64_t n, int threads = 256) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 65535LL * 16) b = 65535LL * 16;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------- schedule -----
+struct tg_sched {
+    int64_t *order = nullptr;               // M edge ids, heaviest first
+    unsigned long long *s = nullptr;        // n neighbour-degree sums
+    int64_t M = 0, n = 0;
+};
+
+void tg_sched_free(tg_graph *g) {
+    if (!g->sched) return;
+    (void)cudaDeviceSynchronize();
+    tg_dfree(g->sched->order, 0, nullptr);
+    tg_dfree(g->sched->s, 0, nullptr);
+    (void)cudaDeviceSynchronize();
+    delete g->sched;
+    g->sched = nullptr;
+}
+
+static int get_sched(const tg_graph *g, cudaStream_t s, tg_sched **out) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (g->sched) {
+        *out = g->sched;
+        return TG_OK;
+    }
+    tg_sched *sc = new (std::nothrow) tg_sched();
+    if (!sc) return TG_ENOMEM;
+    sc->M = g->M;
+    sc->n = g->n;
+    DevBuf<int64_t> order;
+    DevBuf<unsigned long long> sv;
+    if (!order.alloc(g->M > 0 ? g->M : 1, s) || !sv.alloc(g->n, s)) {
+        delete sc;
+        return TG_ENOMEM;
+    }
+    k_neighbor_degree_sum<<<grid_for(g->n * 32), 256, 0, s>>>(g->rowptr, g->adj, g->n, sv.p);
+    if (cudaGetLastError() != cudaSuccess) {
+        delete sc;
+        return TG_ECUDA;
+    }
+    if (g->M > 0) {
+        DevBuf<uint64_t> k1, k2;
+        if (!k1.alloc(g->M, s) || !k2.alloc(g->M, s)) {
+            delete sc;
+            return TG_ENOMEM;
+        }
+        const int ebits = tg_bitlen((uint64_t)g->M);
+        const int cbits = 10;
+        k_sched_keys<<<grid_for(g->M), 256, 0, s>>>(g->edges, g->M, sv.p, ebits, cbits, k1.p);
+        uint64_t *res = k1.p;
+        int r = tg_radix_sort_u64(k1.p, k2.p, g->M, ebits + cbits, s, &res);
+        if (r != TG_OK) {
+            delete sc;
+            return r;
+        }
+        k_sched_unpack<<<grid_for(g->M), 256, 0, s>>>(res, g->M, (1ull << ebits) - 1ull,
+                                                      order.p);
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+            delete sc;
+            return TG_ECUDA;
+        }
+    } else if (cudaStreamSynchronize(s) != cudaSuccess) {
+        delete sc;
+        return TG_ECUDA;
+    }
+    sc->order = order.release();
+    sc->s = sv.release();
+    g->sched = sc;
+    *out = sc;
+    return TG_OK;
+}
+
+// ------------------------------------------------------------ launches ----
+static int num_sms() {
+    int dev = 0, sms = 0;
+    (void)cudaGetDevice(&dev);
+    (void)cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+static size_t warp_smem_bytes(int P) { return ((size_t)C_NUM * P * 4 + 3 * 16 * 4 + 32 * 4 + 15) & ~(size_t)15; }
+
+// Launch the counting kernel over `count` edges (order[item] or e0 + item).
+static int launch_count(const tg_graph *g, int k, int level, const int64_t *order, int64_t e0,
+                        int64_t count, uint64_t *rows, int64_t width,
+                        unsigned long long *hist, cudaStream_t s) {
+    const int L = g->L, P = L * (L + 1) / 2;
+    if (count <= 0) return TG_OK;
+    DevBuf<unsigned long long> queue;
+    if (!queue.alloc(1, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
+    CountParams p{};
+    p.rowptr = g->rowptr;
+    p.adj = g->adj;
+    p.toff = g->toff;
+    p.ntype = g->ntype;
+    p.edges = g->edges;
+    p.order = order;
+    p.e0 = e0;
+    p.count = count;
+    p.L = L;
+    p.P = P;
+    p.k = k;
+    p.level = level;
+    p.queue = queue.p;
+    p.rows = rows;
+    p.width = width;
+    p.hist = hist;
+    p.hist_len = tg_global_len(L, k);
+    p.off1 = tg_binom(L + 1, 2);
+    p.off2 = p.off1 + tg_binom(L + 2, 3);
+    p.off4 = p.off1 + 2 * tg_binom(L + 2, 3);
+    p.n4 = tg_binom(L + 3, 4);
+    const size_t hist_bytes = ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
+    p.hist_smem = (!rows && hist_bytes <= 48 * 1024) ? 1 : 0;
+    const size_t smem = (p.hist_smem ? hist_bytes : 0) + kWarps * warp_smem_bytes(P);
+    TG_TRY_CUDA(cudaFuncSetAttribute(k_count_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    int per_sm = 0;
+    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_warp, kBlock, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)num_sms() * per_sm;
+    const int64_t need = (count + kWarps - 1) / kWarps;
+    if (grid > need) grid = need;
+    k_count_warp<<<(unsigned)grid, kBlock, smem, s>>>(p);
+    TG_TRY_CUDA(cudaGetLastError());
+    return TG_OK;
+}
+
+static int check_counts(const tg_graph *g, int k) {
+    if (!g) return TG_EINVAL;
+    if (k != 3 && k != 4) return TG_EINVAL;
+    // 32-bit per-edge enumerated counters: every one is bounded by 2M; the
+    // flattened walk indexes up to 32 * Delta entries.
+    if (2 * g->M >= ((int64_t)1 << 31) || 32 * g->max_degree >= ((int64_t)1 << 31))
+        return TG_EOVERFLOW;
+    return TG_OK;
+}
+
+static int sums_impl(const tg_graph *g, int k, int64_t e0, int64_t e1,
+                     unsigned long long *dsums, cudaStream_t s) {
+    const int64_t len = tg_global_len(g->L, k);
+    TG_TRY_CUDA(cudaMemsetAsync(dsums, 0, len * 8, s));
+    tg_sched *sc = nullptr;
+    const int64_t *order = nullptr;
+    if (e0 == 0 && e1 == g->M) {
+        TG_TRY(get_sched(g, s, &sc));
+        order = sc->order;
+    }
+    return launch_count(g, k, TG_GRAPHLET, order, e0, e1 - e0, nullptr, 0, dsums, s);
+}
+
+extern "C" int tg_count_global(const tg_graph *g, int32_t k, uint64_t *out, void *stream) {
+    TG_TRY(check_counts(g, k));
+    if (!out) return TG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int L = g->L;
+    const int64_t len = tg_global_len(L, k);
+    DevBuf<unsigned long long> sums;
+    DevBuf<unsigned> err;
+    if (!sums.alloc(len, s) || !err.alloc(1, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(err.p, 0, 4, s));
+    TG_TRY(sums_impl(g, k, 0, g->M, sums.p, s));
+    const bool dev_out = tg_is_device_ptr(out);
+    DevBuf<uint64_t> tmp;
+    uint64_t *dst = out;
+    if (!dev_out) {
+        if (!tmp.alloc(len, s)) return TG_ENOMEM;
+        dst = tmp.p;
+    }
+    const int64_t off1 = tg_binom(L + 1, 2), n3 = tg_binom(L + 2, 3);
+    k_finalize<<<grid_for(len), 256, 0, s>>>(sums.p, dst, len, off1, off1 + n3, off1 + 2 * n3,
+                                             tg_binom(L + 3, 4), err.p);
+    TG_TRY_CUDA(cudaGetLastError());
+    unsigned herr = 0;
+    TG_TRY_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, s));
+    if (!dev_out) TG_TRY_CUDA(cudaMemcpyAsync(out, dst, len * 8, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    if (herr) return TG_EINTERNAL;
+    return TG_OK;
+}
+
+extern "C" int tg_count_range(const tg_graph *g, int32_t k, int64_t e0, int64_t e1,
+                              uint64_t *sums, void *stream) {
+    TG_TRY(check_counts(g, k));
+    if (!sums || e0 < 0 || e1 < e0 || e1 > g->M) return TG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t len = tg_global_len(g->L, k);
+    if (tg_is_device_ptr(sums)) {
+        TG_TRY(sums_impl(g, k, e0, e1, reinterpret_cast<unsigned long long *>(sums), s));
+        TG_TRY_CUDA(cudaStreamSynchronize(s));
+        return TG_OK;
+    }
+    DevBuf<unsigned long long> d;
+    if (!d.alloc(len, s)) return TG_ENOMEM;
+    TG_TRY(sums_impl(g, k, e0, e1, d.p, s));
+    TG_TRY_CUDA(cudaMemcpyAsync(sums, d.p, len * 8, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    return TG_OK;
+}
+
+extern "C" int tg_count_per_edge(const tg_graph *g, int32_t k, int32_t level, uint64_t *rows,
+                                 void *stream) {
+    TG_TRY(check_counts(g, k));
+    if (!rows || (level != TG_GRAPHLET && level != TG_ORBIT)) return TG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t width = tg_slots(g->L, k, level);
+    if (g->M == 0) return TG_OK;
+    tg_sched *sc = nullptr;
+    TG_TRY(get_sched(g, s, &sc));
+    if (tg_is_device_ptr(rows)) {
+        TG_TRY(launch_count(g, k, level, sc->order, 0, g->M, rows, width, nullptr, s));
+        TG_TRY_CUDA(cudaStreamSynchronize(s));
+        return TG_OK;
+    }
+    DevBuf<uint64_t> d;
+    if (!d.alloc((size_t)g->M * width, s)) return TG_ENOMEM;
+    TG_TRY(launch_count(g, k, level, sc->order, 0, g->M, d.p, width, nullptr, s));
+    TG_TRY_CUDA(cudaMemcpyAsync(rows, d.p, (size_t)g->M * width * 8, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    return TG_OK;
+}
+
+extern "C" int tg_work_model(const tg_graph *g, uint64_t *entries, void *stream) {
+    if (!g || !entries) return TG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    *entries = 0;
+    if (g->M == 0) return TG_OK;
+    tg_sched *sc = nullptr;
+    TG_TRY(get_sched(g, s, &sc));
+    DevBuf<unsigned long long> tot;
+    if (!tot.alloc(1, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(tot.p, 0, 8, s));
+    k_work_model<<<grid_for(g->M * 32), 256, 0, s>>>(g->rowptr, g->adj, g->toff, g->edges, g->M,
+                                                     g->L, sc->s, tot.p, nullptr);
+    TG_TRY_CUDA(cudaGetLastError());
+    unsigned long long h = 0;
+    TG_TRY_CUDA(cudaMemcpyAsync(&h, tot.p, 8, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    *entries = h;
+    return TG_OK;
+}

@@ -1,0 +1,114 @@
+// Internal declarations of the typed-graphlet library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "../../include/tg.h"
+
+// Packed adjacency entry: (type << TG_TSHIFT) | node id (new, degree-ordered
+// ids).  Sorting entries as unsigned integers sorts a list by (type, id), so
+// every typed neighbourhood is a contiguous range and the type of a
+// neighbour is read from the entry itself.
+#define TG_TSHIFT 28
+#define TG_IDMASK ((1u << TG_TSHIFT) - 1u)
+
+// Device-side error bits (OR-ed into a flag word the host reads back).
+#define TG_DERR_INPUT 1u      // node id or type out of range in the input
+#define TG_DERR_DIVISIBLE 2u  // a global sum not divisible by |E(H)|
+#define TG_DERR_BOUNDS 4u     // an internal bounds check failed
+
+struct tg_sched;  // per-graph counting schedule (tg_count.cu)
+
+struct tg_graph {
+    int64_t n = 0;
+    int64_t m_input = 0;
+    int64_t M = 0;
+    int64_t n_nonisolated = 0;
+    int64_t max_degree = 0;
+    int32_t L = 0;
+    int device = 0;
+    int64_t device_bytes = 0;
+
+    int64_t *rowptr = nullptr;   // n+1, new ids
+    uint32_t *adj = nullptr;     // 2M packed entries
+    int32_t *toff = nullptr;     // n*(L+1) relative type offsets per node
+    uint8_t *ntype = nullptr;    // n, type of new id
+    int2 *edges = nullptr;       // M, (new a, new b) in canonical order
+    int32_t *new2old = nullptr;  // n
+
+    mutable std::mutex mu;           // guards the lazily built schedule
+    mutable tg_sched *sched = nullptr;
+};
+
+// ----------------------------------------------------------------- memory --
+void *tg_dalloc(size_t bytes, cudaStream_t s);  // NULL on failure
+void tg_dfree(void *p, size_t bytes, cudaStream_t s);
+
+// Scoped device buffer: freed (stream-ordered) when the scope ends.
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t bytes = 0;
+    cudaStream_t s = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { reset(); }
+    bool alloc(size_t count, cudaStream_t st) {
+        reset();
+        s = st;
+        bytes = count * sizeof(T);
+        if (bytes == 0) bytes = sizeof(T);
+        p = static_cast<T *>(tg_dalloc(bytes, st));
+        return p != nullptr;
+    }
+    void reset() {
+        if (p) tg_dfree(p, bytes, s);
+        p = nullptr;
+    }
+    T *release() {
+        T *q = p;
+        p = nullptr;
+        return q;
+    }
+};
+
+#define TG_TRY_CUDA(call)                         \
+    do {                                          \
+        cudaError_t _e = (call);                  \
+        if (_e != cudaSuccess) return TG_ECUDA;   \
+    } while (0)
+
+#define TG_TRY(call)                              \
+    do {                                          \
+        int _r = (call);                          \
+        if (_r != TG_OK) return _r;               \
+    } while (0)
+
+// ------------------------------------------------------------- primitives --
+// Exclusive prefix sums (out may alias in).  n >= 0.
+int tg_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);
+int tg_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+// LSD radix sort of uint64 keys on their low `bits` bits (stable).  `keys` and
+// `tmp` hold n entries each; *result points at whichever holds the output.
+int tg_radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits, cudaStream_t s,
+                      uint64_t **result);
+
+int tg_bitlen(uint64_t x);  // number of bits needed to represent x (0 -> 0)
+
+// Is p a device pointer (or managed)?  Host pointers, registered or not, -> false.
+bool tg_is_device_ptr(const void *p);
+
+// ------------------------------------------------------------- layout -----
+static inline int64_t tg_binom(int64_t a, int64_t b) {
+    if (b < 0 || a < b) return 0;
+    int64_t r = 1;
+    for (int64_t i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+    return r;
+}
+
+// Free the lazily built schedule of a graph (tg_count.cu).
+void tg_sched_free(tg_graph *g);
