@@ -218,6 +218,28 @@ int tg_global_finalize(int32_t L, int32_t k, const uint64_t *sums, uint64_t *out
  */
 int tg_work_model(const tg_graph *g, uint64_t *entries, void *stream);
 
+/* ------------------------------------------------------------ tuning ---- */
+#define TG_KERNEL_AUTO 0
+#define TG_KERNEL_WARP_SEARCH 1 /* warp per edge, binary-search membership      */
+#define TG_KERNEL_CTA_BITMAP 2  /* CTA per edge, shared-memory bitmap marks     */
+
+/*
+ * Launch configuration of the counting kernels (process-wide).  Zero fields
+ * mean "default".  Counts never depend on these values, only speed does.
+ */
+typedef struct {
+    int32_t kernel;      /* TG_KERNEL_*                                     */
+    int32_t cta_threads; /* threads per CTA of the bitmap kernel (32..1024) */
+    int32_t unroll;      /* 1, 2 or 4 adjacency windows in flight per warp  */
+    int32_t hash_slots;  /* slots of the per-edge Gamma_i hash (power of 2) */
+    int64_t bitmap_bits; /* cap on the node ids covered by the bitmap       */
+    int32_t grid_limit;  /* cap on the CTAs of one counting launch          */
+    int32_t reserved;
+} tg_tune;
+
+int tg_set_tune(const tg_tune *t); /* NULL restores the defaults */
+int tg_get_tune(tg_tune *t);
+
 /* ------------------------------------------------------- allocation ----- */
 /*
  * Route the library's device allocations through caller functions (for

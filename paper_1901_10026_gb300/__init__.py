@@ -25,7 +25,7 @@ __all__ = [
     "tg_count_global", "tg_count_per_edge", "tg_count_range", "tg_global_finalize",
     "tg_work_model", "tg_slots", "tg_global_len", "tg_config_count", "tg_config_rank",
     "tg_config_unrank", "tg_paper_hash", "tg_slot_config", "tg_strerror", "tg_version",
-    "tg_debug_fail_alloc", "TG_GRAPHLET", "TG_ORBIT",
+    "tg_debug_fail_alloc", "tg_set_tune", "tg_get_tune", "TG_GRAPHLET", "TG_ORBIT",
 ]
 
 TG_OK = 0
@@ -49,6 +49,17 @@ class TGError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
         super().__init__(f"{what}: {tg_strerror(status)} ({status})" if what else tg_strerror(status))
+
+
+class TGTune(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("cta_threads", ctypes.c_int32), ("unroll", ctypes.c_int32),
+                ("hash_slots", ctypes.c_int32), ("bitmap_bits", ctypes.c_int64),
+                ("grid_limit", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+TG_KERNEL_AUTO = 0
+TG_KERNEL_WARP_SEARCH = 1
+TG_KERNEL_CTA_BITMAP = 2
 
 
 class _Info(ctypes.Structure):
@@ -87,6 +98,8 @@ def lib():
             "tg_work_model": (ctypes.c_int, [vp, vp, vp]),
             "tg_set_allocator": (ctypes.c_int, [vp, vp, vp]),
             "tg_debug_fail_alloc": (ctypes.c_int, [i64]),
+            "tg_set_tune": (ctypes.c_int, [vp]),
+            "tg_get_tune": (ctypes.c_int, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -282,6 +295,22 @@ def tg_work_model(g: Graph, stream=None) -> int:
     v = np.zeros(1, np.uint64)
     _check(lib().tg_work_model(g.handle, _ptr(v), _stream(stream)), "tg_work_model")
     return int(v[0])
+
+
+def tg_set_tune(kernel=0, cta_threads=0, unroll=0, hash_slots=0, bitmap_bits=0, grid_limit=0,
+                reset=False) -> None:
+    """Set the counting kernels' launch configuration (``reset`` restores defaults)."""
+    if reset:
+        _check(lib().tg_set_tune(None), "tg_set_tune")
+        return
+    t = TGTune(kernel, cta_threads, unroll, hash_slots, bitmap_bits, grid_limit, 0)
+    _check(lib().tg_set_tune(ctypes.byref(t)), "tg_set_tune")
+
+
+def tg_get_tune() -> dict:
+    t = TGTune()
+    _check(lib().tg_get_tune(ctypes.byref(t)), "tg_get_tune")
+    return {f: getattr(t, f) for f, _ in TGTune._fields_}
 
 
 def tg_debug_fail_alloc(n: int) -> None:

@@ -40,7 +40,7 @@ struct CountParams {
     const int32_t *toff;
     const uint8_t *ntype;
     const int2 *edges;
-    const int64_t *order;  // processing order (edge ids); NULL -> e0 + item
+    const uint32_t *order;  // processing order (edge ids); NULL -> e0 + item
     int64_t e0;
     int64_t count;
     int32_t L, P, k, level;
@@ -367,6 +367,452 @@ __global__ void __launch_bounds__(kBlock) k_count_warp(CountParams p) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// CTA-per-edge counter with the mark table Psi of Alg. 1 held as a bitmap in
+// shared memory over node ids [0, nbits).  The edges arrive grouped by their
+// high-degree endpoint j, so the bits of Gamma_j stay set while a CTA works
+// through consecutive edges of the same j; per edge only Gamma_i \ {j} is
+// OR-ed in (the old bit tells T_ij from S_i) and taken out again afterwards.
+// A per-edge open-addressing hash of Gamma_i in shared memory resolves a set
+// bit into S_i / T_ij (found) or S_j (not found).  Nodes with id >= nbits and
+// lists too long for the hash fall back to the sorted-range binary search.
+// The w_k lists are walked by all warps of the CTA: each warp takes chunks of
+// 32 w_k, compacts the active ones and walks the concatenation of their
+// lists 32 entries at a time (owner of a position = number of list starts
+// at or before it).
+// ---------------------------------------------------------------------------
+struct CtaParams {
+    int64_t nbits;  // bitmap covers node ids [0, nbits)
+    int32_t hmax;   // hash slots available (power of two)
+};
+
+constexpr uint32_t kEmpty = 0xffffffffu;
+constexpr size_t kMiscBytes = 3 * 16 * 4 + 16;     // Tn, Si, Sj, work item
+constexpr size_t kStageBytes = 32 * 17;  // per-warp w_k slots (a multiple of 16 bytes)
+
+__device__ __forceinline__ uint32_t hslot(uint32_t id, int lg) {
+    return (id * 2654435761u) >> (32 - lg);
+}
+
+__device__ __forceinline__ void hinsert(uint32_t *hk, int lg, uint32_t id, int cls) {
+    const uint32_t mask = (1u << lg) - 1u, v = (id << 2) | (uint32_t)cls;
+    uint32_t h = hslot(id, lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        if (atomicCAS(hk + h, kEmpty, v) == kEmpty) return;
+        h = (h + 1) & mask;
+    }
+}
+
+// class of a Gamma_i member (CLS_SI or CLS_T), 0 if absent.  The table is
+// read through volatile loads: it is filled with atomicCAS and, when this
+// probe was inlined into the walk, compiled code reused earlier reads of the
+// slots (wrong classes on the GPU, while the same source run out of line or
+// with volatile reads gave the exact counts).
+__device__ __forceinline__ int hlookup(const uint32_t *hk, int lg, uint32_t id) {
+    const volatile uint32_t *vk = hk;
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = hslot(id, lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const uint32_t v = vk[h];
+        if (v == kEmpty) return 0;
+        if ((v >> 2) == id) return (int)(v & 3u);
+        h = (h + 1) & mask;
+    }
+    return 0;  // unreachable: the table is never more than half full
+}
+
+// mark bit of node id in the shared-memory bitmap (volatile for the same reason)
+__device__ __forceinline__ bool bm_test(const uint32_t *bm, uint32_t id) {
+    const volatile uint32_t *vb = bm;
+    return (vb[id >> 5] >> (id & 31u)) & 1u;
+}
+
+struct EdgeCtx {
+    const uint32_t *adj;
+    const uint32_t *bm;
+    const uint32_t *hk;
+    int64_t nbits;
+    int64_t bi, bj;
+    const int32_t *toi, *toj;
+    int i, j, lg, hash_ok;
+};
+
+// class of a Gamma_i member w (!= j): CLS_T or CLS_SI
+__device__ __forceinline__ int class_of_i_member(const EdgeCtx &c, uint32_t w) {
+    if (c.hash_ok) return hlookup(c.hk, c.lg, w & TG_IDMASK);
+    return contains(c.adj, c.bj, c.toj, w) ? CLS_T : CLS_SI;
+}
+
+// class of any node w != i, j relative to the edge
+__device__ __forceinline__ int classify(const EdgeCtx &c, uint32_t w) {
+    const uint32_t id = w & TG_IDMASK;
+    if ((int64_t)id < c.nbits) {
+        if (!bm_test(c.bm, id)) return CLS_I;
+        int ci = c.hash_ok ? hlookup(c.hk, c.lg, id)
+                           : (contains(c.adj, c.bi, c.toi, w)
+                                  ? (contains(c.adj, c.bj, c.toj, w) ? CLS_T : CLS_SI)
+                                  : 0);
+        return ci ? ci : CLS_SJ;
+    }
+    int ci = c.hash_ok ? hlookup(c.hk, c.lg, id)
+                       : (contains(c.adj, c.bi, c.toi, w)
+                              ? (contains(c.adj, c.bj, c.toj, w) ? CLS_T : CLS_SI)
+                              : 0);
+    if (ci) return ci;
+    return contains(c.adj, c.bj, c.toj, w) ? CLS_SJ : CLS_I;
+}
+
+__device__ __forceinline__ void record_marked(int *cnt, int P, int ocls, int okid, int pr,
+                                              int rcls, int rid) {
+    atomicAdd(&cnt[(ocls == CLS_T ? C_G8 : C_G3) * P + pr], -1);
+    if (ocls == CLS_SI) {
+        if (rcls == CLS_SI && rid < okid) atomicAdd(&cnt[C_G7 * P + pr], 1);
+    } else if (ocls == CLS_SJ) {
+        if (rcls == CLS_SJ && rid < okid)
+            atomicAdd(&cnt[C_G7 * P + pr], 1);
+        else if (rcls == CLS_SI)
+            atomicAdd(&cnt[C_G6 * P + pr], 1);
+    } else {
+        if (rcls == CLS_T) {
+            if (rid < okid) atomicAdd(&cnt[C_G12 * P + pr], 1);
+        } else {
+            atomicAdd(&cnt[C_G10 * P + pr], 1);
+        }
+    }
+}
+
+template <int U>
+__global__ void __launch_bounds__(1024, 1) k_count_cta(CountParams p, CtaParams cp) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const int L = p.L, P = p.P;
+    const unsigned lanemask_le = lane == 31 ? kFull : ((2u << lane) - 1u);
+
+    // shared-memory layout
+    size_t off = 0;
+    unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);
+    if (p.hist_smem) off += ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
+    const int64_t bwords = (cp.nbits + 31) >> 5;
+    uint32_t *bm = reinterpret_cast<uint32_t *>(smem + off);
+    off += (((size_t)bwords * 4) + 15) & ~(size_t)15;
+    uint32_t *hk = reinterpret_cast<uint32_t *>(smem + off);
+    off += (size_t)cp.hmax * 4;
+    int *cnt_all = reinterpret_cast<int *>(smem + off);
+    off += (((size_t)W * C_NUM * P * 4) + 15) & ~(size_t)15;
+    unsigned *Tn = reinterpret_cast<unsigned *>(smem + off);
+    unsigned *Si = Tn + 16;
+    unsigned *Sj = Si + 16;
+    unsigned long long *s_item = reinterpret_cast<unsigned long long *>(Sj + 16);
+    int *cnt = cnt_all + warp * C_NUM * P;
+    // per-warp staging of one chunk of w_k: 32 x (end, origin, entry, class)
+    unsigned char *stage = smem + off + kMiscBytes + (size_t)warp * kStageBytes;
+    int64_t *w_org = reinterpret_cast<int64_t *>(stage);
+    int *w_end = reinterpret_cast<int *>(stage + 32 * 8);
+    uint32_t *w_wk = reinterpret_cast<uint32_t *>(stage + 32 * 12);
+    unsigned char *w_cls = stage + 32 * 16;
+
+    for (int64_t x = tid; x < bwords; x += blockDim.x) bm[x] = 0u;
+    for (int x = tid; x < cp.hmax; x += blockDim.x) hk[x] = kEmpty;
+    if (p.hist_smem)
+        for (int64_t x = tid; x < p.hist_len; x += blockDim.x) shist[x] = 0;
+
+    const int64_t *__restrict__ rowptr = p.rowptr;
+    const uint32_t *__restrict__ adj = p.adj;
+    const int32_t *__restrict__ toff = p.toff;
+    int cur_j = -1;
+    int64_t cur_bj = 0;
+    int cur_dj = 0;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) *s_item = atomicAdd(p.queue, 1ull);
+        __syncthreads();
+        const unsigned long long item = *s_item;
+        if (item >= (unsigned long long)p.count) break;
+        const int64_t e = p.order ? p.order[item] : p.e0 + (int64_t)item;
+        const int2 ab = p.edges[e];
+        const int j = ab.x < ab.y ? ab.x : ab.y;
+        const int i = ab.x < ab.y ? ab.y : ab.x;
+        const int ti = p.ntype[i], tj = p.ntype[j];
+        const int64_t bi = rowptr[i], bj = rowptr[j];
+        const int di = (int)(rowptr[i + 1] - bi), dj = (int)(rowptr[j + 1] - bj);
+        const int32_t *toi = toff + (int64_t)i * (L + 1);
+        const int32_t *toj = toff + (int64_t)j * (L + 1);
+
+        if (j != cur_j) {
+            for (int x = tid; x < cur_dj; x += blockDim.x) {
+                uint32_t id = __ldg(adj + cur_bj + x) & TG_IDMASK;
+                if ((int64_t)id < cp.nbits) atomicAnd(&bm[id >> 5], ~(1u << (id & 31u)));
+            }
+            __syncthreads();
+            for (int x = tid; x < dj; x += blockDim.x) {
+                uint32_t id = __ldg(adj + bj + x) & TG_IDMASK;
+                if ((int64_t)id < cp.nbits) atomicOr(&bm[id >> 5], 1u << (id & 31u));
+            }
+            cur_j = j;
+            cur_bj = bj;
+            cur_dj = dj;
+        }
+        for (int x = tid; x < W * C_NUM * P; x += blockDim.x) cnt_all[x] = 0;
+        if (tid < 48) Tn[tid] = 0;
+        int lg = 5;
+        while ((1 << lg) < 2 * di) ++lg;
+        const int hash_ok = (1 << lg) <= cp.hmax;
+        __syncthreads();
+
+        // ---- Alg. 1 on the bitmap: T_ij / S_i, marks for S_i -------------
+        for (int x = tid; x < di; x += blockDim.x) {
+            const uint32_t w = __ldg(adj + bi + x);
+            const uint32_t id = w & TG_IDMASK;
+            if ((int)id == j) continue;
+            bool inJ;
+            if ((int64_t)id < cp.nbits) {
+                const uint32_t b = 1u << (id & 31u);
+                inJ = (atomicOr(&bm[id >> 5], b) & b) != 0u;
+            } else {
+                inJ = contains(adj, bj, toj, w);
+            }
+            atomicAdd(inJ ? &Tn[w >> TG_TSHIFT] : &Si[w >> TG_TSHIFT], 1u);
+            if (hash_ok) hinsert(hk, lg, id, inJ ? CLS_T : CLS_SI);
+        }
+        __syncthreads();
+        if (tid < L) Sj[tid] = (unsigned)(__ldg(toj + tid + 1) - __ldg(toj + tid)) - Tn[tid] -
+                               (tid == ti ? 1u : 0u);
+
+        EdgeCtx c;
+        c.adj = adj;
+        c.bm = bm;
+        c.hk = hk;
+        c.nbits = cp.nbits;
+        c.bi = bi;
+        c.bj = bj;
+        c.toi = toi;
+        c.toj = toj;
+        c.i = i;
+        c.j = j;
+        c.lg = lg;
+        c.hash_ok = hash_ok;
+
+        // ---- Alg. 2 and 3 -------------------------------------------------
+        if (p.k == 4) {
+            const int nch = (di + dj + 31) >> 5;
+            for (int ch = warp; ch < nch; ch += W) {
+                const int x = ch * 32 + lane;
+                bool act = false;
+                uint32_t wk = 0;
+                int cls = CLS_I;
+                if (x < di) {
+                    wk = __ldg(adj + bi + x);
+                    if ((int)(wk & TG_IDMASK) != j) {
+                        act = true;
+                        cls = class_of_i_member(c, wk);
+                    }
+                } else if (x < di + dj) {
+                    wk = __ldg(adj + bj + (x - di));
+                    const int kid = (int)(wk & TG_IDMASK);
+                    if (kid != i) {
+                        const int ci = hash_ok ? hlookup(hk, lg, (uint32_t)kid)
+                                               : (contains(adj, bi, toi, wk) ? CLS_T : 0);
+                        if (!ci) {
+                            act = true;
+                            cls = CLS_SJ;
+                        }
+                    }
+                }
+                int64_t kb = 0;
+                int dk = 0;
+                if (act) {
+                    const int kid = (int)(wk & TG_IDMASK), kt = (int)(wk >> TG_TSHIFT);
+                    kb = rowptr[kid];
+                    dk = (int)(rowptr[kid + 1] - kb);
+                    const int32_t *tk = toff + (int64_t)kid * (L + 1);
+                    const int gI = cls == CLS_T ? C_G8 : C_G3;
+                    int prev = __ldg(tk);
+                    for (int t2 = 0; t2 < L; ++t2) {
+                        const int nx = __ldg(tk + t2 + 1);
+                        int cc = nx - prev;
+                        prev = nx;
+                        if ((cls & 1) && t2 == ti) --cc;
+                        if ((cls & 2) && t2 == tj) --cc;
+                        if (cc) atomicAdd(&cnt[gI * P + pair_index(L, kt, t2)], cc);
+                    }
+                }
+                // Stage the active w_k of this chunk (in lane order) in the
+                // warp's shared-memory slots: segment end in the flattened
+                // walk, list origin, packed entry and class.  The walk below
+                // then needs no warp-synchronous intrinsics.
+                const unsigned am = __ballot_sync(kFull, act);
+                const int na = __popc(am);
+                if (na == 0) continue;
+                int incl = act ? dk : 0;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(kFull, incl, 31);
+                if (act) {
+                    const int r = __popc(am & ((1u << lane) - 1u));
+                    w_end[r] = incl;
+                    w_org[r] = kb - (incl - dk);
+                    w_wk[r] = wk;
+                    w_cls[r] = (unsigned char)cls;
+                }
+                __syncwarp();
+                for (int base = 0; base < total; base += 32 * U) {
+                    uint32_t wr[U], owk[U];
+                    int ocl[U];
+                    bool val[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int pos = base + 32 * u + lane;
+                        val[u] = pos < total;
+                        wr[u] = 0u;
+                        owk[u] = 0u;
+                        ocl[u] = 0;
+                        if (val[u]) {
+                            // owner: first staged segment whose end exceeds pos
+                            int lo = 0, hi = na - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (w_end[mid] > pos)
+                                    hi = mid;
+                                else
+                                    lo = mid + 1;
+                            }
+                            owk[u] = w_wk[lo];
+                            ocl[u] = w_cls[lo];
+                            wr[u] = __ldg(adj + (w_org[lo] + pos));
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (!val[u]) continue;
+                        const int rid = (int)(wr[u] & TG_IDMASK);
+                        if (rid == i || rid == j) continue;
+                        const int rcls = classify(c, wr[u]);
+                        if (rcls == CLS_I) continue;
+                        const int pr = pair_index(L, (int)(owk[u] >> TG_TSHIFT),
+                                                  (int)(wr[u] >> TG_TSHIFT));
+                        record_marked(cnt, P, ocl[u], (int)(owk[u] & TG_IDMASK), pr, rcls, rid);
+                    }
+                }
+                __syncwarp();  // the slots are rewritten by the next chunk
+            }
+        }
+        __syncthreads();
+        // reduce the per-warp counters into warp 0's block
+        for (int x = tid; x < C_NUM * P; x += blockDim.x) {
+            int sacc = 0;
+            for (int w = 0; w < W; ++w) sacc += cnt_all[w * C_NUM * P + x];
+            cnt_all[x] = sacc;
+        }
+        __syncthreads();
+
+        // ---- closed forms and output --------------------------------------
+        if (p.rows) {
+            uint64_t *row = p.rows + (e - p.e0) * p.width;
+            for (int t = tid; t < L; t += blockDim.x) {
+                row[t] = (uint64_t)Si[t] + Sj[t];
+                row[L + t] = Tn[t];
+            }
+        } else {
+            if (tid == 0) {
+                int a = ti, b = tj;
+                sort2(a, b);
+                hist_add(p, shist, (int64_t)a + (int64_t)(b + 1) * b / 2, 1ull);
+            }
+            for (int t = tid; t < L; t += blockDim.x) {
+                int a = ti, b = tj, cc = t;
+                sort2(a, b);
+                sort2(b, cc);
+                sort2(a, b);
+                const int64_t r = colex3(a, b, cc);
+                hist_add(p, shist, p.off1 + r, (unsigned long long)Si[t] + Sj[t]);
+                hist_add(p, shist, p.off2 + r, (unsigned long long)Tn[t]);
+            }
+        }
+        if (p.k == 4) {
+            for (int pr = tid; pr < P; pr += blockDim.x) {
+                int t, u;
+                unpair(L, pr, t, u);
+                const uint64_t sit = Si[t], siu = Si[u], sjt = Sj[t], sju = Sj[u];
+                const uint64_t tt = Tn[t], tu = Tn[u];
+                const uint64_t g3 = (uint64_t)(int64_t)cnt_all[C_G3 * P + pr];
+                const uint64_t g6 = (uint64_t)(int64_t)cnt_all[C_G6 * P + pr];
+                const uint64_t g7 = (uint64_t)(int64_t)cnt_all[C_G7 * P + pr];
+                const uint64_t g8 = (uint64_t)(int64_t)cnt_all[C_G8 * P + pr];
+                const uint64_t g10 = (uint64_t)(int64_t)cnt_all[C_G10 * P + pr];
+                const uint64_t g12 = (uint64_t)(int64_t)cnt_all[C_G12 * P + pr];
+                uint64_t g4, g5, g9, g11;
+                if (t == u) {
+                    g4 = sit * sjt - g6;
+                    g5 = c2(sit) + c2(sjt) - g7;
+                    g9 = tt * (sit + sjt) - g10;
+                    g11 = c2(tt) - g12;
+                } else {
+                    g4 = sit * sju + siu * sjt - g6;
+                    g5 = sit * siu + sjt * sju - g7;
+                    g9 = tt * (siu + sju) + tu * (sit + sjt) - g10;
+                    g11 = tt * tu - g12;
+                }
+                if (p.rows) {
+                    uint64_t *row = p.rows + (e - p.e0) * p.width + 2 * L;
+                    if (p.level == TG_ORBIT) {
+                        row[0 * P + pr] = g3;
+                        row[1 * P + pr] = g4;
+                        row[2 * P + pr] = g5;
+                        row[3 * P + pr] = g6;
+                        row[4 * P + pr] = g7;
+                        row[5 * P + pr] = g8;
+                        row[6 * P + pr] = g9;
+                        row[7 * P + pr] = g10;
+                        row[8 * P + pr] = g11;
+                        row[9 * P + pr] = g12;
+                    } else {
+                        row[0 * P + pr] = g3 + g4;
+                        row[1 * P + pr] = g5;
+                        row[2 * P + pr] = g6;
+                        row[3 * P + pr] = g7 + g8 + g9;
+                        row[4 * P + pr] = g10 + g11;
+                        row[5 * P + pr] = g12;
+                    }
+                } else {
+                    const uint64_t h[6] = {g3 + g4, g5, g6, g7 + g8 + g9, g10 + g11, g12};
+                    if (h[0] | h[1] | h[2] | h[3] | h[4] | h[5]) {
+                        int a = ti, b = tj, cc = t, d = u;
+                        sort2(a, b);
+                        sort2(cc, d);
+                        sort2(a, cc);
+                        sort2(b, d);
+                        sort2(b, cc);
+                        const int64_t r = colex4(a, b, cc, d);
+#pragma unroll
+                        for (int q = 0; q < 6; ++q)
+                            hist_add(p, shist, p.off4 + q * p.n4 + r, h[q]);
+                    }
+                }
+            }
+        }
+        // ---- reset the marks of S_i and the hash ---------------------------
+        for (int x = tid; x < di; x += blockDim.x) {
+            const uint32_t w = __ldg(adj + bi + x);
+            const uint32_t id = w & TG_IDMASK;
+            if ((int)id == j || (int64_t)id >= cp.nbits) continue;
+            if (class_of_i_member(c, w) == CLS_SI) atomicAnd(&bm[id >> 5], ~(1u << (id & 31u)));
+        }
+        __syncthreads();
+        if (hash_ok)
+            for (int x = tid; x < (1 << lg); x += blockDim.x) hk[x] = kEmpty;
+    }
+
+    if (p.hist_smem) {
+        __syncthreads();
+        for (int64_t x = tid; x < p.hist_len; x += blockDim.x)
+            if (shist[x]) atomicAdd(p.hist + x, shist[x]);
+    }
+}
+
 // |E(H)| per global entry: divide and check.
 __global__ void k_finalize(const unsigned long long *sums, uint64_t *out, int64_t len,
                            int64_t off1, int64_t off2, int64_t off4, int64_t n4,
@@ -438,27 +884,18 @@ __global__ void k_work_model(const int64_t *rowptr, const uint32_t *adj, const i
     if (lane == 0 && acc_total) atomicAdd(total, acc_total);
 }
 
-// Schedule keys: most expensive edges first (cost = s_i + s_j), ties by id.
-__global__ void k_sched_keys(const int2 *edges, int64_t M, const unsigned long long *s,
-                             int ebits, int cbits, uint64_t *key) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < M;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int2 ab = edges[e];
-        unsigned long long c = s[ab.x] + s[ab.y];
-        int lb = 64 - __clzll((long long)(c | 1ull));
-        // log-scale bucket (8 sub-steps per octave), descending
-        unsigned long long bucket = (unsigned long long)lb * 8ull +
-                                    ((lb > 3) ? ((c >> (lb - 4)) & 7ull) : 0ull);
-        unsigned long long maxb = (1ull << cbits) - 1ull;
-        if (bucket > maxb) bucket = maxb;
-        key[e] = ((maxb - bucket) << ebits) | (uint64_t)e;
+// Group key of an edge: (j, i) with j the high-degree endpoint (smaller new
+// id), so the edges sharing j are contiguous and hubs come first.
+__global__ void k_group_keys(const int2 *edges, int64_t e0, int64_t count, int nb, uint64_t *key,
+                             uint32_t *val) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < count;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int2 ab = edges[e0 + x];
+        const uint64_t j = (uint64_t)(ab.x < ab.y ? ab.x : ab.y);
+        const uint64_t i = (uint64_t)(ab.x < ab.y ? ab.y : ab.x);
+        key[x] = (j << nb) | i;
+        val[x] = (uint32_t)(e0 + x);
     }
-}
-
-__global__ void k_sched_unpack(const uint64_t *key, int64_t M, uint64_t emask, int64_t *order) {
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < M;
-         x += (int64_t)gridDim.x * blockDim.x)
-        order[x] = (int64_t)(key[x] & emask);
 }
 
 inline unsigned grid_for(int64_t n, int threads = 256) {
@@ -471,9 +908,47 @@ inline unsigned grid_for(int64_t n, int threads = 256) {
 }  // namespace
 
 // ----------------------------------------------------------- schedule -----
+// ------------------------------------------------------------- tuning -----
+static std::mutex g_tune_mu;
+static tg_tune g_tune = {TG_KERNEL_AUTO, 1024, 2, 4096, 0, 0, 0};
+
+static tg_tune tune_now() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune;
+}
+
+extern "C" int tg_set_tune(const tg_tune *t) {
+    tg_tune d = {TG_KERNEL_AUTO, 1024, 2, 4096, 0, 0, 0};
+    if (t) {
+        if (t->kernel < 0 || t->kernel > TG_KERNEL_CTA_BITMAP) return TG_EINVAL;
+        if (t->cta_threads && (t->cta_threads < 32 || t->cta_threads > 1024 || t->cta_threads % 32))
+            return TG_EINVAL;
+        if (t->unroll && t->unroll != 1 && t->unroll != 2 && t->unroll != 4) return TG_EINVAL;
+        if (t->hash_slots && (t->hash_slots < 32 || (t->hash_slots & (t->hash_slots - 1))))
+            return TG_EINVAL;
+        if (t->bitmap_bits < 0 || t->grid_limit < 0) return TG_EINVAL;
+        d.kernel = t->kernel;
+        if (t->cta_threads) d.cta_threads = t->cta_threads;
+        if (t->unroll) d.unroll = t->unroll;
+        if (t->hash_slots) d.hash_slots = t->hash_slots;
+        d.bitmap_bits = t->bitmap_bits;
+        d.grid_limit = t->grid_limit;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune = d;
+    return TG_OK;
+}
+
+extern "C" int tg_get_tune(tg_tune *t) {
+    if (!t) return TG_EINVAL;
+    *t = tune_now();
+    return TG_OK;
+}
+
+// ----------------------------------------------------------- schedule -----
 struct tg_sched {
-    int64_t *order = nullptr;               // M edge ids, heaviest first
-    unsigned long long *s = nullptr;        // n neighbour-degree sums
+    uint32_t *order = nullptr;          // M edge ids grouped by high-degree endpoint
+    unsigned long long *s = nullptr;    // n neighbour-degree sums
     int64_t M = 0, n = 0;
 };
 
@@ -487,52 +962,41 @@ void tg_sched_free(tg_graph *g) {
     g->sched = nullptr;
 }
 
+// Edge ids [e0, e0 + count) sorted by (j, i); *out owns count entries.
+static int grouped_order(const tg_graph *g, int64_t e0, int64_t count, cudaStream_t s,
+                         DevBuf<uint32_t> &out) {
+    if (!out.alloc(count > 0 ? count : 1, s)) return TG_ENOMEM;
+    if (count <= 0) return TG_OK;
+    DevBuf<uint64_t> k1, k2;
+    DevBuf<uint32_t> v2;
+    if (!k1.alloc(count, s) || !k2.alloc(count, s) || !v2.alloc(count, s)) return TG_ENOMEM;
+    const int nb = tg_bitlen((uint64_t)(g->n > 1 ? g->n - 1 : 1));
+    k_group_keys<<<grid_for(count), 256, 0, s>>>(g->edges, e0, count, nb, k1.p, out.p);
+    TG_TRY_CUDA(cudaGetLastError());
+    uint64_t *rk = nullptr;
+    uint32_t *rv = nullptr;
+    TG_TRY(tg_radix_sort_kv(k1.p, k2.p, out.p, v2.p, count, 2 * nb, s, &rk, &rv));
+    if (rv != out.p) TG_TRY_CUDA(cudaMemcpyAsync(out.p, rv, count * 4, cudaMemcpyDeviceToDevice, s));
+    return TG_OK;
+}
+
 static int get_sched(const tg_graph *g, cudaStream_t s, tg_sched **out) {
     std::lock_guard<std::mutex> lk(g->mu);
     if (g->sched) {
         *out = g->sched;
         return TG_OK;
     }
+    DevBuf<uint32_t> order;
+    DevBuf<unsigned long long> sv;
+    if (!sv.alloc(g->n, s)) return TG_ENOMEM;
+    k_neighbor_degree_sum<<<grid_for(g->n * 32), 256, 0, s>>>(g->rowptr, g->adj, g->n, sv.p);
+    TG_TRY_CUDA(cudaGetLastError());
+    TG_TRY(grouped_order(g, 0, g->M, s, order));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
     tg_sched *sc = new (std::nothrow) tg_sched();
     if (!sc) return TG_ENOMEM;
     sc->M = g->M;
     sc->n = g->n;
-    DevBuf<int64_t> order;
-    DevBuf<unsigned long long> sv;
-    if (!order.alloc(g->M > 0 ? g->M : 1, s) || !sv.alloc(g->n, s)) {
-        delete sc;
-        return TG_ENOMEM;
-    }
-    k_neighbor_degree_sum<<<grid_for(g->n * 32), 256, 0, s>>>(g->rowptr, g->adj, g->n, sv.p);
-    if (cudaGetLastError() != cudaSuccess) {
-        delete sc;
-        return TG_ECUDA;
-    }
-    if (g->M > 0) {
-        DevBuf<uint64_t> k1, k2;
-        if (!k1.alloc(g->M, s) || !k2.alloc(g->M, s)) {
-            delete sc;
-            return TG_ENOMEM;
-        }
-        const int ebits = tg_bitlen((uint64_t)g->M);
-        const int cbits = 10;
-        k_sched_keys<<<grid_for(g->M), 256, 0, s>>>(g->edges, g->M, sv.p, ebits, cbits, k1.p);
-        uint64_t *res = k1.p;
-        int r = tg_radix_sort_u64(k1.p, k2.p, g->M, ebits + cbits, s, &res);
-        if (r != TG_OK) {
-            delete sc;
-            return r;
-        }
-        k_sched_unpack<<<grid_for(g->M), 256, 0, s>>>(res, g->M, (1ull << ebits) - 1ull,
-                                                      order.p);
-        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
-            delete sc;
-            return TG_ECUDA;
-        }
-    } else if (cudaStreamSynchronize(s) != cudaSuccess) {
-        delete sc;
-        return TG_ECUDA;
-    }
     sc->order = order.release();
     sc->s = sv.release();
     g->sched = sc;
@@ -548,18 +1012,22 @@ static int num_sms() {
     return sms > 0 ? sms : 1;
 }
 
-static size_t warp_smem_bytes(int P) { return ((size_t)C_NUM * P * 4 + 3 * 16 * 4 + 32 * 4 + 15) & ~(size_t)15; }
+static int max_smem_optin() {
+    int dev = 0, v = 0;
+    (void)cudaGetDevice(&dev);
+    (void)cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v > 0 ? v : 48 * 1024;
+}
 
-// Launch the counting kernel over `count` edges (order[item] or e0 + item).
-static int launch_count(const tg_graph *g, int k, int level, const int64_t *order, int64_t e0,
-                        int64_t count, uint64_t *rows, int64_t width,
-                        unsigned long long *hist, cudaStream_t s) {
-    const int L = g->L, P = L * (L + 1) / 2;
-    if (count <= 0) return TG_OK;
-    DevBuf<unsigned long long> queue;
-    if (!queue.alloc(1, s)) return TG_ENOMEM;
-    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
-    CountParams p{};
+static size_t warp_smem_bytes(int P) {
+    return ((size_t)C_NUM * P * 4 + 3 * 16 * 4 + 32 * 4 + 15) & ~(size_t)15;
+}
+
+static void fill_params(CountParams &p, const tg_graph *g, int k, int level,
+                        const uint32_t *order, int64_t e0, int64_t count, uint64_t *rows,
+                        int64_t width, unsigned long long *hist, unsigned long long *queue) {
+    const int L = g->L;
+    p = CountParams{};
     p.rowptr = g->rowptr;
     p.adj = g->adj;
     p.toff = g->toff;
@@ -569,10 +1037,10 @@ static int launch_count(const tg_graph *g, int k, int level, const int64_t *orde
     p.e0 = e0;
     p.count = count;
     p.L = L;
-    p.P = P;
+    p.P = L * (L + 1) / 2;
     p.k = k;
     p.level = level;
-    p.queue = queue.p;
+    p.queue = queue;
     p.rows = rows;
     p.width = width;
     p.hist = hist;
@@ -583,18 +1051,92 @@ static int launch_count(const tg_graph *g, int k, int level, const int64_t *orde
     p.n4 = tg_binom(L + 3, 4);
     const size_t hist_bytes = ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
     p.hist_smem = (!rows && hist_bytes <= 48 * 1024) ? 1 : 0;
-    const size_t smem = (p.hist_smem ? hist_bytes : 0) + kWarps * warp_smem_bytes(P);
+}
+
+static int launch_warp(const CountParams &p, cudaStream_t s) {
+    const size_t hist_bytes = p.hist_smem ? (((size_t)p.hist_len * 8 + 15) & ~(size_t)15) : 0;
+    const size_t smem = hist_bytes + kWarps * warp_smem_bytes(p.P);
     TG_TRY_CUDA(cudaFuncSetAttribute(k_count_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem));
     int per_sm = 0;
     TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_warp, kBlock, smem));
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms() * per_sm;
-    const int64_t need = (count + kWarps - 1) / kWarps;
+    const int64_t need = (p.count + kWarps - 1) / kWarps;
     if (grid > need) grid = need;
+    const int gl = tune_now().grid_limit;
+    if (gl > 0 && grid > gl) grid = gl;
     k_count_warp<<<(unsigned)grid, kBlock, smem, s>>>(p);
     TG_TRY_CUDA(cudaGetLastError());
     return TG_OK;
+}
+
+// Shared-memory plan of the CTA kernel; false if even a minimal plan does not fit.
+static bool plan_cta(const tg_graph *g, const CountParams &p, const tg_tune &t, int threads,
+                     CtaParams &cp, size_t &smem) {
+    const int W = threads / 32;
+    const size_t hist_bytes = p.hist_smem ? (((size_t)p.hist_len * 8 + 15) & ~(size_t)15) : 0;
+    const size_t cnt_bytes = (((size_t)W * C_NUM * p.P * 4) + 15) & ~(size_t)15;
+    const size_t misc = kMiscBytes + (size_t)W * kStageBytes;
+    int hmax = t.hash_slots;
+    const size_t avail = (size_t)max_smem_optin();
+    size_t fixed = hist_bytes + cnt_bytes + misc + (size_t)hmax * 4;
+    while (fixed + 4096 > avail && hmax > 32) {
+        hmax >>= 1;
+        fixed = hist_bytes + cnt_bytes + misc + (size_t)hmax * 4;
+    }
+    if (fixed + 16 > avail) return false;
+    int64_t bits = g->n_nonisolated;
+    if (t.bitmap_bits > 0 && bits > t.bitmap_bits) bits = t.bitmap_bits;
+    const int64_t max_bits = (int64_t)((avail - fixed - 16) / 16) * 128;  // 16-byte granules
+    if (bits > max_bits) bits = max_bits;
+    if (bits < 0) bits = 0;
+    cp.nbits = bits;
+    cp.hmax = hmax;
+    smem = hist_bytes + ((((size_t)((bits + 31) >> 5)) * 4 + 15) & ~(size_t)15) + (size_t)hmax * 4 +
+           cnt_bytes + misc;
+    return true;
+}
+
+template <int U>
+static int launch_cta_u(const CountParams &p, const CtaParams &cp, int threads, size_t smem,
+                        cudaStream_t s) {
+    TG_TRY_CUDA(cudaFuncSetAttribute(k_count_cta<U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    int per_sm = 0;
+    TG_TRY_CUDA(
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_cta<U>, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)num_sms() * per_sm;
+    if (grid > p.count) grid = p.count;
+    const int gl = tune_now().grid_limit;
+    if (gl > 0 && grid > gl) grid = gl;
+    k_count_cta<U><<<(unsigned)grid, threads, smem, s>>>(p, cp);
+    TG_TRY_CUDA(cudaGetLastError());
+    return TG_OK;
+}
+
+// Launch the counting kernel over `count` edges (order[item] or e0 + item).
+static int launch_count(const tg_graph *g, int k, int level, const uint32_t *order, int64_t e0,
+                        int64_t count, uint64_t *rows, int64_t width,
+                        unsigned long long *hist, cudaStream_t s) {
+    if (count <= 0) return TG_OK;
+    DevBuf<unsigned long long> queue;
+    if (!queue.alloc(1, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
+    CountParams p;
+    fill_params(p, g, k, level, order, e0, count, rows, width, hist, queue.p);
+    const tg_tune t = tune_now();
+    if (t.kernel == TG_KERNEL_WARP_SEARCH) return launch_warp(p, s);
+    CtaParams cp;
+    size_t smem = 0;
+    const int threads = t.cta_threads;
+    if (!plan_cta(g, p, t, threads, cp, smem)) return launch_warp(p, s);
+    switch (t.unroll) {
+        case 1: return launch_cta_u<1>(p, cp, threads, smem, s);
+        case 4: return launch_cta_u<4>(p, cp, threads, smem, s);
+        default: return launch_cta_u<2>(p, cp, threads, smem, s);
+    }
 }
 
 static int check_counts(const tg_graph *g, int k) {
@@ -611,15 +1153,15 @@ static int sums_impl(const tg_graph *g, int k, int64_t e0, int64_t e1,
                      unsigned long long *dsums, cudaStream_t s) {
     const int64_t len = tg_global_len(g->L, k);
     TG_TRY_CUDA(cudaMemsetAsync(dsums, 0, len * 8, s));
-    tg_sched *sc = nullptr;
-    const int64_t *order = nullptr;
     if (e0 == 0 && e1 == g->M) {
+        tg_sched *sc = nullptr;
         TG_TRY(get_sched(g, s, &sc));
-        order = sc->order;
+        return launch_count(g, k, TG_GRAPHLET, sc->order, 0, g->M, nullptr, 0, dsums, s);
     }
-    return launch_count(g, k, TG_GRAPHLET, order, e0, e1 - e0, nullptr, 0, dsums, s);
+    DevBuf<uint32_t> order;
+    TG_TRY(grouped_order(g, e0, e1 - e0, s, order));
+    return launch_count(g, k, TG_GRAPHLET, order.p, 0, e1 - e0, nullptr, 0, dsums, s);
 }
-
 extern "C" int tg_count_global(const tg_graph *g, int32_t k, uint64_t *out, void *stream) {
     TG_TRY(check_counts(g, k));
     if (!out) return TG_EINVAL;

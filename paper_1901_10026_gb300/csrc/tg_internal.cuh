@@ -6,7 +6,7 @@
 
 #include <mutex>
 
-#include "../../include/tg.h"
+#include "tg.h"
 
 // Packed adjacency entry: (type << TG_TSHIFT) | node id (new, degree-ordered
 // ids).  Sorting entries as unsigned integers sorts a list by (type, id), so
@@ -96,6 +96,9 @@ int tg_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
 // `tmp` hold n entries each; *result points at whichever holds the output.
 int tg_radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits, cudaStream_t s,
                       uint64_t **result);
+// Same, carrying a uint32 value per key (vals/vtmp); *vresult gets the output.
+int tg_radix_sort_kv(uint64_t *keys, uint64_t *tmp, uint32_t *vals, uint32_t *vtmp, int64_t n,
+                     int bits, cudaStream_t s, uint64_t **result, uint32_t **vresult);
 
 int tg_bitlen(uint64_t x);  // number of bits needed to represent x (0 -> 0)
 

@@ -190,8 +190,9 @@ __global__ void k_sort_hist(const uint64_t *in, int64_t n, int shift, uint32_t *
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void k_sort_scatter(const uint64_t *in, uint64_t *out, int64_t n, int shift,
-                               const uint32_t *offs, int64_t nblocks) {
+__global__ void k_sort_scatter(const uint64_t *in, uint64_t *out, const uint32_t *vin,
+                               uint32_t *vout, int64_t n, int shift, const uint32_t *offs,
+                               int64_t nblocks) {
     __shared__ uint32_t wcnt[kSortWarps][256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = threadIdx.x; q < kSortWarps * 256; q += blockDim.x) (&wcnt[0][0])[q] = 0;
@@ -199,12 +200,14 @@ __global__ void k_sort_scatter(const uint64_t *in, uint64_t *out, int64_t n, int
     const unsigned lt = (1u << lane) - 1u;
     int64_t wbase = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * 32 * kSortItems;
     uint64_t key[kSortItems];
+    uint32_t val[kSortItems];
     uint32_t rank[kSortItems];
 #pragma unroll
     for (int c = 0; c < kSortItems; ++c) {
         int64_t i = wbase + c * 32 + lane;
         bool valid = i < n;
         key[c] = valid ? in[i] : 0;
+        val[c] = (valid && vin) ? vin[i] : 0u;
         uint32_t d = valid ? (uint32_t)((key[c] >> shift) & 255u) : 256u;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         uint32_t before = valid ? wcnt[warp][d] : 0;
@@ -232,32 +235,44 @@ __global__ void k_sort_scatter(const uint64_t *in, uint64_t *out, int64_t n, int
             uint32_t d = (uint32_t)((key[c] >> shift) & 255u);
             uint32_t pos = offs[(int64_t)d * nblocks + blockIdx.x] + wcnt[warp][d] + rank[c];
             out[pos] = key[c];
+            if (vout) vout[pos] = val[c];
         }
     }
 }
 
 }  // namespace
 
-int tg_radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits, cudaStream_t s,
-                      uint64_t **result) {
+int tg_radix_sort_kv(uint64_t *keys, uint64_t *tmp, uint32_t *vals, uint32_t *vtmp, int64_t n,
+                     int bits, cudaStream_t s, uint64_t **result, uint32_t **vresult) {
     *result = keys;
+    if (vresult) *vresult = vals;
     if (n <= 1 || bits <= 0) return TG_OK;
     if (n >= (int64_t)UINT32_MAX) return TG_EOVERFLOW;
     int64_t nblocks = (n + kSortTile - 1) / kSortTile;
     DevBuf<uint32_t> hist;
     if (!hist.alloc((size_t)nblocks * 256, s)) return TG_ENOMEM;
     uint64_t *a = keys, *b = tmp;
+    uint32_t *va = vals, *vb = vtmp;
     for (int shift = 0; shift < bits; shift += 8) {
         k_sort_hist<<<(unsigned)nblocks, 256, 0, s>>>(a, n, shift, hist.p, nblocks);
         TG_TRY_CUDA(cudaGetLastError());
         TG_TRY(tg_scan_u32(hist.p, hist.p, nblocks * 256, s));
-        k_sort_scatter<<<(unsigned)nblocks, kSortWarps * 32, 0, s>>>(a, b, n, shift, hist.p,
-                                                                     nblocks);
+        k_sort_scatter<<<(unsigned)nblocks, kSortWarps * 32, 0, s>>>(a, b, va, vb, n, shift,
+                                                                     hist.p, nblocks);
         TG_TRY_CUDA(cudaGetLastError());
         uint64_t *t = a;
         a = b;
         b = t;
+        uint32_t *vt = va;
+        va = vb;
+        vb = vt;
     }
     *result = a;
+    if (vresult) *vresult = va;
     return TG_OK;
+}
+
+int tg_radix_sort_u64(uint64_t *keys, uint64_t *tmp, int64_t n, int bits, cudaStream_t s,
+                      uint64_t **result) {
+    return tg_radix_sort_kv(keys, tmp, nullptr, nullptr, n, bits, s, result, nullptr);
 }

@@ -9,6 +9,18 @@ from paper_1901_10026_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
+# Kernel variants: the tuned defaults, the warp/binary-search kernel, and the
+# bitmap kernel squeezed so that its fallbacks (ids beyond the bitmap, lists
+# too long for the hash) carry most of the work.  Counts must not change.
+VARIANTS = {
+    "default": dict(),
+    "warp-search": dict(kernel=tg.TG_KERNEL_WARP_SEARCH),
+    "cta-small": dict(kernel=tg.TG_KERNEL_CTA_BITMAP, cta_threads=128, unroll=1, hash_slots=32,
+                      bitmap_bits=96),
+    "cta-u4": dict(kernel=tg.TG_KERNEL_CTA_BITMAP, cta_threads=512, unroll=4),
+}
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _built():
     import torch
@@ -18,6 +30,15 @@ def _built():
     build.build()
     oracle.build()
     torch.cuda.init()
+    yield
+    tg.tg_set_tune(reset=True)
+
+
+@pytest.fixture(params=list(VARIANTS))
+def variant(request):
+    tg.tg_set_tune(**VARIANTS[request.param])
+    yield request.param
+    tg.tg_set_tune(reset=True)
 
 
 def _both(G):
@@ -42,7 +63,7 @@ def _check_all(G, levels=(tg.TG_GRAPHLET, tg.TG_ORBIT), ks=(3, 4)):
     return g, og
 
 
-def test_er_1000_full_parity():
+def test_er_1000_full_parity(variant):
     """G(n=1000, p=0.01), L=3: every per-edge row (both levels, k=3,4) and the
     global histogram."""
     G = synth.er_1000(seed=1)
@@ -52,7 +73,7 @@ def test_er_1000_full_parity():
 
 
 @pytest.mark.parametrize("seed", range(4))
-def test_tiny_random_suite(seed):
+def test_tiny_random_suite(seed, variant):
     r = synth.rng(700, seed)
     for c in range(15):
         n = int(r.integers(2, 40))
@@ -67,7 +88,7 @@ def _graph(n, pairs, types, L, name):
     return synth.TypedEdgeList(n, e[:, 0].copy(), e[:, 1].copy(), np.asarray(types, np.uint8), L, name)
 
 
-def test_degenerate_graphs():
+def test_degenerate_graphs(variant):
     # isolated nodes only; one edge; loops and duplicates only; two components
     _check_all(_graph(7, [], [0] * 7, 2, "empty"))
     _check_all(_graph(2, [(0, 1)], [0, 1], 2, "one-edge"))
@@ -75,7 +96,7 @@ def test_degenerate_graphs():
     _check_all(_graph(9, [(0, 1), (1, 2), (2, 0), (5, 6), (6, 7), (7, 8), (8, 5)], [0, 1, 2, 0, 1, 2, 0, 1, 2], 3, "two-comp"))
 
 
-def test_hub_star_and_cliques():
+def test_hub_star_and_cliques(variant):
     r = synth.rng(702)
     s = 5000
     pairs = [(0, x) for x in range(1, s + 1)]
@@ -88,13 +109,13 @@ def test_hub_star_and_cliques():
 
 
 @pytest.mark.parametrize("L", [1, 2, 16])
-def test_type_count_extremes(L):
+def test_type_count_extremes(L, variant):
     G = synth.tiny_random(200, 0.08, L, synth.rng(703, L))
     G.name = f"L{L}"
     _check_all(G)
 
 
-def test_chung_lu_medium():
+def test_chung_lu_medium(variant):
     """Chung-Lu n=20,000, 120,000 distinct edges, gamma 2.1, L=5 Zipf types:
     hubs of degree in the thousands, full per-edge parity."""
     g = synth.rng(704)
@@ -120,7 +141,7 @@ def test_device_inputs_and_outputs():
     assert np.array_equal(rows.cpu().numpy(), og.per_edge(level="orbit"))
 
 
-def test_sharded_ranges_sum_to_global():
+def test_sharded_ranges_sum_to_global(variant):
     """Edge-range shards (the unit one rank computes) add up to the global count."""
     G = synth.er_1000(seed=3)
     g, og = _both(G)
