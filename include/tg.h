@@ -222,6 +222,7 @@ int tg_work_model(const tg_graph *g, uint64_t *entries, void *stream);
 #define TG_KERNEL_AUTO 0
 #define TG_KERNEL_WARP_SEARCH 1 /* warp per edge, binary-search membership      */
 #define TG_KERNEL_CTA_BITMAP 2  /* CTA per edge, shared-memory bitmap marks     */
+#define TG_KERNEL_REUSE 3       /* Alg. 1 triangle counts reused for Alg. 2-3   */
 
 /*
  * Launch configuration of the counting kernels (process-wide).  Zero fields

@@ -60,6 +60,7 @@ class TGTune(ctypes.Structure):
 TG_KERNEL_AUTO = 0
 TG_KERNEL_WARP_SEARCH = 1
 TG_KERNEL_CTA_BITMAP = 2
+TG_KERNEL_REUSE = 3
 
 
 class _Info(ctypes.Structure):

@@ -21,18 +21,17 @@
 #include <new>
 #include <vector>
 
-#include "tg_internal.cuh"
+#include "tg_device.cuh"
 
 namespace {
 
+using namespace tgd;
+
 constexpr int kWarps = 8;
 constexpr int kBlock = kWarps * 32;
-constexpr unsigned kFull = 0xffffffffu;
 
 // enumerated-orbit counter rows (per warp)
 enum { C_G3 = 0, C_G6 = 1, C_G7 = 2, C_G8 = 3, C_G10 = 4, C_G12 = 5, C_NUM = 6 };
-// classes of a node relative to the edge (bit 0: in Gamma_i, bit 1: in Gamma_j)
-enum { CLS_I = 0, CLS_SI = 1, CLS_SJ = 2, CLS_T = 3 };
 
 struct CountParams {
     const int64_t *rowptr;
@@ -52,58 +51,6 @@ struct CountParams {
     int32_t hist_smem;
     int64_t off1, off2, off4, n4;
 };
-
-__device__ __forceinline__ int pair_index(int L, int a, int b) {
-    if (a > b) {
-        int t = a;
-        a = b;
-        b = t;
-    }
-    return a * L - (a * (a - 1)) / 2 + (b - a);
-}
-
-__device__ __forceinline__ void unpair(int L, int p, int &t, int &u) {
-    t = 0;
-    while (p >= L - t) {
-        p -= L - t;
-        ++t;
-    }
-    u = t + p;
-}
-
-__device__ __forceinline__ uint64_t c2(uint64_t x) { return x < 2 ? 0 : x * (x - 1) / 2; }
-
-__device__ __forceinline__ int64_t colex3(int a, int b, int c) {
-    // a <= b <= c
-    return (int64_t)a + (int64_t)(b + 1) * b / 2 + (int64_t)(c + 2) * (c + 1) * c / 6;
-}
-__device__ __forceinline__ int64_t colex4(int a, int b, int c, int d) {
-    return colex3(a, b, c) + (int64_t)(d + 3) * (d + 2) * (d + 1) * d / 24;
-}
-__device__ __forceinline__ void sort2(int &a, int &b) {
-    if (a > b) {
-        int t = a;
-        a = b;
-        b = t;
-    }
-}
-
-// Is the packed entry w in the list at adj + base?  `to` holds the list's type
-// offsets, so only the typed range Gamma^{type(w)} is searched.
-__device__ __forceinline__ bool contains(const uint32_t *__restrict__ adj, int64_t base,
-                                         const int32_t *__restrict__ to, uint32_t w) {
-    int t = (int)(w >> TG_TSHIFT);
-    int lo = __ldg(to + t), hi = __ldg(to + t + 1);
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        uint32_t x = __ldg(adj + base + mid);
-        if (x < w)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    return lo < __ldg(to + t + 1) && __ldg(adj + base + lo) == w;
-}
 
 __device__ __forceinline__ void hist_add(const CountParams &p, unsigned long long *shist,
                                          int64_t x, unsigned long long v) {
@@ -386,47 +333,6 @@ struct CtaParams {
     int32_t hmax;   // hash slots available (power of two)
 };
 
-constexpr uint32_t kEmpty = 0xffffffffu;
-constexpr size_t kMiscBytes = 3 * 16 * 4 + 16;     // Tn, Si, Sj, work item
-constexpr size_t kStageBytes = 32 * 17;  // per-warp w_k slots (a multiple of 16 bytes)
-
-__device__ __forceinline__ uint32_t hslot(uint32_t id, int lg) {
-    return (id * 2654435761u) >> (32 - lg);
-}
-
-__device__ __forceinline__ void hinsert(uint32_t *hk, int lg, uint32_t id, int cls) {
-    const uint32_t mask = (1u << lg) - 1u, v = (id << 2) | (uint32_t)cls;
-    uint32_t h = hslot(id, lg);
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        if (atomicCAS(hk + h, kEmpty, v) == kEmpty) return;
-        h = (h + 1) & mask;
-    }
-}
-
-// class of a Gamma_i member (CLS_SI or CLS_T), 0 if absent.  The table is
-// read through volatile loads: it is filled with atomicCAS and, when this
-// probe was inlined into the walk, compiled code reused earlier reads of the
-// slots (wrong classes on the GPU, while the same source run out of line or
-// with volatile reads gave the exact counts).
-__device__ __forceinline__ int hlookup(const uint32_t *hk, int lg, uint32_t id) {
-    const volatile uint32_t *vk = hk;
-    const uint32_t mask = (1u << lg) - 1u;
-    uint32_t h = hslot(id, lg);
-    for (uint32_t probe = 0; probe <= mask; ++probe) {
-        const uint32_t v = vk[h];
-        if (v == kEmpty) return 0;
-        if ((v >> 2) == id) return (int)(v & 3u);
-        h = (h + 1) & mask;
-    }
-    return 0;  // unreachable: the table is never more than half full
-}
-
-// mark bit of node id in the shared-memory bitmap (volatile for the same reason)
-__device__ __forceinline__ bool bm_test(const uint32_t *bm, uint32_t id) {
-    const volatile uint32_t *vb = bm;
-    return (vb[id >> 5] >> (id & 31u)) & 1u;
-}
-
 struct EdgeCtx {
     const uint32_t *adj;
     const uint32_t *bm;
@@ -479,6 +385,20 @@ __device__ __forceinline__ void record_marked(int *cnt, int P, int ocls, int oki
             atomicAdd(&cnt[C_G10 * P + pr], 1);
         }
     }
+}
+
+// Orbit row incremented by a marked pair (w_k of class ocls, w_r of class
+// rcls, lower = w_r < w_k), or -1: Alg. 2 (g7 inside one S-set with the
+// symmetry break, g6 from the S_j pass) and Alg. 3 (g12 inside T with the
+// symmetry break, g10 from T to S_i u S_j).
+__device__ __forceinline__ int marked_orbit(int ocls, int rcls, bool lower) {
+    if (ocls == CLS_SI) return (rcls == CLS_SI && lower) ? C_G7 : -1;
+    if (ocls == CLS_SJ) {
+        if (rcls == CLS_SJ) return lower ? C_G7 : -1;
+        return rcls == CLS_SI ? C_G6 : -1;
+    }
+    if (rcls == CLS_T) return lower ? C_G12 : -1;
+    return C_G10;
 }
 
 template <int U>
@@ -621,20 +541,31 @@ __global__ void __launch_bounds__(1024, 1) k_count_cta(CountParams p, CtaParams 
                 }
                 int64_t kb = 0;
                 int dk = 0;
+                const int kid0 = (int)(wk & TG_IDMASK), kt0 = (int)(wk >> TG_TSHIFT);
+                const int gI0 = cls == CLS_T ? C_G8 : C_G3;
+                const int32_t *tk = toff + (int64_t)kid0 * (L + 1);
                 if (act) {
-                    const int kid = (int)(wk & TG_IDMASK), kt = (int)(wk >> TG_TSHIFT);
-                    kb = rowptr[kid];
-                    dk = (int)(rowptr[kid + 1] - kb);
-                    const int32_t *tk = toff + (int64_t)kid * (L + 1);
-                    const int gI = cls == CLS_T ? C_G8 : C_G3;
-                    int prev = __ldg(tk);
+                    kb = rowptr[kid0];
+                    dk = (int)(rowptr[kid0 + 1] - kb);
+                }
+                // typed degree vector of w_k (minus i and j) into g3 / g8,
+                // summed over the lanes that share (orbit, type of w_k)
+                {
+                    const int dkey = act ? (gI0 * 16 + kt0) : -1;
+                    const unsigned dm = __match_any_sync(kFull, dkey);
+                    const bool dlead = act && lane == __ffs(dm) - 1;
+                    int prev = act ? __ldg(tk) : 0;
                     for (int t2 = 0; t2 < L; ++t2) {
-                        const int nx = __ldg(tk + t2 + 1);
-                        int cc = nx - prev;
-                        prev = nx;
-                        if ((cls & 1) && t2 == ti) --cc;
-                        if ((cls & 2) && t2 == tj) --cc;
-                        if (cc) atomicAdd(&cnt[gI * P + pair_index(L, kt, t2)], cc);
+                        int cc = 0;
+                        if (act) {
+                            const int nx = __ldg(tk + t2 + 1);
+                            cc = nx - prev;
+                            prev = nx;
+                            if ((cls & 1) && t2 == ti) --cc;
+                            if ((cls & 2) && t2 == tj) --cc;
+                        }
+                        const int sum = __reduce_add_sync(dm, cc);
+                        if (dlead && sum) atomicAdd(&cnt[gI0 * P + pair_index(L, kt0, t2)], sum);
                     }
                 }
                 // Stage the active w_k of this chunk (in lane order) in the
@@ -687,14 +618,28 @@ __global__ void __launch_bounds__(1024, 1) k_count_cta(CountParams p, CtaParams 
                     }
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        if (!val[u]) continue;
-                        const int rid = (int)(wr[u] & TG_IDMASK);
-                        if (rid == i || rid == j) continue;
-                        const int rcls = classify(c, wr[u]);
-                        if (rcls == CLS_I) continue;
-                        const int pr = pair_index(L, (int)(owk[u] >> TG_TSHIFT),
-                                                  (int)(wr[u] >> TG_TSHIFT));
-                        record_marked(cnt, P, ocl[u], (int)(owk[u] & TG_IDMASK), pr, rcls, rid);
+                        // counter updates of this position: key1 gets -1
+                        // (g3 / g8 correction), key2 gets +1 (g6, g7, g10 or
+                        // g12); -1 means none
+                        int key1 = -1, key2 = -1;
+                        if (val[u]) {
+                            const int rid = (int)(wr[u] & TG_IDMASK);
+                            if (rid != i && rid != j) {
+                                const int rcls = classify(c, wr[u]);
+                                if (rcls != CLS_I) {
+                                    const int pr = pair_index(L, (int)(owk[u] >> TG_TSHIFT),
+                                                              (int)(wr[u] >> TG_TSHIFT));
+                                    key1 = (ocl[u] == CLS_T ? C_G8 : C_G3) * P + pr;
+                                    const int row =
+                                        marked_orbit(ocl[u], rcls, rid < (int)(owk[u] & TG_IDMASK));
+                                    if (row >= 0) key2 = row * P + pr;
+                                }
+                            }
+                        }
+                        const unsigned m1 = __match_any_sync(kFull, key1);
+                        if (key1 >= 0 && lane == __ffs(m1) - 1) atomicAdd(&cnt[key1], -__popc(m1));
+                        const unsigned m2 = __match_any_sync(kFull, key2);
+                        if (key2 >= 0 && lane == __ffs(m2) - 1) atomicAdd(&cnt[key2], __popc(m2));
                     }
                 }
                 __syncwarp();  // the slots are rewritten by the next chunk
@@ -920,7 +865,7 @@ static tg_tune tune_now() {
 extern "C" int tg_set_tune(const tg_tune *t) {
     tg_tune d = {TG_KERNEL_AUTO, 1024, 2, 4096, 0, 0, 0};
     if (t) {
-        if (t->kernel < 0 || t->kernel > TG_KERNEL_CTA_BITMAP) return TG_EINVAL;
+        if (t->kernel < 0 || t->kernel > TG_KERNEL_REUSE) return TG_EINVAL;
         if (t->cta_threads && (t->cta_threads < 32 || t->cta_threads > 1024 || t->cta_threads % 32))
             return TG_EINVAL;
         if (t->unroll && t->unroll != 1 && t->unroll != 2 && t->unroll != 4) return TG_EINVAL;
@@ -1116,11 +1061,17 @@ static int launch_cta_u(const CountParams &p, const CtaParams &cp, int threads, 
     return TG_OK;
 }
 
-// Launch the counting kernel over `count` edges (order[item] or e0 + item).
-static int launch_count(const tg_graph *g, int k, int level, const uint32_t *order, int64_t e0,
-                        int64_t count, uint64_t *rows, int64_t width,
-                        unsigned long long *hist, cudaStream_t s) {
+// Launch the counting kernel over `count` edges (order[item] or e0 + item);
+// full_order is the grouped order of the whole graph.
+static int launch_count(const tg_graph *g, int k, int level, const uint32_t *full_order,
+                        const uint32_t *order, int64_t e0, int64_t count, uint64_t *rows,
+                        int64_t width, unsigned long long *hist, cudaStream_t s) {
     if (count <= 0) return TG_OK;
+    {
+        const tg_tune t0 = tune_now();
+        if ((t0.kernel == TG_KERNEL_AUTO || t0.kernel == TG_KERNEL_REUSE) && order)
+            return tg_reuse_count(g, k, level, full_order, order, count, rows, width, hist, t0, s);
+    }
     DevBuf<unsigned long long> queue;
     if (!queue.alloc(1, s)) return TG_ENOMEM;
     TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
@@ -1153,14 +1104,14 @@ static int sums_impl(const tg_graph *g, int k, int64_t e0, int64_t e1,
                      unsigned long long *dsums, cudaStream_t s) {
     const int64_t len = tg_global_len(g->L, k);
     TG_TRY_CUDA(cudaMemsetAsync(dsums, 0, len * 8, s));
-    if (e0 == 0 && e1 == g->M) {
-        tg_sched *sc = nullptr;
-        TG_TRY(get_sched(g, s, &sc));
-        return launch_count(g, k, TG_GRAPHLET, sc->order, 0, g->M, nullptr, 0, dsums, s);
-    }
+    tg_sched *sc = nullptr;
+    TG_TRY(get_sched(g, s, &sc));
+    if (e0 == 0 && e1 == g->M)
+        return launch_count(g, k, TG_GRAPHLET, sc->order, sc->order, 0, g->M, nullptr, 0, dsums,
+                            s);
     DevBuf<uint32_t> order;
     TG_TRY(grouped_order(g, e0, e1 - e0, s, order));
-    return launch_count(g, k, TG_GRAPHLET, order.p, 0, e1 - e0, nullptr, 0, dsums, s);
+    return launch_count(g, k, TG_GRAPHLET, sc->order, order.p, 0, e1 - e0, nullptr, 0, dsums, s);
 }
 extern "C" int tg_count_global(const tg_graph *g, int32_t k, uint64_t *out, void *stream) {
     TG_TRY(check_counts(g, k));
@@ -1221,13 +1172,13 @@ extern "C" int tg_count_per_edge(const tg_graph *g, int32_t k, int32_t level, ui
     tg_sched *sc = nullptr;
     TG_TRY(get_sched(g, s, &sc));
     if (tg_is_device_ptr(rows)) {
-        TG_TRY(launch_count(g, k, level, sc->order, 0, g->M, rows, width, nullptr, s));
+        TG_TRY(launch_count(g, k, level, sc->order, sc->order, 0, g->M, rows, width, nullptr, s));
         TG_TRY_CUDA(cudaStreamSynchronize(s));
         return TG_OK;
     }
     DevBuf<uint64_t> d;
     if (!d.alloc((size_t)g->M * width, s)) return TG_ENOMEM;
-    TG_TRY(launch_count(g, k, level, sc->order, 0, g->M, d.p, width, nullptr, s));
+    TG_TRY(launch_count(g, k, level, sc->order, sc->order, 0, g->M, d.p, width, nullptr, s));
     TG_TRY_CUDA(cudaMemcpyAsync(rows, d.p, (size_t)g->M * width * 8, cudaMemcpyDeviceToHost, s));
     TG_TRY_CUDA(cudaStreamSynchronize(s));
     return TG_OK;

@@ -115,19 +115,22 @@ __global__ void k_apply_relabel(const uint64_t *key, int64_t n, uint64_t idmask,
 // Directed entries keyed (src << (tb + nb)) | (type(dst) << nb) | dst.
 __global__ void k_directed_keys(const int32_t *lo, const int32_t *hi, int64_t M,
                                 const int32_t *old2new, const uint8_t *ntype, int nb, int tb,
-                                uint64_t *key, int2 *edges) {
+                                uint64_t *key, uint32_t *val, int2 *edges) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < M;
          e += (int64_t)gridDim.x * blockDim.x) {
         uint64_t a = (uint64_t)old2new[lo[e]], b = (uint64_t)old2new[hi[e]];
         key[2 * e] = (a << (tb + nb)) | ((uint64_t)ntype[b] << nb) | b;
         key[2 * e + 1] = (b << (tb + nb)) | ((uint64_t)ntype[a] << nb) | a;
+        val[2 * e] = (uint32_t)e;
+        val[2 * e + 1] = (uint32_t)e;
         edges[e] = make_int2((int)a, (int)b);
     }
 }
 
 // Packs the sorted entries and records the type boundaries of each row.
-__global__ void k_fill_adj(const uint64_t *key, int64_t total, int nb, int tb, int32_t L,
-                           const int64_t *rowptr, uint32_t *adj, int32_t *toff) {
+__global__ void k_fill_adj(const uint64_t *key, const uint32_t *val, int64_t total, int nb,
+                           int tb, int32_t L, const int64_t *rowptr, uint32_t *adj,
+                           uint32_t *eid, int32_t *toff) {
     const uint64_t nmask = ((uint64_t)1 << nb) - 1, tmask = ((uint64_t)1 << tb) - 1;
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < total;
          x += (int64_t)gridDim.x * blockDim.x) {
@@ -136,6 +139,7 @@ __global__ void k_fill_adj(const uint64_t *key, int64_t total, int nb, int tb, i
         int32_t t = (int32_t)((k >> nb) & tmask);
         uint32_t id = (uint32_t)(k & nmask);
         adj[x] = ((uint32_t)t << TG_TSHIFT) | id;
+        eid[x] = val[x];
         int64_t r0 = rowptr[v], r1 = rowptr[v + 1];
         int32_t tp = -1;
         if (x > r0) tp = (int32_t)((key[x - 1] >> nb) & tmask);
@@ -224,6 +228,7 @@ int build_impl(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
                 tg_dfree(g->ntype, 0, s);
                 tg_dfree(g->edges, 0, s);
                 tg_dfree(g->new2old, 0, s);
+                tg_dfree(g->eid, 0, s);
                 delete g;
             }
         }
@@ -286,23 +291,28 @@ int build_impl(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
     g->adj = (uint32_t *)tg_dalloc((total > 0 ? total : 1) * 4, s);
     g->edges = (int2 *)tg_dalloc((M > 0 ? M : 1) * sizeof(int2), s);
     g->toff = (int32_t *)tg_dalloc(n * (L + 1) * 4, s);
-    if (!g->adj || !g->edges || !g->toff) return TG_ENOMEM;
+    g->eid = (uint32_t *)tg_dalloc((total > 0 ? total : 1) * 4, s);
+    if (!g->adj || !g->edges || !g->toff || !g->eid) return TG_ENOMEM;
     TG_TRY_CUDA(cudaMemsetAsync(g->toff, 0, n * (L + 1) * 4, s));
     if (M > 0) {
         DevBuf<uint64_t> d1, d2;
-        if (!d1.alloc(total, s) || !d2.alloc(total, s)) return TG_ENOMEM;
+        DevBuf<uint32_t> v1, v2;
+        if (!d1.alloc(total, s) || !d2.alloc(total, s) || !v1.alloc(total, s) ||
+            !v2.alloc(total, s))
+            return TG_ENOMEM;
         k_directed_keys<<<grid_for(M), kThreads, 0, s>>>(lo.p, hi.p, M, old2new.p, g->ntype, nb,
-                                                         tb, d1.p, g->edges);
+                                                         tb, d1.p, v1.p, g->edges);
         TG_TRY_CUDA(cudaGetLastError());
         uint64_t *ds = d1.p;
-        TG_TRY(tg_radix_sort_u64(d1.p, d2.p, total, 2 * nb + tb, s, &ds));
-        k_fill_adj<<<grid_for(total), kThreads, 0, s>>>(ds, total, nb, tb, L, g->rowptr, g->adj,
-                                                        g->toff);
+        uint32_t *vs = v1.p;
+        TG_TRY(tg_radix_sort_kv(d1.p, d2.p, v1.p, v2.p, total, 2 * nb + tb, s, &ds, &vs));
+        k_fill_adj<<<grid_for(total), kThreads, 0, s>>>(ds, vs, total, nb, tb, L, g->rowptr,
+                                                        g->adj, g->eid, g->toff);
         TG_TRY_CUDA(cudaGetLastError());
     }
     TG_TRY_CUDA(cudaStreamSynchronize(s));
     TG_TRY_CUDA(cudaGetLastError());
-    g->device_bytes = (n + 1) * 8 + total * 4 + n * (L + 1) * 4 + n + M * 8 + n * 4;
+    g->device_bytes = (n + 1) * 8 + 2 * total * 4 + n * (L + 1) * 4 + n + M * 8 + n * 4;
     guard.g = nullptr;
     *out = g;
     return TG_OK;
@@ -331,6 +341,7 @@ extern "C" int tg_free_graph(tg_graph *g) {
     tg_dfree(g->ntype, 0, s);
     tg_dfree(g->edges, 0, s);
     tg_dfree(g->new2old, 0, s);
+    tg_dfree(g->eid, 0, s);
     (void)cudaStreamSynchronize(s);
     delete g;
     return TG_OK;

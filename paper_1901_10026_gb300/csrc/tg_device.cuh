@@ -1,0 +1,108 @@
+// Device helpers shared by the counting kernels (typed pairs, colex ranks,
+// sorted-range membership, the per-edge hash of Gamma_i and the bitmap test).
+#pragma once
+
+#include "tg_internal.cuh"
+
+namespace tgd {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// classes of a node relative to the edge (bit 0: in Gamma_i, bit 1: in Gamma_j)
+enum { CLS_I = 0, CLS_SI = 1, CLS_SJ = 2, CLS_T = 3 };
+
+__device__ __forceinline__ int pair_index(int L, int a, int b) {
+    if (a > b) {
+        int t = a;
+        a = b;
+        b = t;
+    }
+    return a * L - (a * (a - 1)) / 2 + (b - a);
+}
+
+__device__ __forceinline__ void unpair(int L, int p, int &t, int &u) {
+    t = 0;
+    while (p >= L - t) {
+        p -= L - t;
+        ++t;
+    }
+    u = t + p;
+}
+
+__device__ __forceinline__ uint64_t c2(uint64_t x) { return x < 2 ? 0 : x * (x - 1) / 2; }
+
+__device__ __forceinline__ int64_t colex3(int a, int b, int c) {
+    // a <= b <= c
+    return (int64_t)a + (int64_t)(b + 1) * b / 2 + (int64_t)(c + 2) * (c + 1) * c / 6;
+}
+__device__ __forceinline__ int64_t colex4(int a, int b, int c, int d) {
+    return colex3(a, b, c) + (int64_t)(d + 3) * (d + 2) * (d + 1) * d / 24;
+}
+__device__ __forceinline__ void sort2(int &a, int &b) {
+    if (a > b) {
+        int t = a;
+        a = b;
+        b = t;
+    }
+}
+
+// Is the packed entry w in the list at adj + base?  `to` holds the list's type
+// offsets, so only the typed range Gamma^{type(w)} is searched.
+__device__ __forceinline__ bool contains(const uint32_t *__restrict__ adj, int64_t base,
+                                         const int32_t *__restrict__ to, uint32_t w) {
+    int t = (int)(w >> TG_TSHIFT);
+    int lo = __ldg(to + t), hi = __ldg(to + t + 1);
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        uint32_t x = __ldg(adj + base + mid);
+        if (x < w)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo < __ldg(to + t + 1) && __ldg(adj + base + lo) == w;
+}
+
+constexpr uint32_t kEmpty = 0xffffffffu;
+constexpr size_t kMiscBytes = 3 * 16 * 4 + 16;     // Tn, Si, Sj, work item
+constexpr size_t kStageBytes = 32 * 17;  // per-warp w_k slots (a multiple of 16 bytes)
+
+__device__ __forceinline__ uint32_t hslot(uint32_t id, int lg) {
+    return (id * 2654435761u) >> (32 - lg);
+}
+
+__device__ __forceinline__ void hinsert(uint32_t *hk, int lg, uint32_t id, int cls) {
+    const uint32_t mask = (1u << lg) - 1u, v = (id << 2) | (uint32_t)cls;
+    uint32_t h = hslot(id, lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        if (atomicCAS(hk + h, kEmpty, v) == kEmpty) return;
+        h = (h + 1) & mask;
+    }
+}
+
+// class of a Gamma_i member (CLS_SI or CLS_T), 0 if absent.  The table is
+// read through volatile loads: it is filled with atomicCAS and, when this
+// probe was inlined into the walk, compiled code reused earlier reads of the
+// slots (wrong classes on the GPU, while the same source run out of line or
+// with volatile reads gave the exact counts).
+__device__ __forceinline__ int hlookup(const uint32_t *hk, int lg, uint32_t id) {
+    const volatile uint32_t *vk = hk;
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = hslot(id, lg);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const uint32_t v = vk[h];
+        if (v == kEmpty) return 0;
+        if ((v >> 2) == id) return (int)(v & 3u);
+        h = (h + 1) & mask;
+    }
+    return 0;  // unreachable: the table is never more than half full
+}
+
+// mark bit of node id in the shared-memory bitmap (volatile for the same reason)
+__device__ __forceinline__ bool bm_test(const uint32_t *bm, uint32_t id) {
+    const volatile uint32_t *vb = bm;
+    return (vb[id >> 5] >> (id & 31u)) & 1u;
+}
+
+
+}  // namespace tgd

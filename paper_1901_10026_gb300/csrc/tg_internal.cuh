@@ -37,6 +37,7 @@ struct tg_graph {
     int32_t *toff = nullptr;     // n*(L+1) relative type offsets per node
     uint8_t *ntype = nullptr;    // n, type of new id
     int2 *edges = nullptr;       // M, (new a, new b) in canonical order
+    uint32_t *eid = nullptr;     // 2M, canonical edge id of each adjacency entry
     int32_t *new2old = nullptr;  // n
 
     mutable std::mutex mu;           // guards the lazily built schedule
@@ -115,3 +116,9 @@ static inline int64_t tg_binom(int64_t a, int64_t b) {
 
 // Free the lazily built schedule of a graph (tg_count.cu).
 void tg_sched_free(tg_graph *g);
+
+// Counts through Alg. 1's typed triangle counts (tg_reuse.cu).  full_order is
+// the grouped order of all M edges; order[0..count) the edges to count.
+int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_order,
+                   const uint32_t *order, int64_t count, uint64_t *rows, int64_t width,
+                   unsigned long long *hist, const tg_tune &t, cudaStream_t s);

@@ -18,6 +18,9 @@ VARIANTS = {
     "cta-small": dict(kernel=tg.TG_KERNEL_CTA_BITMAP, cta_threads=128, unroll=1, hash_slots=32,
                       bitmap_bits=96),
     "cta-u4": dict(kernel=tg.TG_KERNEL_CTA_BITMAP, cta_threads=512, unroll=4),
+    "reuse-small": dict(kernel=tg.TG_KERNEL_REUSE, cta_threads=64, unroll=1, hash_slots=32,
+                        bitmap_bits=96),
+    "reuse-u4": dict(kernel=tg.TG_KERNEL_REUSE, cta_threads=256, unroll=4, grid_limit=3),
 }
 
 
