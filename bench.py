@@ -1,0 +1,363 @@
+"""Benchmark: typed 3/4-node graphlet counting on one graph (global counts).
+
+Workload: Chung-Lu graph, n = 1,000,000, exactly 8,000,000 distinct edges
+(average degree 16), exponent 2.1, L = 5 node types drawn Zipf(s = 1.2); the
+global typed 2/3/4-node counts in uint64.  One step = the whole path on one
+input: typed CSR build from the device-resident raw edge list
+(tg_build_csr) and the global count (tg_count_global: Alg. 1 for every edge,
+per-edge enumeration, closed forms, reduction, division by |E(H)|).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line (rank 0).  N > 1 runs under torch.distributed.run: every
+rank builds the graph and counts a cost-balanced range of edges, then one
+NCCL sum of the histograms.  ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "typed 4-node graphlet edges/s"
+UNIT = "edges/s"
+WORKLOAD = "Chung-Lu n=1,000,000 m=8,000,000 gamma=2.1, L=5 Zipf(1.2) types, global k=4"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--oracle-edges", type=int, default=6000,
+                    help="edges in the CPU oracle sample (cpu_baseline)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload():
+    from paper_1901_10026_gb300 import synth
+    return synth.cl_1m()
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = open(f"/tmp/tg_clocks_{os.getpid()}.csv", "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.out is not None:
+            self.out.close()
+
+    def summary(self):
+        path = f"/tmp/tg_clocks_{os.getpid()}.csv"
+        if self.proc is None or not os.path.exists(path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        os.remove(path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline --
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = float(json.load(open(path))["hbm_gbs"])
+        return v, "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def committed_traffic():
+    """DRAM bytes per edge of the count kernel from the committed ncu summary,
+    used only while the kernel source still matches the one profiled."""
+    path = os.path.join(ROOT, "profiles", "k_count_reuse_traffic.json")
+    src = os.path.join(ROOT, "paper_1901_10026_gb300", "csrc", "tg_reuse.cu")
+    try:
+        rec = json.load(open(path))
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("source_sha256") != digest:
+            return None
+        return float(rec["dram_bytes_per_edge"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# -------------------------------------------------------------- reference --
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    G = workload()
+    og = oracle.OracleGraph.from_edges(G)
+    rng = np.random.default_rng(0)
+    per_step = max(1, args.oracle_edges // 3)
+    samples = [np.sort(rng.choice(og.M, per_step, replace=False)) for _ in range(args.warmup + args.steps)]
+    times = []
+    for s, pick in enumerate(samples):
+        t0 = time.perf_counter()
+        og.per_edge(k=4, level="graphlet", edges=pick)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    mean = sum(times) / len(times)
+    value = per_step / mean
+    cores = oracle.max_threads()
+    sample = (f"{per_step} random edges of the workload graph per step (per-edge graphlet rows, "
+              f"Alg. 1-3 + closed forms in C, OpenMP)")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD, "n": G.n, "M": og.M, "L": G.L, "k": 4,
+                   "sample_edges_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(G, n_edges):
+    import oracle
+    og = oracle.OracleGraph.from_edges(G)
+    rng = np.random.default_rng(1)
+    pick = np.sort(rng.choice(og.M, min(n_edges, og.M), replace=False))
+    t0 = time.perf_counter()
+    og.per_edge(k=4, level="graphlet", edges=pick)
+    dt = time.perf_counter() - t0
+    return {"value": pick.shape[0] / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{pick.shape[0]} random edges of the workload graph (per-edge graphlet rows, "
+                      f"{dt:.1f} s of CPU time on the host)"}
+
+
+# -------------------------------------------------------------------- gpu ---
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as tdist
+
+    import paper_1901_10026_gb300 as tg
+    from paper_1901_10026_gb300 import dist as tgdist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    G = workload()
+    src_d = torch.from_numpy(G.src).to(dev)
+    dst_d = torch.from_numpy(G.dst).to(dev)
+    typ_d = torch.from_numpy(G.types).to(dev)
+    L, k = G.L, 4
+    glen = tg.tg_global_len(L, k)
+
+    # shard ranges from the canonical edge list of the built graph (untimed)
+    g0 = tg.tg_build_csr(G.n, src_d, dst_d, typ_d, L)
+    M = g0.M
+    if world > 1:
+        eu, ev = tg.tg_edge_list(g0)
+        ranges = tgdist.shard_ranges(tgdist.edge_costs(G.n, eu, ev), world)
+        e0, e1 = ranges[rank]
+    else:
+        e0, e1 = 0, M
+    work_entries = tg.tg_work_model(g0)
+    log_delta = math.log2(max(2, g0.max_degree))
+    g0.close()
+
+    out_d = torch.zeros(glen, dtype=torch.int64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step(host=False):
+        if host:
+            g = tg.tg_build_csr(G.n, G.src, G.dst, G.types, L)
+        else:
+            g = tg.tg_build_csr(G.n, src_d, dst_d, typ_d, L)
+        if world == 1:
+            if host:
+                res = tg.tg_count_global(g, k)
+            else:
+                tg.tg_count_global(g, k, out_d)
+                res = None
+        else:
+            tg.tg_count_range(g, k, e0, e1, out_d)
+            tgdist.allreduce_sums(out_d)
+            res = tg.tg_global_finalize(L, k, out_d.cpu().numpy().view(np.uint64)) if host else None
+        g.close()
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    launches0 = tg.tg_launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    count_ms, timings = [], []
+    with ClockSampler(local) as clk:
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        for s in range(args.steps):
+            flush.zero_()  # L2 flush between steps, outside the step's events
+            ev[s][0].record(stream)
+            step()
+            ev[s][1].record(stream)
+            tm = tg.tg_last_timing()
+            timings.append(tm)
+            count_ms.append(tm["count_ms"])
+        torch.cuda.synchronize()
+        if world > 1:
+            tdist.barrier()
+    clocks = clk.summary()
+    launches = tg.tg_launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    local_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([local_ms], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    else:
+        total_ms = local_ms
+    ms_per_step = total_ms / args.steps
+    value = M / (ms_per_step / 1e3)
+
+    # end to end: host inputs copied in and the histogram read back every step
+    torch.cuda.synchronize()
+    e2e_times = []
+    for s in range(max(1, args.steps)):
+        if world > 1:
+            tdist.barrier()
+        t0 = time.perf_counter()
+        res = step(host=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = G.src.nbytes + G.dst.nbytes + G.types.nbytes
+    d2h = glen * 8
+
+    # roofline of the dominant kernel (the per-edge count kernel)
+    peak, peak_kind = measured_peak_gbs()
+    kern_s = statistics.mean(count_ms) / 1e3
+    units = timings[-1]["edges"]
+    paper_bytes = 4.0 * work_entries * (units / M)
+    tm = timings[-1]
+    # entries the count kernel must touch: Gamma_i, the walked S_i / T lists,
+    # one binary search per probe pair, and per T member two edge ids, two tau
+    # rows, a typed-degree row and the search for its position in Gamma_j
+    own_bytes = 4.0 * (tm["gamma_entries"] + tm["walked_entries"]) + \
+        tm["probe_pairs"] * 4.0 * log_delta + tm["t_members"] * 4.0 * (2 + 3 * L + 1 + log_delta)
+    traffic_per_edge = committed_traffic()
+    roofline = {
+        "bound": "hbm", "achieved": paper_bytes / kern_s / 1e9, "peak": peak, "unit": "GB/s",
+        "frac": paper_bytes / kern_s / 1e9 / peak,
+        "traffic": (traffic_per_edge * units) if traffic_per_edge is not None else None,
+        "peak_kind": peak_kind, "kernel": "k_count_reuse", "kernel_ms": kern_s * 1e3,
+        "algorithmic_bytes": paper_bytes,
+        "algorithmic_basis": "paper work model: 4 B x (2 d_i + d_j + sum of d_w over S_i u S_j u T) per edge",
+        "kernel_own_bytes": own_bytes,
+        "kernel_own_gbs": own_bytes / kern_s / 1e9,
+        "kernel_own_frac": own_bytes / kern_s / 1e9 / peak,
+        "phase_ms": {"tau": tm["tau_ms"], "aggregate": tm["aggregate_ms"], "count": tm["count_ms"]},
+    }
+
+    if rank == 0:
+        cpu = cpu_baseline(G, args.oracle_edges) if world == 1 else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": G.n, "M": M, "m_input": G.m, "L": L, "k": k,
+                       "step": "tg_build_csr + tg_count_global from device-resident inputs",
+                       "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"edge ranges x{world}" if world > 1 else "single GPU"},
+            "clocks": clocks,
+            "e2e": {"value": M / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "gpu_launches": int(launches),
+            "paper_work_entries": int(work_entries),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.barrier()
+        tdist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -252,6 +252,29 @@ typedef void *(*tg_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*tg_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 int tg_set_allocator(tg_alloc_fn alloc, tg_free_fn free_fn, void *ctx);
 
+/* ------------------------------------------------------- measurement ---- */
+/* Kernels launched by this library since it was loaded. */
+uint64_t tg_launch_count(void);
+
+/*
+ * Timing and work of the last counting call of this process that used the
+ * default kernel (CUDA events recorded on that call's stream around each
+ * kernel).  Waits for those events.  Returns TG_ENOTFOUND before any call.
+ */
+typedef struct {
+    double tau_ms;            /* Alg. 1 typed triangle counts, every edge   */
+    double aggregate_ms;      /* per-node sums of tau and typed degrees     */
+    double count_ms;          /* per-edge enumeration, identities, output   */
+    uint64_t edges;           /* edges counted                               */
+    uint64_t gamma_entries;   /* entries of Gamma_i read by the count kernel */
+    uint64_t walked_entries;  /* entries of S_i / T lists walked (4-cycles,
+                                 4-cliques)                                  */
+    uint64_t probe_pairs;     /* (T member, T member) adjacency probes       */
+    uint64_t t_members;       /* T members whose tau rows were read          */
+} tg_timing;
+
+int tg_last_timing(tg_timing *out);
+
 /* Failure injection for tests: make the n-th device allocation from now on
  * fail (n >= 1), or disable with n = 0.  Host-side only: the allocation is
  * refused before any CUDA call is made. */

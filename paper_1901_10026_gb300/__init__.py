@@ -25,7 +25,8 @@ __all__ = [
     "tg_count_global", "tg_count_per_edge", "tg_count_range", "tg_global_finalize",
     "tg_work_model", "tg_slots", "tg_global_len", "tg_config_count", "tg_config_rank",
     "tg_config_unrank", "tg_paper_hash", "tg_slot_config", "tg_strerror", "tg_version",
-    "tg_debug_fail_alloc", "tg_set_tune", "tg_get_tune", "TG_GRAPHLET", "TG_ORBIT",
+    "tg_debug_fail_alloc", "tg_set_tune", "tg_get_tune", "tg_launch_count", "tg_last_timing",
+    "TG_GRAPHLET", "TG_ORBIT",
 ]
 
 TG_OK = 0
@@ -55,6 +56,13 @@ class TGTune(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("cta_threads", ctypes.c_int32), ("unroll", ctypes.c_int32),
                 ("hash_slots", ctypes.c_int32), ("bitmap_bits", ctypes.c_int64),
                 ("grid_limit", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class TGTiming(ctypes.Structure):
+    _fields_ = [("tau_ms", ctypes.c_double), ("aggregate_ms", ctypes.c_double),
+                ("count_ms", ctypes.c_double), ("edges", ctypes.c_uint64),
+                ("gamma_entries", ctypes.c_uint64), ("walked_entries", ctypes.c_uint64),
+                ("probe_pairs", ctypes.c_uint64), ("t_members", ctypes.c_uint64)]
 
 
 TG_KERNEL_AUTO = 0
@@ -100,6 +108,8 @@ def lib():
             "tg_set_allocator": (ctypes.c_int, [vp, vp, vp]),
             "tg_debug_fail_alloc": (ctypes.c_int, [i64]),
             "tg_set_tune": (ctypes.c_int, [vp]),
+            "tg_launch_count": (u64, []),
+            "tg_last_timing": (ctypes.c_int, [vp]),
             "tg_get_tune": (ctypes.c_int, [vp]),
         }
         for name, (res, args) in sig.items():
@@ -312,6 +322,18 @@ def tg_get_tune() -> dict:
     t = TGTune()
     _check(lib().tg_get_tune(ctypes.byref(t)), "tg_get_tune")
     return {f: getattr(t, f) for f, _ in TGTune._fields_}
+
+
+def tg_launch_count() -> int:
+    """Kernels launched by libtg.so so far in this process."""
+    return int(lib().tg_launch_count())
+
+
+def tg_last_timing() -> dict:
+    """Per-phase device times (ms) and work counters of the last count call."""
+    t = TGTiming()
+    _check(lib().tg_last_timing(ctypes.byref(t)), "tg_last_timing")
+    return {f: getattr(t, f) for f, _ in TGTiming._fields_}
 
 
 def tg_debug_fail_alloc(n: int) -> None:

@@ -916,7 +916,7 @@ static int grouped_order(const tg_graph *g, int64_t e0, int64_t count, cudaStrea
     DevBuf<uint32_t> v2;
     if (!k1.alloc(count, s) || !k2.alloc(count, s) || !v2.alloc(count, s)) return TG_ENOMEM;
     const int nb = tg_bitlen((uint64_t)(g->n > 1 ? g->n - 1 : 1));
-    k_group_keys<<<grid_for(count), 256, 0, s>>>(g->edges, e0, count, nb, k1.p, out.p);
+    k_group_keys<<<grid_for(count), 256, 0, s>>>(g->edges, e0, count, nb, k1.p, out.p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     uint64_t *rk = nullptr;
     uint32_t *rv = nullptr;
@@ -934,7 +934,7 @@ static int get_sched(const tg_graph *g, cudaStream_t s, tg_sched **out) {
     DevBuf<uint32_t> order;
     DevBuf<unsigned long long> sv;
     if (!sv.alloc(g->n, s)) return TG_ENOMEM;
-    k_neighbor_degree_sum<<<grid_for(g->n * 32), 256, 0, s>>>(g->rowptr, g->adj, g->n, sv.p);
+    k_neighbor_degree_sum<<<grid_for(g->n * 32), 256, 0, s>>>(g->rowptr, g->adj, g->n, sv.p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     TG_TRY(grouped_order(g, 0, g->M, s, order));
     TG_TRY_CUDA(cudaStreamSynchronize(s));
@@ -1011,7 +1011,7 @@ static int launch_warp(const CountParams &p, cudaStream_t s) {
     if (grid > need) grid = need;
     const int gl = tune_now().grid_limit;
     if (gl > 0 && grid > gl) grid = gl;
-    k_count_warp<<<(unsigned)grid, kBlock, smem, s>>>(p);
+    k_count_warp<<<(unsigned)grid, kBlock, smem, s>>>(p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     return TG_OK;
 }
@@ -1056,7 +1056,7 @@ static int launch_cta_u(const CountParams &p, const CtaParams &cp, int threads, 
     if (grid > p.count) grid = p.count;
     const int gl = tune_now().grid_limit;
     if (gl > 0 && grid > gl) grid = gl;
-    k_count_cta<U><<<(unsigned)grid, threads, smem, s>>>(p, cp);
+    k_count_cta<U><<<(unsigned)grid, threads, smem, s>>>(p, cp); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     return TG_OK;
 }
@@ -1133,7 +1133,7 @@ extern "C" int tg_count_global(const tg_graph *g, int32_t k, uint64_t *out, void
     }
     const int64_t off1 = tg_binom(L + 1, 2), n3 = tg_binom(L + 2, 3);
     k_finalize<<<grid_for(len), 256, 0, s>>>(sums.p, dst, len, off1, off1 + n3, off1 + 2 * n3,
-                                             tg_binom(L + 3, 4), err.p);
+                                             tg_binom(L + 3, 4), err.p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     unsigned herr = 0;
     TG_TRY_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, s));
@@ -1195,7 +1195,7 @@ extern "C" int tg_work_model(const tg_graph *g, uint64_t *entries, void *stream)
     if (!tot.alloc(1, s)) return TG_ENOMEM;
     TG_TRY_CUDA(cudaMemsetAsync(tot.p, 0, 8, s));
     k_work_model<<<grid_for(g->M * 32), 256, 0, s>>>(g->rowptr, g->adj, g->toff, g->edges, g->M,
-                                                     g->L, sc->s, tot.p, nullptr);
+                                                     g->L, sc->s, tot.p, nullptr); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     unsigned long long h = 0;
     TG_TRY_CUDA(cudaMemcpyAsync(&h, tot.p, 8, cudaMemcpyDeviceToHost, s));

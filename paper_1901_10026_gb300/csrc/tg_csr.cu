@@ -181,7 +181,7 @@ int build_impl(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
         pdst = ddst.p;
         ptype = dtype.p;
     }
-    k_check_types<<<grid_for(n), kThreads, 0, s>>>(ptype, n, L, err.p);
+    k_check_types<<<grid_for(n), kThreads, 0, s>>>(ptype, n, L, err.p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
 
     // 1-2. canonical keys, sort, unique.
@@ -190,7 +190,7 @@ int build_impl(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
     const uint64_t sentinel = (uint64_t)n * (uint64_t)n;
     uint64_t *sorted = k1.p;
     if (m > 0) {
-        k_canon_keys<<<grid_for(m), kThreads, 0, s>>>(psrc, pdst, m, n, k1.p, err.p);
+        k_canon_keys<<<grid_for(m), kThreads, 0, s>>>(psrc, pdst, m, n, k1.p, err.p); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
         TG_TRY(tg_radix_sort_u64(k1.p, k2.p, m, tg_bitlen(sentinel), s, &sorted));
     }
@@ -198,7 +198,7 @@ int build_impl(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
     if (!flag.alloc(m, s) || !pos.alloc(m, s)) return TG_ENOMEM;
     uint32_t last[2] = {0, 0};
     if (m > 0) {
-        k_unique_flags<<<grid_for(m), kThreads, 0, s>>>(sorted, m, sentinel, flag.p);
+        k_unique_flags<<<grid_for(m), kThreads, 0, s>>>(sorted, m, sentinel, flag.p); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
         TG_TRY(tg_scan_u32(flag.p, pos.p, m, s));
         TG_TRY_CUDA(cudaMemcpyAsync(&last[0], pos.p + (m - 1), 4, cudaMemcpyDeviceToHost, s));
@@ -239,7 +239,7 @@ int build_impl(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
     TG_TRY_CUDA(cudaMemsetAsync(deg.p, 0, n * 4, s));
     if (m > 0) {
         k_compact_edges<<<grid_for(m), kThreads, 0, s>>>(sorted, flag.p, pos.p, m, n, lo.p, hi.p,
-                                                         deg.p);
+                                                         deg.p); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
     }
     k1.reset();
@@ -251,7 +251,7 @@ int build_impl(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
     DevBuf<unsigned long long> stats;
     if (!stats.alloc(2, s)) return TG_ENOMEM;
     TG_TRY_CUDA(cudaMemsetAsync(stats.p, 0, 2 * sizeof(unsigned long long), s));
-    k_max_deg<<<grid_for(n), kThreads, 0, s>>>(deg.p, n, stats.p, stats.p + 1);
+    k_max_deg<<<grid_for(n), kThreads, 0, s>>>(deg.p, n, stats.p, stats.p + 1); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     unsigned long long hstats[2] = {0, 0};
     TG_TRY_CUDA(cudaMemcpyAsync(hstats, stats.p, sizeof(hstats), cudaMemcpyDeviceToHost, s));
@@ -263,7 +263,7 @@ int build_impl(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
     const int tb = tg_bitlen((uint64_t)(L - 1)) > 0 ? tg_bitlen((uint64_t)(L - 1)) : 1;
     DevBuf<uint64_t> r1, r2;
     if (!r1.alloc(n, s) || !r2.alloc(n, s)) return TG_ENOMEM;
-    k_relabel_keys<<<grid_for(n), kThreads, 0, s>>>(deg.p, n, g->max_degree, nb, r1.p);
+    k_relabel_keys<<<grid_for(n), kThreads, 0, s>>>(deg.p, n, g->max_degree, nb, r1.p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     uint64_t *rs = r1.p;
     TG_TRY(tg_radix_sort_u64(r1.p, r2.p, n, nb + tg_bitlen((uint64_t)g->max_degree), s, &rs));
@@ -277,7 +277,7 @@ int build_impl(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
     if (!g->new2old || !g->ntype || !g->rowptr) return TG_ENOMEM;
     k_apply_relabel<<<grid_for(n), kThreads, 0, s>>>(rs, n, ((uint64_t)1 << nb) - 1, deg.p,
                                                      ptype, g->new2old, old2new.p, ndeg.p,
-                                                     g->ntype);
+                                                     g->ntype); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     TG_TRY_CUDA(cudaMemsetAsync(ndeg.p + n, 0, 8, s));
     TG_TRY(tg_scan_i64(ndeg.p, g->rowptr, n + 1, s));
@@ -301,13 +301,13 @@ int build_impl(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
             !v2.alloc(total, s))
             return TG_ENOMEM;
         k_directed_keys<<<grid_for(M), kThreads, 0, s>>>(lo.p, hi.p, M, old2new.p, g->ntype, nb,
-                                                         tb, d1.p, v1.p, g->edges);
+                                                         tb, d1.p, v1.p, g->edges); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
         uint64_t *ds = d1.p;
         uint32_t *vs = v1.p;
         TG_TRY(tg_radix_sort_kv(d1.p, d2.p, v1.p, v2.p, total, 2 * nb + tb, s, &ds, &vs));
         k_fill_adj<<<grid_for(total), kThreads, 0, s>>>(ds, vs, total, nb, tb, L, g->rowptr,
-                                                        g->adj, g->eid, g->toff);
+                                                        g->adj, g->eid, g->toff); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
     }
     TG_TRY_CUDA(cudaStreamSynchronize(s));
@@ -379,7 +379,7 @@ extern "C" int tg_edge_list(const tg_graph *g, int32_t *u, int32_t *v, void *str
     if (g->M == 0) return TG_OK;
     DevBuf<int32_t> du, dv;
     if (!du.alloc(g->M, s) || !dv.alloc(g->M, s)) return TG_ENOMEM;
-    k_edge_list<<<grid_for(g->M), kThreads, 0, s>>>(g->edges, g->new2old, g->M, du.p, dv.p);
+    k_edge_list<<<grid_for(g->M), kThreads, 0, s>>>(g->edges, g->new2old, g->M, du.p, dv.p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     TG_TRY_CUDA(cudaMemcpyAsync(u, du.p, g->M * 4, cudaMemcpyDefault, s));
     TG_TRY_CUDA(cudaMemcpyAsync(v, dv.p, g->M * 4, cudaMemcpyDefault, s));

@@ -103,6 +103,9 @@ int tg_radix_sort_kv(uint64_t *keys, uint64_t *tmp, uint32_t *vals, uint32_t *vt
 
 int tg_bitlen(uint64_t x);  // number of bits needed to represent x (0 -> 0)
 
+// Counts every kernel this library launches (reported by tg_launch_count).
+void tg_note_launch();
+
 // Is p a device pointer (or managed)?  Host pointers, registered or not, -> false.
 bool tg_is_device_ptr(const void *p);
 

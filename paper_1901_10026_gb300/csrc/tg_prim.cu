@@ -10,6 +10,11 @@ static tg_alloc_fn g_alloc = nullptr;
 static tg_free_fn g_free = nullptr;
 static void *g_alloc_ctx = nullptr;
 static std::atomic<int64_t> g_fail_countdown{0};
+static std::atomic<uint64_t> g_launches{0};
+
+void tg_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+extern "C" uint64_t tg_launch_count(void) { return g_launches.load(); }
 
 extern "C" int tg_set_allocator(tg_alloc_fn alloc, tg_free_fn free_fn, void *ctx) {
     if ((alloc == nullptr) != (free_fn == nullptr)) return TG_EINVAL;
@@ -143,16 +148,16 @@ int scan_impl(const T *in, T *out, int64_t n, cudaStream_t s) {
     if (n <= 0) return TG_OK;
     int64_t blocks = (n + kScanTile - 1) / kScanTile;
     if (blocks == 1) {
-        k_tile_scan<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr);
+        k_tile_scan<T><<<1, kScanThreads, 0, s>>>(in, out, n, nullptr); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
         return TG_OK;
     }
     DevBuf<T> part;
     if (!part.alloc(blocks, s)) return TG_ENOMEM;
-    k_tile_reduce<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(in, n, part.p);
+    k_tile_reduce<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(in, n, part.p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     TG_TRY(scan_impl<T>(part.p, part.p, blocks, s));
-    k_tile_scan<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(in, out, n, part.p);
+    k_tile_scan<T><<<(unsigned)blocks, kScanThreads, 0, s>>>(in, out, n, part.p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     return TG_OK;
 }
@@ -254,11 +259,11 @@ int tg_radix_sort_kv(uint64_t *keys, uint64_t *tmp, uint32_t *vals, uint32_t *vt
     uint64_t *a = keys, *b = tmp;
     uint32_t *va = vals, *vb = vtmp;
     for (int shift = 0; shift < bits; shift += 8) {
-        k_sort_hist<<<(unsigned)nblocks, 256, 0, s>>>(a, n, shift, hist.p, nblocks);
+        k_sort_hist<<<(unsigned)nblocks, 256, 0, s>>>(a, n, shift, hist.p, nblocks); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
         TG_TRY(tg_scan_u32(hist.p, hist.p, nblocks * 256, s));
         k_sort_scatter<<<(unsigned)nblocks, kSortWarps * 32, 0, s>>>(a, b, va, vb, n, shift,
-                                                                     hist.p, nblocks);
+                                                                     hist.p, nblocks); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
         uint64_t *t = a;
         a = b;

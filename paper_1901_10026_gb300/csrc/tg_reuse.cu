@@ -30,6 +30,7 @@
 // g4, g5, g9, g11 then follow from Sec. "Combinatorial Relationships" as in
 // the paper.  The counts equal those of Alg. 1-3 exactly; the work drops from
 // sum over w in S_i u S_j u T of d_w to the small side's enumerations.
+#include <mutex>
 #include <new>
 
 #include "tg_device.cuh"
@@ -213,6 +214,7 @@ struct ReuseParams {
     int64_t hist_len;
     int32_t hist_smem;
     int64_t off1, off2, off4, n4;
+    unsigned long long *work;  // [Gamma_i entries, walked entries, probe pairs, T members]
 };
 
 // index of packed entry w in the list at adj + base (typed range search), -1 if absent
@@ -292,6 +294,7 @@ __global__ void __launch_bounds__(1024, 1) k_count_reuse(ReuseParams p) {
     int cur_j = -1;
     int64_t cur_bj = 0;
     int cur_dj = 0;
+    unsigned long long wk_gamma = 0, wk_walk = 0, wk_probe = 0, wk_tmem = 0;  // thread 0
 
     for (;;) {
         __syncthreads();
@@ -352,6 +355,10 @@ __global__ void __launch_bounds__(1024, 1) k_count_reuse(ReuseParams p) {
                       (tid == ti ? 1u : 0u);
         const unsigned ntl = *s_ntl;
         const bool tl_ok = ntl <= (unsigned)kTCap;
+        if (tid == 0) {
+            wk_gamma += (unsigned long long)di;
+            wk_tmem += ntl;
+        }
 
         if (p.k == 4) {
             // Gamma_i in tiles of one member per thread.  Per tile: T members
@@ -453,6 +460,10 @@ __global__ void __launch_bounds__(1024, 1) k_count_reuse(ReuseParams p) {
                     const int r = (int)(((incl >> 41) & mcnt) - 1);
                     p_wk[r] = wk;
                     p_kb[r] = kb;
+                }
+                if (tid == 0) {
+                    wk_walk += (unsigned long long)total;
+                    wk_probe += (unsigned long long)nprobe * ntl;
                 }
                 __syncthreads();
                 // walk the concatenated lists of the staged members
@@ -666,6 +677,34 @@ __global__ void __launch_bounds__(1024, 1) k_count_reuse(ReuseParams p) {
         for (int64_t x = tid; x < p.hist_len; x += blockDim.x)
             if (shist[x]) atomicAdd(p.hist + x, shist[x]);
     }
+    if (tid == 0 && p.work) {
+        atomicAdd(p.work + 0, wk_gamma);
+        atomicAdd(p.work + 1, wk_walk);
+        atomicAdd(p.work + 2, wk_probe);
+        atomicAdd(p.work + 3, wk_tmem);
+    }
+}
+
+// Events and work counters of the last call (see tg_last_timing).
+struct LastTiming {
+    std::mutex mu;
+    bool ready = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    unsigned long long *work = nullptr;  // device, 4 counters
+    uint64_t edges = 0;
+};
+LastTiming g_last;
+
+int timing_begin(cudaStream_t s, unsigned long long **work) {
+    std::lock_guard<std::mutex> lk(g_last.mu);
+    if (!g_last.ev[0]) {
+        for (auto &e : g_last.ev) TG_TRY_CUDA(cudaEventCreate(&e));
+        TG_TRY_CUDA(cudaMalloc(&g_last.work, 4 * sizeof(unsigned long long)));
+    }
+    g_last.ready = false;
+    TG_TRY_CUDA(cudaMemsetAsync(g_last.work, 0, 4 * sizeof(unsigned long long), s));
+    *work = g_last.work;
+    return TG_OK;
 }
 
 int num_sms_r() {
@@ -702,7 +741,7 @@ int launch_reuse_u(const ReuseParams &p, int threads, size_t smem, int grid_limi
     if (grid > p.count) grid = p.count;
     if (grid_limit > 0 && grid > grid_limit) grid = grid_limit;
     if (grid < 1) grid = 1;
-    k_count_reuse<U><<<(unsigned)grid, threads, smem, s>>>(p);
+    k_count_reuse<U><<<(unsigned)grid, threads, smem, s>>>(p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     return TG_OK;
 }
@@ -717,6 +756,8 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
     if (count <= 0) return TG_OK;
     const int L = g->L, L2 = L * L;
     const int64_t M = g->M, n = g->n;
+    unsigned long long *work = nullptr;
+    TG_TRY(timing_begin(s, &work));
     // tau for every edge of the graph (the identities need tau of edges
     // outside the counted range as well)
     DevBuf<uint32_t> tau, theta, dsum, flag, pos, ustart;
@@ -726,7 +767,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
         const uint32_t *ord = full_order;
         const int64_t cnt = M;
         if (!flag.alloc(cnt, s) || !pos.alloc(cnt, s)) return TG_ENOMEM;
-        k_unit_flags<<<grid_r(cnt), 256, 0, s>>>(ord, g->edges, cnt, flag.p);
+        k_unit_flags<<<grid_r(cnt), 256, 0, s>>>(ord, g->edges, cnt, flag.p); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
         TG_TRY(tg_scan_u32(flag.p, pos.p, cnt, s));
         uint32_t lastp = 0, lastf = 0;
@@ -735,11 +776,12 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
         TG_TRY_CUDA(cudaStreamSynchronize(s));
         const uint32_t nunits = lastp + lastf;
         if (!ustart.alloc((size_t)nunits + 1, s)) return TG_ENOMEM;
-        k_unit_starts<<<grid_r(cnt), 256, 0, s>>>(flag.p, pos.p, cnt, ustart.p, nunits);
+        k_unit_starts<<<grid_r(cnt), 256, 0, s>>>(flag.p, pos.p, cnt, ustart.p, nunits); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
         DevBuf<unsigned long long> q;
         if (!q.alloc(1, s)) return TG_ENOMEM;
         TG_TRY_CUDA(cudaMemsetAsync(q.p, 0, 8, s));
+        TG_TRY_CUDA(cudaEventRecord(g_last.ev[0], s));
         const size_t avail = (size_t)smem_optin_r();
         int64_t nbits = g->n_nonisolated;
         if (t.bitmap_bits > 0 && nbits > t.bitmap_bits) nbits = t.bitmap_bits;
@@ -755,19 +797,22 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
         if (grid > nunits) grid = nunits;
         if (grid < 1) grid = 1;
         k_tau<<<(unsigned)grid, 512, smem, s>>>(g->rowptr, g->adj, g->toff, g->edges, ord,
-                                                ustart.p, nunits, L, nbits, q.p, tau.p);
+                                                ustart.p, nunits, L, nbits, q.p, tau.p); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
     }
+    TG_TRY_CUDA(cudaEventRecord(g_last.ev[1], s));
     if (k == 4) {
         if (!theta.alloc((size_t)n * L2, s) || !dsum.alloc((size_t)n * L2, s)) return TG_ENOMEM;
         k_node_aggr<<<grid_r(n * 32), 256, 0, s>>>(g->rowptr, g->adj, g->eid, g->toff, tau.p, n, L,
-                                                   theta.p, dsum.p);
+                                                   theta.p, dsum.p); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
     }
+    TG_TRY_CUDA(cudaEventRecord(g_last.ev[2], s));
     DevBuf<unsigned long long> queue;
     if (!queue.alloc(1, s)) return TG_ENOMEM;
     TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
     ReuseParams p{};
+    p.work = work;
     p.rowptr = g->rowptr;
     p.adj = g->adj;
     p.eid = g->eid;
@@ -811,9 +856,38 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
     p.hmax = hmax;
     const size_t smem = fixed + ((((size_t)((nbits + 31) >> 5)) * 4 + 15) & ~(size_t)15) +
                         (size_t)hmax * 4;
+    int r;
     switch (t.unroll) {
-        case 1: return launch_reuse_u<1>(p, threads, smem, t.grid_limit, s);
-        case 4: return launch_reuse_u<4>(p, threads, smem, t.grid_limit, s);
-        default: return launch_reuse_u<2>(p, threads, smem, t.grid_limit, s);
+        case 1: r = launch_reuse_u<1>(p, threads, smem, t.grid_limit, s); break;
+        case 4: r = launch_reuse_u<4>(p, threads, smem, t.grid_limit, s); break;
+        default: r = launch_reuse_u<2>(p, threads, smem, t.grid_limit, s); break;
     }
+    if (r != TG_OK) return r;
+    TG_TRY_CUDA(cudaEventRecord(g_last.ev[3], s));
+    std::lock_guard<std::mutex> lk(g_last.mu);
+    g_last.edges = (uint64_t)count;
+    g_last.ready = true;
+    return TG_OK;
+}
+
+extern "C" int tg_last_timing(tg_timing *out) {
+    if (!out) return TG_EINVAL;
+    std::lock_guard<std::mutex> lk(g_last.mu);
+    if (!g_last.ready) return TG_ENOTFOUND;
+    TG_TRY_CUDA(cudaEventSynchronize(g_last.ev[3]));
+    float a = 0, b = 0, c = 0;
+    TG_TRY_CUDA(cudaEventElapsedTime(&a, g_last.ev[0], g_last.ev[1]));
+    TG_TRY_CUDA(cudaEventElapsedTime(&b, g_last.ev[1], g_last.ev[2]));
+    TG_TRY_CUDA(cudaEventElapsedTime(&c, g_last.ev[2], g_last.ev[3]));
+    unsigned long long w[4] = {0, 0, 0, 0};
+    TG_TRY_CUDA(cudaMemcpy(w, g_last.work, sizeof(w), cudaMemcpyDeviceToHost));
+    out->tau_ms = a;
+    out->aggregate_ms = b;
+    out->count_ms = c;
+    out->edges = g_last.edges;
+    out->gamma_entries = w[0];
+    out->walked_entries = w[1];
+    out->probe_pairs = w[2];
+    out->t_members = w[3];
+    return TG_OK;
 }
