@@ -34,7 +34,12 @@ if ROOT not in sys.path:
 
 METRIC = "typed 4-node graphlet edges/s"
 UNIT = "edges/s"
-WORKLOAD = "Chung-Lu n=1,000,000 m=8,000,000 gamma=2.1, L=5 Zipf(1.2) types, global k=4"
+WORKLOADS = {
+    "cl1m": "Chung-Lu n=1,000,000 m=8,000,000 gamma=2.1, L=5 Zipf(1.2) types, global k=4",
+    "cl125k": "Chung-Lu n=125,000 m=1,000,000 gamma=2.1, L=5 Zipf(1.2) types, global k=4",
+    "er1000": "Erdos-Renyi G(n=1000, p=0.01), L=3 uniform types, global k=4",
+    "rmat23": "R-MAT scale 23, edge factor 16, (0.57,0.19,0.19,0.05), L=8 uniform types, global k=4",
+}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -44,8 +49,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--oracle-edges", type=int, default=6000,
-                    help="edges in the CPU oracle sample (cpu_baseline)")
+    ap.add_argument("--oracle-edges", type=int, default=20000,
+                    help="edges in the CPU oracle sample (cpu_baseline); 0 skips it")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cl1m",
+                    help="cl1m is the benchmark; the others are profiling and scale cases")
     return ap.parse_args()
 
 
@@ -56,8 +63,14 @@ def dist_env():
     return rank, world, local
 
 
-def workload():
+def workload(name="cl1m"):
     from paper_1901_10026_gb300 import synth
+    if name == "cl125k":
+        return synth.cl_1m(seed=2, n=125_000, m=1_000_000)
+    if name == "er1000":
+        return synth.er_1000(seed=1)
+    if name == "rmat23":
+        return synth.rmat_23()
     return synth.cl_1m()
 
 
@@ -150,10 +163,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     import oracle
-    G = workload()
+    G = workload(args.workload)
     og = oracle.OracleGraph.from_edges(G)
     rng = np.random.default_rng(0)
-    per_step = max(1, args.oracle_edges // 3)
+    per_step = max(1, min(og.M, args.oracle_edges // 6))
     samples = [np.sort(rng.choice(og.M, per_step, replace=False)) for _ in range(args.warmup + args.steps)]
     times = []
     for s, pick in enumerate(samples):
@@ -172,7 +185,7 @@ def run_reference(args, rank, world):
         "warmup": args.warmup, "ms_per_step": mean * 1e3, "higher_is_better": True,
         "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": WORKLOAD, "n": G.n, "M": og.M, "L": G.L, "k": 4,
+        "config": {"workload": WORKLOADS[args.workload], "n": G.n, "M": og.M, "L": G.L, "k": 4,
                    "sample_edges_per_step": per_step},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
@@ -214,7 +227,7 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    G = workload()
+    G = workload(args.workload)
     src_d = torch.from_numpy(G.src).to(dev)
     dst_d = torch.from_numpy(G.dst).to(dev)
     typ_d = torch.from_numpy(G.types).to(dev)
@@ -335,12 +348,12 @@ def main():
     }
 
     if rank == 0:
-        cpu = cpu_baseline(G, args.oracle_edges) if world == 1 else None
+        cpu = cpu_baseline(G, args.oracle_edges) if (world == 1 and args.oracle_edges > 0) else None
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "strong", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": G.n, "M": M, "m_input": G.m, "L": L, "k": k,
+            "config": {"workload": WORKLOADS[args.workload], "n": G.n, "M": M, "m_input": G.m, "L": L, "k": k,
                        "step": "tg_build_csr + tg_count_global from device-resident inputs",
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"edge ranges x{world}" if world > 1 else "single GPU"},
