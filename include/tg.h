@@ -218,6 +218,35 @@ int tg_global_finalize(int32_t L, int32_t k, const uint64_t *sums, uint64_t *out
  */
 int tg_work_model(const tg_graph *g, uint64_t *entries, void *stream);
 
+/* ----------------------------------------------------- no allocation ---- */
+/*
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory when they need a count: code running inside
+ * an arena or pool that owns all device memory, plugins of a host program
+ * that forbids allocation after start-up, or latency-critical loops that
+ * cannot absorb cudaMalloc's implicit synchronisation.
+ *
+ * tg_count_global_noalloc computes the same result as tg_count_global (same
+ * layout, same errors) but the library allocates nothing during the call: no
+ * cudaMalloc, cudaFree, stream-ordered allocation or allocator callback.  Its
+ * scratch (the undivided sums, a work counter, an error word) is one fixed
+ * device array of (TG_NOALLOC_MAX_GLOBAL + 32) * 8 bytes (33 KB) that every
+ * GPU which loads the library keeps until the process exits.
+ *   - tg_global_len(L, k) must not exceed TG_NOALLOC_MAX_GLOBAL (k = 4 with
+ *     L <= 9, or k = 3 with any L); larger requests return TG_EINVAL.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the array.  Calls whose work overlaps on the GPU (other
+ *     streams, other host threads) race on it and give wrong counts; order
+ *     them on one stream or synchronise between them.
+ *   - `out` is caller-owned host or device memory; the graph is an input
+ *     built earlier (tg_build_csr).  Synchronises `stream`.
+ * The counting kernel is the warp-per-edge form of Alg. 1-3 with binary-search
+ * membership, so it suits graphs of moderate size and degree.
+ */
+#define TG_NOALLOC_MAX_GLOBAL 4096
+int tg_count_global_noalloc(const tg_graph *g, int32_t k, uint64_t *out, void *stream);
+
 /* ------------------------------------------------------------ tuning ---- */
 #define TG_KERNEL_AUTO 0
 #define TG_KERNEL_WARP_SEARCH 1 /* warp per edge, binary-search membership      */

@@ -22,7 +22,7 @@ from . import build as _build
 
 __all__ = [
     "TGError", "Graph", "lib", "tg_build_csr", "tg_free_graph", "tg_graph_info", "tg_edge_list",
-    "tg_count_global", "tg_count_per_edge", "tg_count_range", "tg_global_finalize",
+    "tg_count_global", "tg_count_global_noalloc", "tg_count_per_edge", "tg_count_range", "tg_global_finalize",
     "tg_work_model", "tg_slots", "tg_global_len", "tg_config_count", "tg_config_rank",
     "tg_config_unrank", "tg_paper_hash", "tg_slot_config", "tg_strerror", "tg_version",
     "tg_debug_fail_alloc", "tg_set_tune", "tg_get_tune", "tg_launch_count", "tg_last_timing",
@@ -109,6 +109,7 @@ def lib():
             "tg_debug_fail_alloc": (ctypes.c_int, [i64]),
             "tg_set_tune": (ctypes.c_int, [vp]),
             "tg_launch_count": (u64, []),
+            "tg_count_global_noalloc": (ctypes.c_int, [vp, i32, vp, vp]),
             "tg_last_timing": (ctypes.c_int, [vp]),
             "tg_get_tune": (ctypes.c_int, [vp]),
         }
@@ -276,6 +277,14 @@ def tg_count_global(g: Graph, k: int = 4, out=None, stream=None):
     if out is None:
         out = np.zeros(tg_global_len(g.L, k), np.uint64)
     _check(lib().tg_count_global(g.handle, k, _ptr(out), _stream(stream)), "tg_count_global")
+    return out
+
+
+def tg_count_global_noalloc(g: Graph, k: int, out, stream=None):
+    """Global counts into the caller's ``out``; the library allocates nothing
+    (fixed scratch array, see include/tg.h)."""
+    _check(lib().tg_count_global_noalloc(g.handle, k, _ptr(out), _stream(stream)),
+           "tg_count_global_noalloc")
     return out
 
 
