@@ -270,6 +270,114 @@ typedef struct {
 int tg_set_tune(const tg_tune *t); /* NULL restores the defaults */
 int tg_get_tune(tg_tune *t);
 
+/* ---------------------------------------------------------- batches ----- */
+/*
+ * Many graphs in one persistent launch.  Every (graph, edge) pair is a work
+ * item; items are ordered by an estimate of their Alg. 2-3 work (heaviest
+ * first) in one shared queue that the warps of a single persistent launch
+ * drain.  A plan holds the device descriptors, the queue and the scratch; its
+ * runs are replayed from a captured CUDA graph.
+ *
+ * mode: TG_BATCH_GLOBAL        outs[g]: tg_global_len(L_g, k) uint64
+ *       TG_BATCH_PER_EDGE_GRAPHLET / _ORBIT
+ *                              outs[g]: M_g x tg_slots(L_g, k, level) uint64
+ * outs[g] must be device memory (TG_EINVAL otherwise).  The graphs must stay
+ * alive, and the outputs valid, for the life of the plan.
+ */
+#define TG_BATCH_GLOBAL 0
+#define TG_BATCH_PER_EDGE_GRAPHLET 1
+#define TG_BATCH_PER_EDGE_ORBIT 2
+
+typedef struct tg_batch tg_batch;
+
+/* Build a plan.  tune may be NULL; tune->cta_threads (if set) fixes the CTA
+ * size of the persistent kernel.  Synchronises `stream`. */
+int tg_batch_create(int32_t G, tg_graph *const *graphs, int32_t k, int32_t mode,
+                    uint64_t *const *outs, const tg_tune *tune, void *stream, tg_batch **out);
+
+/* One run of the plan (captured into a CUDA graph on first use and replayed
+ * afterwards).  Synchronises `stream`; TG_EINTERNAL if a global sum is not
+ * divisible by |E(H)|. */
+int tg_batch_run(tg_batch *b, void *stream);
+
+/* Autotuner: times the persistent kernel with 4, 8 and 16 warps per CTA, with
+ * and without the cost-ordered queue, keeps the fastest and re-captures the
+ * CUDA graph.  *best_threads (may be NULL) receives the CTA size, negative
+ * when the natural item order won. */
+int tg_batch_tune(tg_batch *b, void *stream, int32_t *best_threads);
+
+int tg_batch_destroy(tg_batch *b);
+
+/* One-shot form: create, autotune when tune == NULL, run, destroy. */
+int tg_count_batch(int32_t G, tg_graph *const *graphs, int32_t k, int32_t mode,
+                   uint64_t *const *outs, const tg_tune *tune, void *stream);
+
+/* ---------------------------------------------------------- serving ----- */
+/*
+ * A serving loop for global-count requests on graphs of different sizes.
+ * A dispatcher thread admits queued requests, in arrival order, whenever the
+ * request's device-memory estimate fits the remaining budget and a slot is
+ * free (a small request may pass a large one that waits for memory); admitted
+ * requests run on `slots` worker threads, each with its own CUDA stream, so
+ * their work overlaps on the GPU; a small admitted request (input pairs <=
+ * batch_edges) takes further small queued requests along, up to batch_max,
+ * and they run as one batched launch (continuous batching).
+ */
+typedef struct tg_server tg_server;
+
+typedef struct {
+    int32_t slots;            /* requests in flight at once (default 4)         */
+    int32_t queue_cap;        /* queued requests before TG_EBUSY (default 4096) */
+    int64_t mem_budget_bytes; /* device bytes admitted requests may use (8 GiB)  */
+    int32_t device;           /* CUDA device of the server                       */
+    int32_t batch_max;        /* most requests in one batched launch (32)        */
+    int64_t batch_edges;      /* input pairs of a request that may be grouped
+                                 (default 20000; 0 disables grouping)            */
+} tg_serve_cfg;
+
+typedef struct {
+    int64_t n, m;             /* nodes, input pairs                              */
+    const int32_t *src, *dst; /* host arrays of m ids (copied by submit)         */
+    const uint8_t *type;      /* host array of n types (copied by submit)        */
+    int32_t L, k;             /* types, graphlet size (3 or 4)                   */
+} tg_request;
+
+typedef struct {
+    int32_t status;           /* TG_OK or the request's error                    */
+    int32_t cuda_error;       /* cudaError_t behind a TG_ECUDA status, else 0    */
+    int64_t len;              /* entries of the global histogram                 */
+    double latency_ms;        /* submit to completion                            */
+} tg_result;
+
+typedef struct {
+    uint64_t completed, failed, queued;
+    double p50_ms, p99_ms, max_ms; /* latency of completed requests              */
+    double graphs_per_s;           /* completed / (last completion - first submit) */
+    int64_t peak_in_flight, peak_bytes;
+    uint64_t batched_launches, grouped_requests;
+} tg_serve_stats_t;
+
+/* NULL cfg uses the defaults.  Returns NULL if the threads cannot start. */
+tg_server *tg_serve_create(const tg_serve_cfg *cfg);
+
+/* Copy the request and queue it.  TG_EINVAL (bad ids/types/sizes),
+ * TG_ENOMEM_ADMIT (its estimate exceeds the whole budget: it can never run),
+ * TG_EBUSY (queue full). */
+int tg_serve_submit(tg_server *sv, const tg_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_ms for the ticket's result (TG_ETIMEDOUT otherwise; the
+ * request stays pending).  On success the histogram (tg_global_len(L, k)
+ * entries) is copied to the host array `out` of out_len entries and the ticket
+ * is released.  TG_ENOTFOUND for unknown or already released tickets. */
+int tg_serve_wait(tg_server *sv, uint64_t ticket, int32_t timeout_ms, uint64_t *out,
+                  int64_t out_len, tg_result *info);
+
+int tg_serve_stats(tg_server *sv, tg_serve_stats_t *stats);
+
+/* Stop accepting work, run what is admitted, refuse what is queued (those
+ * tickets complete with TG_EBUSY), join the threads and free the server. */
+void tg_serve_destroy(tg_server *sv);
+
 /* ------------------------------------------------------- allocation ----- */
 /*
  * Route the library's device allocations through caller functions (for
@@ -285,10 +393,16 @@ int tg_set_allocator(tg_alloc_fn alloc, tg_free_fn free_fn, void *ctx);
 /* Kernels launched by this library since it was loaded. */
 uint64_t tg_launch_count(void);
 
+/* The cudaError_t value of the last CUDA call of this library that failed on
+ * the calling host thread (the cause of its last TG_ECUDA), or 0. */
+int32_t tg_last_cuda_error(void);
+
 /*
- * Timing and work of the last counting call of this process that used the
- * default kernel (CUDA events recorded on that call's stream around each
- * kernel).  Waits for those events.  Returns TG_ENOTFOUND before any call.
+ * Timing and work of the calling host thread's last counting call that used
+ * the default kernel (CUDA events recorded on that call's stream around each
+ * kernel).  Waits for those events.  Returns TG_ENOTFOUND before any such
+ * call on this thread.  Each host thread keeps its own record, so calls made
+ * concurrently from several threads do not mix.
  */
 typedef struct {
     double tau_ms;            /* Alg. 1 typed triangle counts, every edge   */

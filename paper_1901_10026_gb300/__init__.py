@@ -22,11 +22,11 @@ from . import build as _build
 
 __all__ = [
     "TGError", "Graph", "lib", "tg_build_csr", "tg_free_graph", "tg_graph_info", "tg_edge_list",
-    "tg_count_global", "tg_count_global_noalloc", "tg_count_per_edge", "tg_count_range", "tg_global_finalize",
+    "tg_count_global", "tg_count_global_noalloc", "tg_count_per_edge", "Batch", "tg_count_batch", "Server", "tg_count_range", "tg_global_finalize",
     "tg_work_model", "tg_slots", "tg_global_len", "tg_config_count", "tg_config_rank",
     "tg_config_unrank", "tg_paper_hash", "tg_slot_config", "tg_strerror", "tg_version",
     "tg_debug_fail_alloc", "tg_set_tune", "tg_get_tune", "tg_launch_count", "tg_last_timing",
-    "TG_GRAPHLET", "TG_ORBIT",
+    "tg_last_cuda_error", "TG_GRAPHLET", "TG_ORBIT",
 ]
 
 TG_OK = 0
@@ -65,10 +65,39 @@ class TGTiming(ctypes.Structure):
                 ("probe_pairs", ctypes.c_uint64), ("t_members", ctypes.c_uint64)]
 
 
+TG_BATCH_GLOBAL = 0
+TG_BATCH_PER_EDGE_GRAPHLET = 1
+TG_BATCH_PER_EDGE_ORBIT = 2
+
 TG_KERNEL_AUTO = 0
 TG_KERNEL_WARP_SEARCH = 1
 TG_KERNEL_CTA_BITMAP = 2
 TG_KERNEL_REUSE = 3
+
+
+class TGServeCfg(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("queue_cap", ctypes.c_int32),
+                ("mem_budget_bytes", ctypes.c_int64), ("device", ctypes.c_int32),
+                ("batch_max", ctypes.c_int32), ("batch_edges", ctypes.c_int64)]
+
+
+class TGRequest(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("src", ctypes.c_void_p),
+                ("dst", ctypes.c_void_p), ("type", ctypes.c_void_p), ("L", ctypes.c_int32),
+                ("k", ctypes.c_int32)]
+
+
+class TGResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("cuda_error", ctypes.c_int32), ("len", ctypes.c_int64),
+                ("latency_ms", ctypes.c_double)]
+
+
+class TGServeStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("graphs_per_s", ctypes.c_double), ("peak_in_flight", ctypes.c_int64),
+                ("peak_bytes", ctypes.c_int64), ("batched_launches", ctypes.c_uint64),
+                ("grouped_requests", ctypes.c_uint64)]
 
 
 class _Info(ctypes.Structure):
@@ -109,7 +138,18 @@ def lib():
             "tg_debug_fail_alloc": (ctypes.c_int, [i64]),
             "tg_set_tune": (ctypes.c_int, [vp]),
             "tg_launch_count": (u64, []),
+            "tg_last_cuda_error": (i32, []),
             "tg_count_global_noalloc": (ctypes.c_int, [vp, i32, vp, vp]),
+            "tg_batch_create": (ctypes.c_int, [i32, vp, i32, i32, vp, vp, vp, ctypes.POINTER(vp)]),
+            "tg_batch_run": (ctypes.c_int, [vp, vp]),
+            "tg_batch_tune": (ctypes.c_int, [vp, vp, ctypes.POINTER(i32)]),
+            "tg_batch_destroy": (ctypes.c_int, [vp]),
+            "tg_count_batch": (ctypes.c_int, [i32, vp, i32, i32, vp, vp, vp]),
+            "tg_serve_create": (vp, [vp]),
+            "tg_serve_submit": (ctypes.c_int, [vp, vp, ctypes.POINTER(u64)]),
+            "tg_serve_wait": (ctypes.c_int, [vp, u64, i32, vp, i64, vp]),
+            "tg_serve_stats": (ctypes.c_int, [vp, vp]),
+            "tg_serve_destroy": (None, [vp]),
             "tg_last_timing": (ctypes.c_int, [vp]),
             "tg_get_tune": (ctypes.c_int, [vp]),
         }
@@ -154,6 +194,8 @@ def _stream(stream):
 
 def _check(rc: int, what: str):
     if rc != TG_OK:
+        if rc == TG_ECUDA:  # name the CUDA error (recorded per host thread)
+            what = f"{what} (cudaError_t {int(lib().tg_last_cuda_error())})"
         raise TGError(rc, what)
 
 
@@ -288,6 +330,111 @@ def tg_count_global_noalloc(g: Graph, k: int, out, stream=None):
     return out
 
 
+def _handles(graphs, outs):
+    G = len(graphs)
+    if len(outs) != G:
+        raise ValueError("one output per graph")
+    hs = (ctypes.c_void_p * max(G, 1))(*[g.handle.value for g in graphs])
+    ps = (ctypes.c_void_p * max(G, 1))(*[_ptr(o).value for o in outs])
+    return G, hs, ps
+
+
+class Batch:
+    """A batched-count plan over resident graphs (include/tg.h, tg_batch_*).
+
+    ``outs`` are device tensors, one per graph (global histograms or per-edge
+    rows, by ``mode``).  The graphs and outputs must outlive the plan."""
+
+    def __init__(self, graphs, k, mode, outs, cta_threads=0, stream=None):
+        self._graphs, self._outs = list(graphs), list(outs)
+        G, hs, ps = _handles(self._graphs, self._outs)
+        self._keep = (hs, ps)
+        tune = TGTune(0, cta_threads, 0, 0, 0, 0, 0) if cta_threads else None
+        h = ctypes.c_void_p()
+        _check(lib().tg_batch_create(G, hs, k, mode, ps, ctypes.byref(tune) if tune else None,
+                                     _stream(stream), ctypes.byref(h)), "tg_batch_create")
+        self._h = h
+
+    def run(self, stream=None):
+        _check(lib().tg_batch_run(self._h, _stream(stream)), "tg_batch_run")
+
+    def tune(self, stream=None) -> int:
+        best = ctypes.c_int32(0)
+        _check(lib().tg_batch_tune(self._h, _stream(stream), ctypes.byref(best)), "tg_batch_tune")
+        return int(best.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().tg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tg_count_batch(graphs, k, mode, outs, cta_threads=0, stream=None):
+    """One-shot batched count (autotuned unless ``cta_threads`` is given)."""
+    G, hs, ps = _handles(list(graphs), list(outs))
+    tune = TGTune(0, cta_threads, 0, 0, 0, 0, 0) if cta_threads else None
+    _check(lib().tg_count_batch(G, hs, k, mode, ps, ctypes.byref(tune) if tune else None,
+                                _stream(stream)), "tg_count_batch")
+    return outs
+
+
+class Server:
+    """The serving loop (include/tg.h, tg_serve_*)."""
+
+    def __init__(self, slots=4, mem_budget_bytes=8 << 30, queue_cap=4096, device=0, batch_max=32,
+                 batch_edges=20000):
+        self._cfg = TGServeCfg(slots, queue_cap, mem_budget_bytes, device, batch_max, batch_edges)
+        h = lib().tg_serve_create(ctypes.byref(self._cfg))
+        if not h:
+            raise TGError(TG_ENOMEM, "tg_serve_create")
+        self._h = ctypes.c_void_p(h)
+        self._meta = {}
+
+    def submit(self, n, src, dst, types, L, k=4) -> int:
+        src = np.ascontiguousarray(src, dtype=np.int32)
+        dst = np.ascontiguousarray(dst, dtype=np.int32)
+        types = np.ascontiguousarray(types, dtype=np.uint8)
+        req = TGRequest(int(n), int(src.shape[0]), _ptr(src), _ptr(dst), _ptr(types), int(L), int(k))
+        t = ctypes.c_uint64(0)
+        _check(lib().tg_serve_submit(self._h, ctypes.byref(req), ctypes.byref(t)), "tg_serve_submit")
+        self._meta[t.value] = (L, k)
+        return int(t.value)
+
+    def wait(self, ticket, timeout_ms=60000):
+        L, k = self._meta.get(ticket, (16, 4))
+        out = np.zeros(max(1, tg_global_len(L, k)), np.uint64)
+        info = TGResult()
+        rc = lib().tg_serve_wait(self._h, ticket, int(timeout_ms), _ptr(out), out.shape[0],
+                                 ctypes.byref(info))
+        if rc == TG_ECUDA and info.cuda_error:
+            raise TGError(rc, f"tg_serve_wait (cudaError_t {info.cuda_error})")
+        _check(rc, "tg_serve_wait")
+        self._meta.pop(ticket, None)
+        return out[: info.len], info.latency_ms
+
+    def stats(self) -> dict:
+        st = TGServeStats()
+        _check(lib().tg_serve_stats(self._h, ctypes.byref(st)), "tg_serve_stats")
+        return {f: getattr(st, f) for f, _ in TGServeStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().tg_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def tg_count_per_edge(g: Graph, k: int = 4, level: int = TG_GRAPHLET, rows=None, stream=None):
     if rows is None:
         rows = np.zeros((g.M, tg_slots(g.L, k, level)), np.uint64)
@@ -336,6 +483,11 @@ def tg_get_tune() -> dict:
 def tg_launch_count() -> int:
     """Kernels launched by libtg.so so far in this process."""
     return int(lib().tg_launch_count())
+
+
+def tg_last_cuda_error() -> int:
+    """cudaError_t of this thread's last failed CUDA call inside libtg.so (0 if none)."""
+    return int(lib().tg_last_cuda_error())
 
 
 def tg_last_timing() -> dict:

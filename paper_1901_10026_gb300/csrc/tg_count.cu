@@ -907,6 +907,14 @@ void tg_sched_free(tg_graph *g) {
     g->sched = nullptr;
 }
 
+void tg_sched_free_on(tg_graph *g, cudaStream_t s) {
+    if (!g->sched) return;
+    tg_dfree(g->sched->order, 0, s);
+    tg_dfree(g->sched->s, 0, s);
+    delete g->sched;
+    g->sched = nullptr;
+}
+
 // Edge ids [e0, e0 + count) sorted by (j, i); *out owns count entries.
 static int grouped_order(const tg_graph *g, int64_t e0, int64_t count, cudaStream_t s,
                          DevBuf<uint32_t> &out) {
@@ -1001,8 +1009,7 @@ static void fill_params(CountParams &p, const tg_graph *g, int k, int level,
 static int launch_warp(const CountParams &p, cudaStream_t s) {
     const size_t hist_bytes = p.hist_smem ? (((size_t)p.hist_len * 8 + 15) & ~(size_t)15) : 0;
     const size_t smem = hist_bytes + kWarps * warp_smem_bytes(p.P);
-    TG_TRY_CUDA(cudaFuncSetAttribute(k_count_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    TG_TRY(tg_allow_max_smem((const void *)k_count_warp));
     int per_sm = 0;
     TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_warp, kBlock, smem));
     if (per_sm < 1) per_sm = 1;
@@ -1046,8 +1053,7 @@ static bool plan_cta(const tg_graph *g, const CountParams &p, const tg_tune &t, 
 template <int U>
 static int launch_cta_u(const CountParams &p, const CtaParams &cp, int threads, size_t smem,
                         cudaStream_t s) {
-    TG_TRY_CUDA(cudaFuncSetAttribute(k_count_cta<U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    TG_TRY(tg_allow_max_smem((const void *)k_count_cta<U>));
     int per_sm = 0;
     TG_TRY_CUDA(
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_cta<U>, threads, smem));

@@ -347,6 +347,20 @@ extern "C" int tg_free_graph(tg_graph *g) {
     return TG_OK;
 }
 
+int tg_free_graph_on(tg_graph *g, cudaStream_t s) {
+    if (!g) return TG_OK;
+    tg_sched_free_on(g, s);
+    tg_dfree(g->rowptr, 0, s);
+    tg_dfree(g->adj, 0, s);
+    tg_dfree(g->toff, 0, s);
+    tg_dfree(g->ntype, 0, s);
+    tg_dfree(g->edges, 0, s);
+    tg_dfree(g->new2old, 0, s);
+    tg_dfree(g->eid, 0, s);
+    delete g;
+    return TG_OK;
+}
+
 extern "C" int tg_graph_info(const tg_graph *g, tg_info *info) {
     if (!g || !info) return TG_EINVAL;
     info->n = g->n;

@@ -77,10 +77,17 @@ struct DevBuf {
     }
 };
 
+// Records the cudaError_t behind a TG_ECUDA for tg_last_cuda_error (per
+// host thread).
+void tg_note_cuda_error(cudaError_t e);
+
 #define TG_TRY_CUDA(call)                         \
     do {                                          \
         cudaError_t _e = (call);                  \
-        if (_e != cudaSuccess) return TG_ECUDA;   \
+        if (_e != cudaSuccess) {                  \
+            tg_note_cuda_error(_e);               \
+            return TG_ECUDA;                      \
+        }                                         \
     } while (0)
 
 #define TG_TRY(call)                              \
@@ -106,6 +113,12 @@ int tg_bitlen(uint64_t x);  // number of bits needed to represent x (0 -> 0)
 // Counts every kernel this library launches (reported by tg_launch_count).
 void tg_note_launch();
 
+// Lets `func` take the device's opt-in maximum of dynamic shared memory (less
+// its static shared memory).  Every caller writes the same value, so a call on
+// another host thread can never lower the limit between this thread's sizing
+// and its launch; launches are then checked against their own size only.
+int tg_allow_max_smem(const void *func);
+
 // Is p a device pointer (or managed)?  Host pointers, registered or not, -> false.
 bool tg_is_device_ptr(const void *p);
 
@@ -119,6 +132,9 @@ static inline int64_t tg_binom(int64_t a, int64_t b) {
 
 // Free the lazily built schedule of a graph (tg_count.cu).
 void tg_sched_free(tg_graph *g);
+// Stream-ordered frees for a graph used only on stream s (no device sync).
+void tg_sched_free_on(tg_graph *g, cudaStream_t s);
+int tg_free_graph_on(tg_graph *g, cudaStream_t s);
 
 // Counts through Alg. 1's typed triangle counts (tg_reuse.cu).  full_order is
 // the grouped order of all M edges; order[0..count) the edges to count.

@@ -271,8 +271,7 @@ extern "C" int tg_count_global_noalloc(const tg_graph *g, int32_t k, uint64_t *o
     if (g->M > 0) {
         const size_t wbytes = ((size_t)CN * p.P * 4 + 3 * 16 * 4 + 15) & ~(size_t)15;
         const size_t smem = kNaWarps * wbytes;
-        TG_TRY_CUDA(cudaFuncSetAttribute(k_noalloc_count,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        TG_TRY(tg_allow_max_smem((const void *)k_noalloc_count));
         int dev = 0, sms = 1, per_sm = 1;
         TG_TRY_CUDA(cudaGetDevice(&dev));
         TG_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

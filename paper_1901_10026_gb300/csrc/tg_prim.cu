@@ -14,7 +14,25 @@ static std::atomic<uint64_t> g_launches{0};
 
 void tg_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+static thread_local int32_t g_cuda_error = 0;
+
+void tg_note_cuda_error(cudaError_t e) { g_cuda_error = (int32_t)e; }
+
+extern "C" int32_t tg_last_cuda_error(void) { return g_cuda_error; }
+
 extern "C" uint64_t tg_launch_count(void) { return g_launches.load(); }
+
+int tg_allow_max_smem(const void *func) {
+    int dev = 0, optin = 0;
+    TG_TRY_CUDA(cudaGetDevice(&dev));
+    TG_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa{};
+    TG_TRY_CUDA(cudaFuncGetAttributes(&fa, func));
+    const int v = optin - (int)fa.sharedSizeBytes;
+    if (v <= 0) return TG_EINVAL;
+    TG_TRY_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    return TG_OK;
+}
 
 extern "C" int tg_set_allocator(tg_alloc_fn alloc, tg_free_fn free_fn, void *ctx) {
     if ((alloc == nullptr) != (free_fn == nullptr)) return TG_EINVAL;

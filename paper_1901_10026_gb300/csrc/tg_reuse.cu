@@ -685,18 +685,24 @@ __global__ void __launch_bounds__(1024, 1) k_count_reuse(ReuseParams p) {
     }
 }
 
-// Events and work counters of the last call (see tg_last_timing).
+// Events and work counters of the calling thread's last call (see
+// tg_last_timing).  One set per host thread, so counts run concurrently from
+// several threads (the serving loop's workers) neither reset nor mix each
+// other's counters.
 struct LastTiming {
-    std::mutex mu;
     bool ready = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     unsigned long long *work = nullptr;  // device, 4 counters
     uint64_t edges = 0;
+    ~LastTiming() {
+        for (auto &e : ev)
+            if (e) (void)cudaEventDestroy(e);
+        if (work) (void)cudaFree(work);
+    }
 };
-LastTiming g_last;
+thread_local LastTiming g_last;
 
 int timing_begin(cudaStream_t s, unsigned long long **work) {
-    std::lock_guard<std::mutex> lk(g_last.mu);
     if (!g_last.ev[0]) {
         for (auto &e : g_last.ev) TG_TRY_CUDA(cudaEventCreate(&e));
         TG_TRY_CUDA(cudaMalloc(&g_last.work, 4 * sizeof(unsigned long long)));
@@ -731,8 +737,7 @@ inline unsigned grid_r(int64_t n, int threads = 256) {
 template <int U>
 int launch_reuse_u(const ReuseParams &p, int threads, size_t smem, int grid_limit,
                    cudaStream_t s) {
-    TG_TRY_CUDA(cudaFuncSetAttribute(k_count_reuse<U>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TG_TRY(tg_allow_max_smem((const void *)k_count_reuse<U>));
     int per_sm = 0;
     TG_TRY_CUDA(
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_reuse<U>, threads, smem));
@@ -788,8 +793,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
         const int64_t maxb = (int64_t)((avail - 64) / 16) * 128;
         if (nbits > maxb) nbits = maxb;
         const size_t smem = ((((size_t)((nbits + 31) >> 5)) * 4 + 15) & ~(size_t)15) + 16;
-        TG_TRY_CUDA(cudaFuncSetAttribute(k_tau, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
+        TG_TRY(tg_allow_max_smem((const void *)k_tau));
         int per_sm = 0;
         TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tau, 512, smem));
         if (per_sm < 1) per_sm = 1;
@@ -864,7 +868,6 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
     }
     if (r != TG_OK) return r;
     TG_TRY_CUDA(cudaEventRecord(g_last.ev[3], s));
-    std::lock_guard<std::mutex> lk(g_last.mu);
     g_last.edges = (uint64_t)count;
     g_last.ready = true;
     return TG_OK;
@@ -872,7 +875,6 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
 
 extern "C" int tg_last_timing(tg_timing *out) {
     if (!out) return TG_EINVAL;
-    std::lock_guard<std::mutex> lk(g_last.mu);
     if (!g_last.ready) return TG_ENOTFOUND;
     TG_TRY_CUDA(cudaEventSynchronize(g_last.ev[3]));
     float a = 0, b = 0, c = 0;
