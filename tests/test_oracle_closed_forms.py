@@ -26,16 +26,28 @@ def _graph(n, edges, types, L):
     return synth.TypedEdgeList(n, e[:, 0].copy(), e[:, 1].copy(), np.array(types, np.uint8), L)
 
 
-def _global(oracle_mod, G):
+@pytest.fixture(params=["o1", "o2"])
+def which(request):
+    """The global counts under test: the paper-method oracle (o1) or the
+    independent non-induced-inversion oracle (o2).  Per-edge checks use o1."""
+    return request.param
+
+
+def _global(oracle_mod, G, which="o1"):
     og = oracle_mod.OracleGraph.from_edges(G)
-    return layout.decode_global(og.global_counts(k=4), G.L, 4), og
+    if which == "o2":
+        from oracle import o2
+        vec = o2.global_counts(G.n, G.src, G.dst, G.types, G.L, 4)
+    else:
+        vec = og.global_counts(k=4)
+    return layout.decode_global(vec, G.L, 4), og
 
 
 @pytest.mark.parametrize("n,L,seed", [(4, 1, 0), (6, 2, 1), (8, 3, 2), (9, 4, 3), (7, 3, 4)])
-def test_typed_clique(oracle_mod, n, L, seed):
+def test_typed_clique(oracle_mod, which, n, L, seed):
     types = synth.uniform_types(n, L, synth.rng(910, seed))
     G = _graph(n, list(itertools.combinations(range(n), 2)), types, L)
-    got, og = _global(oracle_mod, G)
+    got, og = _global(oracle_mod, G, which)
     cnt = Counter(int(t) for t in types)
     want = {}
     for size, h in ((2, 0), (3, 2), (4, 8)):
@@ -64,10 +76,10 @@ def test_typed_clique(oracle_mod, n, L, seed):
 
 
 @pytest.mark.parametrize("s,L,seed", [(3, 1, 0), (6, 2, 1), (9, 3, 2), (12, 4, 3)])
-def test_typed_star(oracle_mod, s, L, seed):
+def test_typed_star(oracle_mod, which, s, L, seed):
     types = synth.uniform_types(s + 1, L, synth.rng(911, seed))
     G = _graph(s + 1, [(0, x) for x in range(1, s + 1)], types, L)
-    got, og = _global(oracle_mod, G)
+    got, og = _global(oracle_mod, G, which)
     c0 = int(types[0])
     leaves = Counter(int(t) for t in types[1:])
     want = {}
@@ -111,10 +123,10 @@ def _windows(types, n, size, cyclic):
 
 
 @pytest.mark.parametrize("n,L,seed", [(5, 2, 0), (7, 3, 1), (12, 4, 2), (30, 3, 3)])
-def test_typed_cycle(oracle_mod, n, L, seed):
+def test_typed_cycle(oracle_mod, which, n, L, seed):
     types = synth.uniform_types(n, L, synth.rng(912, seed))
     G = _graph(n, [(x, (x + 1) % n) for x in range(n)], types, L)
-    got, og = _global(oracle_mod, G)
+    got, og = _global(oracle_mod, G, which)
     want = {}
     for size, h in ((2, 0), (3, 1), (4, 3)):
         for m, c in _windows(types, n, size, True).items():
@@ -130,18 +142,18 @@ def test_typed_cycle(oracle_mod, n, L, seed):
         assert all(o in (1, 3, 4) for (o, _) in d)
 
 
-def test_four_cycle(oracle_mod):
+def test_four_cycle(oracle_mod, which):
     types = [0, 1, 0, 1]
     G = _graph(4, [(0, 1), (1, 2), (2, 3), (3, 0)], types, 2)
-    got, _ = _global(oracle_mod, G)
+    got, _ = _global(oracle_mod, G, which)
     assert got == {(0, (0, 1)): 4, (1, (0, 0, 1)): 2, (1, (0, 1, 1)): 2, (5, (0, 0, 1, 1)): 1}
 
 
 @pytest.mark.parametrize("n,L,seed", [(4, 1, 0), (9, 2, 1), (25, 3, 2)])
-def test_typed_path(oracle_mod, n, L, seed):
+def test_typed_path(oracle_mod, which, n, L, seed):
     types = synth.uniform_types(n, L, synth.rng(913, seed))
     G = _graph(n, [(x, x + 1) for x in range(n - 1)], types, L)
-    got, _ = _global(oracle_mod, G)
+    got, _ = _global(oracle_mod, G, which)
     want = {}
     for size, h in ((2, 0), (3, 1), (4, 3)):
         for m, c in _windows(types, n, size, False).items():
@@ -150,12 +162,12 @@ def test_typed_path(oracle_mod, n, L, seed):
 
 
 @pytest.mark.parametrize("a,b,L,seed", [(2, 2, 1, 0), (3, 4, 2, 1), (5, 6, 3, 2), (4, 7, 4, 3)])
-def test_typed_complete_bipartite(oracle_mod, a, b, L, seed):
+def test_typed_complete_bipartite(oracle_mod, which, a, b, L, seed):
     types = synth.uniform_types(a + b, L, synth.rng(914, seed))
     A = Counter(int(t) for t in types[:a])
     B = Counter(int(t) for t in types[a:])
     G = _graph(a + b, [(x, a + y) for x in range(a) for y in range(b)], types, L)
-    got, _ = _global(oracle_mod, G)
+    got, _ = _global(oracle_mod, G, which)
     want = Counter()
     # edges: one node per side
     for ma in layout.multisets(L, 1):
