@@ -252,6 +252,8 @@ int tg_count_global_noalloc(const tg_graph *g, int32_t k, uint64_t *out, void *s
 #define TG_KERNEL_WARP_SEARCH 1 /* warp per edge, binary-search membership      */
 #define TG_KERNEL_CTA_BITMAP 2  /* CTA per edge, shared-memory bitmap marks     */
 #define TG_KERNEL_REUSE 3       /* Alg. 1 triangle counts reused for Alg. 2-3   */
+#define TG_KERNEL_CYCLES 4      /* REUSE's identities, with 4-cycles and 4-cliques
+                                   enumerated once over the whole graph (default) */
 
 /*
  * Launch configuration of the counting kernels (process-wide).  Zero fields
@@ -260,8 +262,12 @@ int tg_count_global_noalloc(const tg_graph *g, int32_t k, uint64_t *out, void *s
 typedef struct {
     int32_t kernel;      /* TG_KERNEL_*                                     */
     int32_t cta_threads; /* threads per CTA of the bitmap kernel (32..1024) */
-    int32_t unroll;      /* 1, 2 or 4 adjacency windows in flight per warp  */
-    int32_t hash_slots;  /* slots of the per-edge Gamma_i hash (power of 2) */
+    int32_t unroll;      /* 1, 2 or 4 adjacency windows in flight per warp;
+                            CYCLES kernel: 4-cycle anchors split over the
+                            grid: 1 none, 4 all, 2 (default) the costly ones */
+    int32_t hash_slots;  /* slots of the per-edge Gamma_i hash (power of 2);
+                            CYCLES kernel: cap on the 4-clique candidates
+                            staged per warp                                 */
     int64_t bitmap_bits; /* cap on the node ids covered by the bitmap       */
     int32_t grid_limit;  /* cap on the CTAs of one counting launch          */
     int32_t reserved;
@@ -399,21 +405,27 @@ int32_t tg_last_cuda_error(void);
 
 /*
  * Timing and work of the calling host thread's last counting call that used
- * the default kernel (CUDA events recorded on that call's stream around each
- * kernel).  Waits for those events.  Returns TG_ENOTFOUND before any such
- * call on this thread.  Each host thread keeps its own record, so calls made
- * concurrently from several threads do not mix.
+ * the REUSE or CYCLES kernel (CUDA events recorded on that call's stream
+ * around each phase).  Waits for those events.  Returns TG_ENOTFOUND before
+ * any such call on this thread.  Each host thread keeps its own record, so
+ * calls made concurrently from several threads do not mix.  Phases a kernel
+ * does not have read 0.
  */
 typedef struct {
     double tau_ms;            /* Alg. 1 typed triangle counts, every edge   */
     double aggregate_ms;      /* per-node sums of tau and typed degrees     */
-    double count_ms;          /* per-edge enumeration, identities, output   */
+    double count_ms;          /* per-edge pass: identities, closed forms,
+                                 output                                      */
     uint64_t edges;           /* edges counted                               */
-    uint64_t gamma_entries;   /* entries of Gamma_i read by the count kernel */
-    uint64_t walked_entries;  /* entries of S_i / T lists walked (4-cycles,
-                                 4-cliques)                                  */
-    uint64_t probe_pairs;     /* (T member, T member) adjacency probes       */
+    uint64_t gamma_entries;   /* entries of Gamma_i read by the per-edge pass */
+    uint64_t walked_entries;  /* REUSE: entries of S_i / T lists walked      */
+    uint64_t probe_pairs;     /* REUSE: (T member, T member) adjacency probes */
     uint64_t t_members;       /* T members whose tau rows were read          */
+    double cycles_ms;         /* CYCLES: 4-cycle enumeration                 */
+    double cliques_ms;        /* CYCLES: 4-clique enumeration                */
+    uint64_t wedges;          /* CYCLES: degree-ordered wedges (per pass)    */
+    uint64_t clique_tests;    /* CYCLES: candidate tests of the clique search */
+    uint64_t cliques;         /* CYCLES: 4-cliques found                     */
 } tg_timing;
 
 int tg_last_timing(tg_timing *out);

@@ -62,7 +62,10 @@ class TGTiming(ctypes.Structure):
     _fields_ = [("tau_ms", ctypes.c_double), ("aggregate_ms", ctypes.c_double),
                 ("count_ms", ctypes.c_double), ("edges", ctypes.c_uint64),
                 ("gamma_entries", ctypes.c_uint64), ("walked_entries", ctypes.c_uint64),
-                ("probe_pairs", ctypes.c_uint64), ("t_members", ctypes.c_uint64)]
+                ("probe_pairs", ctypes.c_uint64), ("t_members", ctypes.c_uint64),
+                ("cycles_ms", ctypes.c_double), ("cliques_ms", ctypes.c_double),
+                ("wedges", ctypes.c_uint64), ("clique_tests", ctypes.c_uint64),
+                ("cliques", ctypes.c_uint64)]
 
 
 TG_BATCH_GLOBAL = 0
@@ -73,6 +76,7 @@ TG_KERNEL_AUTO = 0
 TG_KERNEL_WARP_SEARCH = 1
 TG_KERNEL_CTA_BITMAP = 2
 TG_KERNEL_REUSE = 3
+TG_KERNEL_CYCLES = 4
 
 
 class TGServeCfg(ctypes.Structure):

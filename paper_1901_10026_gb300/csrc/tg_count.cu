@@ -865,7 +865,7 @@ static tg_tune tune_now() {
 extern "C" int tg_set_tune(const tg_tune *t) {
     tg_tune d = {TG_KERNEL_AUTO, 1024, 2, 4096, 0, 0, 0};
     if (t) {
-        if (t->kernel < 0 || t->kernel > TG_KERNEL_REUSE) return TG_EINVAL;
+        if (t->kernel < 0 || t->kernel > TG_KERNEL_CYCLES) return TG_EINVAL;
         if (t->cta_threads && (t->cta_threads < 32 || t->cta_threads > 1024 || t->cta_threads % 32))
             return TG_EINVAL;
         if (t->unroll && t->unroll != 1 && t->unroll != 2 && t->unroll != 4) return TG_EINVAL;
@@ -1075,7 +1075,9 @@ static int launch_count(const tg_graph *g, int k, int level, const uint32_t *ful
     if (count <= 0) return TG_OK;
     {
         const tg_tune t0 = tune_now();
-        if ((t0.kernel == TG_KERNEL_AUTO || t0.kernel == TG_KERNEL_REUSE) && order)
+        if ((t0.kernel == TG_KERNEL_AUTO || t0.kernel == TG_KERNEL_REUSE ||
+             t0.kernel == TG_KERNEL_CYCLES) &&
+            order)
             return tg_reuse_count(g, k, level, full_order, order, count, rows, width, hist, t0, s);
     }
     DevBuf<unsigned long long> queue;

@@ -1,0 +1,1313 @@
+// Per-edge counts of Alg. 2-3 from two whole-graph enumerations.
+//
+// The identities in tg_reuse.cu express every enumerated orbit of Alg. 2-3
+// through Alg. 1's typed triangle counts tau, per-node sums of tau and of the
+// typed degrees, sums over the triangle nodes T_ij, and two more per-edge
+// quantities that the paper obtains by walking the neighbour lists of
+// S_i u S_j u T_ij:
+//   C4_ij[a][b] = ordered pairs (x in Gamma_i^a \ {j}, w in Gamma_j^b \ {i})
+//                 with x ~ w, i.e. the non-induced 4-cycles i-j-w-x through
+//                 the edge; the 4-cycle term of the identities is
+//                 S6 = C4 - B + [b = phi_i] |T^a|
+//                 (the x in T part of C4 is sum over y in T^a of tau_jy[b],
+//                 less i itself);
+//   Q_ij[a][b]  = ordered adjacent pairs (y in T^a, z in T^b), i.e. the
+//                 4-cliques through the edge.
+// Here both are accumulated per edge from enumerations of the whole graph in
+// degree order (a node ranks higher when its new id is smaller):
+//   4-cycles (k_c4): each non-induced 4-cycle a-u-b-u' is met once, at its
+//     highest-ranked node a, as two wedges a-u-b and a-u'-b whose other nodes
+//     rank below a.  Per anchor a, pass 1 counts the middles u of the wedges
+//     ending at each b by type (c_t(b)); pass 2 adds, for every wedge, the
+//     cycles it closes with the other middles to its two edges; pass 3 clears
+//     the counters.
+//   4-cliques (k_k4): each 4-clique x0 < v < w < x (by rank) is met once from
+//     its lowest node along "up" lists (neighbours of higher rank) and adds one
+//     to each of its six edges, keyed by the unordered types of the two nodes
+//     off the edge.
+// The enumeration work is the number of degree-ordered wedges plus the
+// 4-clique search, instead of sum over w in S_i u S_j u T_ij of d_w per edge.
+// The per-edge pass (k_cyc_edge) then needs only Gamma_i n Gamma_j (the T
+// sums) and O(L^2) identity and closed-form arithmetic.
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "tg_device.cuh"
+
+using namespace tgd;
+
+namespace {
+
+// Inclusive block scan of a packed (count << 52 | length) word; returns the
+// inclusive value of this thread and leaves the block total in wsum[32].
+__device__ __forceinline__ uint64_t block_scan_packed(uint64_t v, uint64_t *wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+    uint64_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t y = lane < W ? wsum[lane] : 0ull;
+        const uint64_t y0 = y;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t z = __shfl_up_sync(kFull, y, o);
+            if (lane >= o) y += z;
+        }
+        if (lane < W) wsum[lane] = y - y0;
+        if (lane == W - 1) wsum[32] = y;
+    }
+    __syncthreads();
+    return incl + wsum[warp];
+}
+
+constexpr uint64_t kLenMask = ((uint64_t)1 << 41) - 1;
+
+// ------------------------------------------------------------ 4-cycles ----
+struct C4Params {
+    const int64_t *rowptr;
+    const uint32_t *adj;
+    const uint32_t *eid;
+    const uint8_t *ntype;
+    int64_t n;
+    int32_t L;
+    int32_t tile;              // members staged per tile (<= blockDim.x)
+    int32_t acc_l2;            // L * L in per-edge mode, 0 in global mode
+    uint32_t *scratch;         // counter slots of n * L, zero on entry and on exit
+    int64_t slot_words;
+    unsigned long long *queue;
+    unsigned long long *c4e;   // per-edge mode: M * L * L, [type next to i][type next to j]
+    unsigned long long *g4;    // global mode: C(L+3,4) sums over wedges of the cycles each
+                               // closes, by type multiset (twice the non-induced 4-cycles)
+    int64_t n4;
+    const uint8_t *split;      // one-CTA kernel: anchors marked here are skipped
+    const int4 *units;         // split kernel: (slot, anchor, first list position, 0)
+    int64_t n_units;
+    int32_t phase;             // split kernel: the pass of this launch
+    unsigned long long *work;  // [4]: wedges
+};
+
+constexpr int kC4Threads = 256;
+
+struct C4Smem {
+    int64_t *m_end, *m_org;
+    uint64_t *wsum;
+    unsigned long long *acc;
+    uint32_t *m_u, *m_e;
+    unsigned long long *s_item, *h4;
+};
+
+__device__ __forceinline__ C4Smem c4_smem(unsigned char *smem, int TM, int acc_l2) {
+    C4Smem m;
+    m.m_end = reinterpret_cast<int64_t *>(smem);
+    m.m_org = m.m_end + TM;
+    m.wsum = reinterpret_cast<uint64_t *>(m.m_org + TM);
+    m.acc = reinterpret_cast<unsigned long long *>(m.wsum + 34);
+    m.m_u = reinterpret_cast<uint32_t *>(m.acc + (size_t)TM * acc_l2);
+    m.m_e = m.m_u + TM;
+    m.s_item = reinterpret_cast<unsigned long long *>(m.m_e + TM + (TM & 1));
+    m.h4 = m.s_item + 2;  // global mode: n4 entries
+    return m;
+}
+
+// One pass over one tile of anchor a's list: the members u (neighbours ranked
+// below a) of the tile and, for each, the entries b of u's list ranked below
+// a.  Pass 0 counts the middles per (b, type), pass 1 adds the closed cycles
+// (per edge, or by type multiset in global mode), pass 2 clears the counters.
+// Called by every thread of the CTA (it holds barriers).
+__device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta, int64_t ba,
+                        int da, int tile, int phase, uint32_t *cnt, unsigned long long &wk) {
+    const int tid = threadIdx.x;
+    const int L = p.L, L2 = L * L, TM = p.tile;
+    const bool global = p.g4 != nullptr;
+    const int x = tile + tid;
+    bool mem = false;
+    uint32_t wu = 0;
+    int64_t bu = 0;
+    int du = 0;
+    if (tid < TM && x < da) {
+        wu = __ldg(p.adj + ba + x);
+        const uint32_t u = wu & TG_IDMASK;
+        if (u > a) {
+            bu = p.rowptr[u];
+            du = (int)(p.rowptr[u + 1] - bu);
+            mem = du > 1;
+        }
+    }
+    const uint64_t incl = block_scan_packed(((uint64_t)mem << 52) | (uint64_t)(mem ? du : 0), sm.wsum);
+    const uint64_t tot = sm.wsum[32];
+    const int nmem = (int)(tot >> 52);
+    const int64_t total = (int64_t)(tot & kLenMask);
+    if (mem) {
+        const int r = (int)((incl >> 52) - 1);
+        const int64_t end = (int64_t)(incl & kLenMask);
+        sm.m_end[r] = end;
+        sm.m_org[r] = bu - (end - du);
+        sm.m_u[r] = wu;
+        sm.m_e[r] = __ldg(p.eid + ba + x);
+    }
+    if (phase == 1 && !global)
+        for (int q = tid; q < nmem * L2; q += blockDim.x) sm.acc[q] = 0ull;
+    __syncthreads();
+    for (int64_t base = 0; base < total; base += blockDim.x) {
+        const int64_t pos = base + tid;
+        if (pos >= total) continue;
+        int lo = 0, hi = nmem - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (sm.m_end[mid] > pos)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        const int64_t at = sm.m_org[lo] + pos;
+        const uint32_t wb = __ldg(p.adj + at);
+        const uint32_t b = wb & TG_IDMASK;
+        if (b <= a) continue;  // b must rank below a (and differ from it)
+        const uint32_t wmu = sm.m_u[lo];
+        const int tu = (int)(wmu >> TG_TSHIFT);
+        uint32_t *cb = cnt + (int64_t)b * L;
+        if (phase == 0) {
+            atomicAdd(cb + tu, 1u);
+            ++wk;
+            continue;
+        }
+        if (phase == 2) {
+            cb[tu] = 0u;
+            continue;
+        }
+        uint32_t c[TG_MAX_TYPES];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int t = 0; t < TG_MAX_TYPES; ++t) {
+            c[t] = t < L ? __ldcg(cb + t) : 0u;
+            sum += c[t];
+        }
+        if (sum < 2) continue;  // no other middle: no cycle
+        const int tb = (int)(wb >> TG_TSHIFT);
+        if (global) {
+            // cycles a-u-b-u' by the multiset {a, b, u, u'}
+            int s0 = ta, s1 = tb, s2 = tu;
+            sort2(s0, s1);
+            sort2(s1, s2);
+            sort2(s0, s1);
+#pragma unroll
+            for (int t = 0; t < TG_MAX_TYPES; ++t) {
+                if (t < L) {
+                    const uint32_t v = c[t] - (t == tu ? 1u : 0u);
+                    if (v) {
+                        int q0 = s0, q1 = s1, q2 = s2, q3 = t;
+                        sort2(q2, q3);
+                        sort2(q1, q2);
+                        sort2(q0, q1);
+                        atomicAdd(sm.h4 + colex4(q0, q1, q2, q3), (unsigned long long)v);
+                    }
+                }
+            }
+            continue;
+        }
+        const uint32_t u = wmu & TG_IDMASK;
+        unsigned long long *row_ub = p.c4e + (int64_t)__ldg(p.eid + at) * L2;
+        unsigned long long *row_au = sm.acc + (int64_t)lo * L2 + tb * L;
+#pragma unroll
+        for (int t = 0; t < TG_MAX_TYPES; ++t) {
+            if (t < L) {
+                const uint32_t v = c[t] - (t == tu ? 1u : 0u);
+                if (v) {
+                    // edge (u, b): u's cycle neighbour a, b's is u' (type t);
+                    // the row is keyed from its larger-id end
+                    atomicAdd(row_ub + (u > b ? ta * L + t : t * L + ta), (unsigned long long)v);
+                    // edge (a, u): u (the larger id) sees b, a sees u'
+                    atomicAdd(row_au + t, (unsigned long long)v);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (phase == 1 && !global) {
+        for (int q = tid; q < nmem * L2; q += blockDim.x) {
+            const unsigned long long v = sm.acc[q];
+            if (v) atomicAdd(p.c4e + (int64_t)sm.m_e[q / L2] * L2 + (q % L2), v);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void c4_finish(const C4Params &p, const C4Smem &sm,
+                                          unsigned long long wk) {
+    if (p.g4) {
+        __syncthreads();
+        for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x)
+            if (sm.h4[q]) atomicAdd(p.g4 + q, sm.h4[q]);
+    }
+    if (p.work && wk) atomicAdd(p.work + 4, wk);
+}
+
+// Anchors not marked in p.split: one CTA per anchor, the three passes in
+// turn over its own counter slot.
+__global__ void __launch_bounds__(kC4Threads) k_c4(C4Params p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const C4Smem sm = c4_smem(smem, p.tile, p.acc_l2);
+    const int tid = threadIdx.x;
+    if (p.g4)
+        for (int64_t q = tid; q < p.n4; q += blockDim.x) sm.h4[q] = 0ull;
+    uint32_t *cnt = p.scratch + (int64_t)blockIdx.x * p.slot_words;
+    unsigned long long wk = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) *sm.s_item = atomicAdd(p.queue, 1ull);
+        __syncthreads();
+        const unsigned long long item = *sm.s_item;
+        if (item >= (unsigned long long)p.n) break;
+        const uint32_t a = (uint32_t)item;
+        if (p.split[a]) continue;
+        const int64_t ba = p.rowptr[a];
+        const int da = (int)(p.rowptr[a + 1] - ba);
+        if (da < 2) continue;  // a cycle through a needs two of its neighbours
+        const int ta = p.ntype[a];
+        for (int phase = 0; phase < 3; ++phase)
+            for (int tile = 0; tile < da; tile += p.tile)
+                c4_tile(p, sm, a, ta, ba, da, tile, phase, cnt, wk);
+    }
+    c4_finish(p, sm, wk);
+}
+
+// Marked (costly) anchors: their tiles are units spread over the whole grid,
+// each anchor on a counter slot of its own; one launch per pass, so a pass
+// sees every count of the pass before it.
+__global__ void __launch_bounds__(kC4Threads) k_c4_split(C4Params p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const C4Smem sm = c4_smem(smem, p.tile, p.acc_l2);
+    const int tid = threadIdx.x;
+    if (p.g4)
+        for (int64_t q = tid; q < p.n4; q += blockDim.x) sm.h4[q] = 0ull;
+    unsigned long long wk = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) *sm.s_item = atomicAdd(p.queue, 1ull);
+        __syncthreads();
+        const unsigned long long item = *sm.s_item;
+        if (item >= (unsigned long long)p.n_units) break;
+        const int4 un = p.units[item];
+        const uint32_t a = (uint32_t)un.y;
+        const int64_t ba = p.rowptr[a];
+        const int da = (int)(p.rowptr[a + 1] - ba);
+        c4_tile(p, sm, a, p.ntype[a], ba, da, un.z, p.phase,
+                p.scratch + (int64_t)un.x * p.slot_words, wk);
+    }
+    c4_finish(p, sm, wk);
+}
+
+// Walk cost of each anchor (sum of d_u over its neighbours u ranked below it)
+// and the total.  One warp per node.
+__global__ void k_c4_cost(const int64_t *rowptr, const uint32_t *adj, int64_t n,
+                          unsigned long long *cost, unsigned long long *total) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long mine = 0;
+    for (int64_t a = wid; a < n; a += nw) {
+        const int64_t b = rowptr[a];
+        const int d = (int)(rowptr[a + 1] - b);
+        unsigned long long c = 0;
+        for (int x = lane; x < d; x += 32) {
+            const uint32_t u = __ldg(adj + b + x) & TG_IDMASK;
+            if ((int64_t)u > a) c += (unsigned long long)(rowptr[u + 1] - rowptr[u]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
+        if (lane == 0) cost[a] = d >= 2 ? c : 0ull;
+        mine += c;
+    }
+    if (lane == 0 && mine) atomicAdd(total, mine);
+}
+
+// split[a] = cost[a] > thr; flag (as uint32) for the compaction
+__global__ void k_c4_mark(const unsigned long long *cost, int64_t n, unsigned long long thr,
+                          uint8_t *split, uint32_t *flag) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x) {
+        const bool h = cost[a] > thr;
+        split[a] = h ? 1 : 0;
+        flag[a] = h ? 1u : 0u;
+    }
+}
+
+__global__ void k_c4_compact(const uint32_t *flag, const uint32_t *pos, int64_t n,
+                             uint32_t *list) {
+    for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
+         a += (int64_t)gridDim.x * blockDim.x)
+        if (flag[a]) list[pos[a]] = (uint32_t)a;
+}
+
+// ------------------------------------------------------------ up lists ----
+// Up list of v: its neighbours of higher rank (smaller new id), kept with
+// their typed offsets and edge ids.  In a (type, id)-sorted list they are a
+// prefix of every typed range.  One warp per node; lane t < L finds the end
+// of the prefix of type t.
+__global__ void k_up_count(const int64_t *rowptr, const uint32_t *adj, const int32_t *toff,
+                           int64_t n, int32_t L, int32_t *utoff, int64_t *utot) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = wid; v < n; v += nw) {
+        const int64_t b = rowptr[v];
+        const int32_t *to = toff + v * (L + 1);
+        int c = 0;
+        if (lane < L) {
+            int lo = __ldg(to + lane), hi = __ldg(to + lane + 1);
+            const int start = lo;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((int64_t)(__ldg(adj + b + mid) & TG_IDMASK) < v)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            c = lo - start;
+        }
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane < L) utoff[v * (L + 1) + lane + 1] = incl;
+        if (lane == 0) utoff[v * (L + 1)] = 0;
+        if (lane == L - 1) utot[v] = incl;
+    }
+}
+
+__global__ void k_up_fill(const int64_t *rowptr, const uint32_t *adj, const uint32_t *eid,
+                          const int32_t *toff, const int32_t *utoff, const int64_t *uoff,
+                          int64_t n, int32_t L, uint32_t *uadj, uint32_t *ueid) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = wid; v < n; v += nw) {
+        const int64_t b = rowptr[v], ub = uoff[v];
+        const int32_t *to = toff + v * (L + 1);
+        const int32_t *uto = utoff + v * (L + 1);
+        for (int t = 0; t < L; ++t) {
+            const int src = __ldg(to + t), dst = __ldg(uto + t);
+            const int c = __ldg(uto + t + 1) - dst;
+            for (int x = lane; x < c; x += 32) {
+                uadj[ub + dst + x] = __ldg(adj + b + src + x);
+                ueid[ub + dst + x] = __ldg(eid + b + src + x);
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------- 4-cliques ----
+struct K4Params {
+    const int64_t *uoff;       // up lists (see k_up_count)
+    const uint32_t *uadj;
+    const uint32_t *ueid;
+    const int32_t *utoff;
+    const uint8_t *ntype;
+    int64_t n;
+    int32_t L, P;
+    int32_t cap;               // W entries per warp in shared memory
+    unsigned long long *queue;
+    unsigned long long *k4e;   // per-edge mode: M * P, 4-cliques by the types of the two
+                               // other nodes
+    unsigned long long *g4;    // global mode: C(L+3,4) 4-clique counts by type multiset
+    int64_t n4;
+    unsigned long long *work;  // [5]: candidate tests, [6]: 4-cliques
+};
+
+constexpr int kK4Warps = 8;
+
+__device__ __forceinline__ void k4_add(unsigned long long *k4e, int64_t e, int P, int L, int a,
+                                       int b, unsigned long long v) {
+    atomicAdd(k4e + e * P + pair_index(L, a, b), v);
+}
+
+__global__ void __launch_bounds__(kK4Warps * 32) k_k4(K4Params p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int L = p.L, P = p.P, cap = p.cap;
+    uint32_t *w_ent = reinterpret_cast<uint32_t *>(smem) + (size_t)warp * cap * (3 + L);
+    int32_t *w_p0 = reinterpret_cast<int32_t *>(w_ent + cap);  // position in x0's list
+    int32_t *w_pv = w_p0 + cap;                                  // position in v's list
+    uint32_t *xacc = reinterpret_cast<uint32_t *>(w_pv + cap);  // cap * L
+    unsigned long long *h4 = reinterpret_cast<unsigned long long *>(
+        smem + (size_t)kK4Warps * cap * (3 + L) * 4);  // global mode: n4 entries
+    const bool global = p.g4 != nullptr;
+    if (global) {
+        for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x) h4[q] = 0ull;
+        __syncthreads();
+    }
+    const uint32_t below = (1u << lane) - 1u;
+    unsigned long long wk_cand = 0, wk_k4 = 0;
+
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(p.queue, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= (unsigned long long)p.n) break;
+        const uint32_t x0 = (uint32_t)item;
+        const int64_t b0 = p.uoff[x0];
+        const int d0 = (int)(p.uoff[x0 + 1] - b0);
+        if (d0 < 3) continue;  // x0 is the lowest node: three more above it
+        const int t0 = p.ntype[x0];
+        const int32_t *to0 = p.utoff + (int64_t)x0 * (L + 1);
+        for (int c0 = 0; c0 < d0; c0 += 32) {
+            const int xx = c0 + lane;
+            uint32_t ev = 0;
+            bool isup = false;
+            if (xx < d0) {
+                ev = __ldg(p.uadj + b0 + xx);
+                isup = true;
+            }
+            unsigned upm = __ballot_sync(kFull, isup);
+            while (upm) {
+                const int src = __ffs(upm) - 1;
+                upm &= upm - 1;
+                const uint32_t vent = __shfl_sync(kFull, ev, src);
+                const uint32_t v = vent & TG_IDMASK;
+                const int tv = (int)(vent >> TG_TSHIFT);
+                const int64_t bv = p.uoff[v];
+                const int dv = (int)(p.uoff[v + 1] - bv);
+                const int32_t *tov = p.utoff + (int64_t)v * (L + 1);
+                const int64_t e0v = __ldg(p.ueid + b0 + c0 + src);
+                // W = up(v) n up(x0) (= up(v) n Gamma(x0)), in the order of up(v)
+                int nw = 0;
+                for (int c1 = 0; c1 < dv; c1 += 32) {
+                    const int q = c1 + lane;
+                    bool ok = false;
+                    uint32_t wq = 0;
+                    int pos0 = -1;
+                    if (q < dv) {
+                        wq = __ldg(p.uadj + bv + q);
+                        pos0 = find_pos(p.uadj, b0, to0, wq);
+                        ok = pos0 >= 0;
+                    }
+                    const unsigned m = __ballot_sync(kFull, ok);
+                    const int r = nw + __popc(m & below);
+                    if (ok && r < cap) {
+                        w_ent[r] = wq;
+                        w_p0[r] = pos0;
+                        w_pv[r] = q;
+                    }
+                    nw += __popc(m);
+                }
+                if (nw < 2) {
+                    __syncwarp();
+                    continue;
+                }
+                const bool staged = nw <= cap;
+                if (staged && !global)
+                    for (int q = lane; q < nw * L; q += 32) xacc[q] = 0u;
+                __syncwarp();
+                // every w of W (staged: from shared memory; else re-derived)
+                for (int c1 = 0, k = 0; staged ? k < nw : c1 < dv;) {
+                    unsigned wm;
+                    uint32_t wlane = 0;
+                    int p0lane = -1;
+                    if (staged) {
+                        wm = 1u;
+                    } else {
+                        const int q = c1 + lane;
+                        bool ok = false;
+                        if (q < dv) {
+                            wlane = __ldg(p.uadj + bv + q);
+                            p0lane = find_pos(p.uadj, b0, to0, wlane);
+                            ok = p0lane >= 0;
+                        }
+                        wm = __ballot_sync(kFull, ok);
+                    }
+                    while (wm) {
+                        const int sl = __ffs(wm) - 1;
+                        wm &= wm - 1;
+                        uint32_t went;
+                        int wp0, wpv;
+                        if (staged) {
+                            went = w_ent[k];
+                            wp0 = w_p0[k];
+                            wpv = w_pv[k];
+                        } else {
+                            went = __shfl_sync(kFull, wlane, sl);
+                            wp0 = __shfl_sync(kFull, p0lane, sl);
+                            wpv = c1 + sl;
+                        }
+                        const uint32_t w = went & TG_IDMASK;
+                        const int tw = (int)(went >> TG_TSHIFT);
+                        const int64_t bw = p.uoff[w];
+                        const int dw = (int)(p.uoff[w + 1] - bw);
+                        const int64_t e0w = __ldg(p.ueid + b0 + wp0);
+                        const int64_t evw = __ldg(p.ueid + bv + wpv);
+                        for (int c2 = 0; c2 < dw; c2 += 32) {
+                            const int r = c2 + lane;
+                            int key = -1;
+                            if (r < dw) {
+                                const uint32_t xe = __ldg(p.uadj + bw + r);
+                                {
+                                    ++wk_cand;
+                                    int64_t e0x = -1, evx = -1;
+                                    if (staged) {
+                                        int lo = 0, hi = nw;
+                                        while (lo < hi) {
+                                            const int mid = (lo + hi) >> 1;
+                                            if (w_ent[mid] < xe)
+                                                lo = mid + 1;
+                                            else
+                                                hi = mid;
+                                        }
+                                        if (lo < nw && w_ent[lo] == xe) {
+                                            // (x0,x) and (v,x) are summed per x below
+                                            if (!global) atomicAdd(xacc + lo * L + tw, 1u);
+                                            e0x = 0;
+                                        }
+                                    } else {
+                                        const int px0 = find_pos(p.uadj, b0, to0, xe);
+                                        if (px0 >= 0) {
+                                            const int pxv = find_pos(p.uadj, bv, tov, xe);
+                                            if (pxv >= 0) {
+                                                e0x = 0;
+                                                if (!global) {
+                                                    evx = __ldg(p.ueid + bv + pxv);
+                                                    k4_add(p.k4e, __ldg(p.ueid + b0 + px0), P, L,
+                                                           tv, tw, 1ull);
+                                                    k4_add(p.k4e, evx, P, L, t0, tw, 1ull);
+                                                }
+                                            }
+                                        }
+                                    }
+                                    if (e0x >= 0) {
+                                        key = (int)(xe >> TG_TSHIFT);
+                                        if (!global)
+                                            k4_add(p.k4e, __ldg(p.ueid + bw + r), P, L, t0, tv,
+                                                   1ull);
+                                        ++wk_k4;
+                                    }
+                                }
+                            }
+                            // edges (x0,v), (x0,w), (v,w), summed over x of one type
+                            const unsigned mm = __match_any_sync(kFull, key);
+                            if (key >= 0 && lane == __ffs(mm) - 1) {
+                                const unsigned long long c = (unsigned long long)__popc(mm);
+                                if (global) {
+                                    int q0 = t0, q1 = tv, q2 = tw, q3 = key;
+                                    sort2(q0, q1);
+                                    sort2(q2, q3);
+                                    sort2(q0, q2);
+                                    sort2(q1, q3);
+                                    sort2(q1, q2);
+                                    atomicAdd(h4 + colex4(q0, q1, q2, q3), c);
+                                } else {
+                                    k4_add(p.k4e, e0v, P, L, tw, key, c);
+                                    k4_add(p.k4e, e0w, P, L, tv, key, c);
+                                    k4_add(p.k4e, evw, P, L, t0, key, c);
+                                }
+                            }
+                        }
+                        if (staged) ++k;
+                    }
+                    if (!staged) c1 += 32;
+                }
+                if (staged && !global) {
+                    __syncwarp();
+                    for (int q = lane; q < nw * L; q += 32) {
+                        const uint32_t c = xacc[q];
+                        if (c) {
+                            const int kx = q / L, tw = q % L;
+                            k4_add(p.k4e, __ldg(p.ueid + b0 + w_p0[kx]), P, L, tv, tw, c);
+                            k4_add(p.k4e, __ldg(p.ueid + bv + w_pv[kx]), P, L, t0, tw, c);
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+    if (global) {
+        __syncthreads();
+        for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x)
+            if (h4[q]) atomicAdd(p.g4 + q, h4[q]);
+    }
+    if (p.work) {
+        if (wk_cand) atomicAdd(p.work + 5, wk_cand);
+        if (wk_k4) atomicAdd(p.work + 6, wk_k4);
+    }
+}
+
+// Global mode: the per-edge pass ran with Q = C4 = 0.  Summed over the edges,
+// Q and C4 enter the graphlet sums (each identity is linear in them) only
+// through the type-multiset totals of 4-cliques K4 and of non-induced
+// 4-cycles N_C4; added here to the undivided sums of h3..h8:
+//   h3 -12 N_C4 - 36 K4, h4 -12 K4, h5 +4 N_C4 + 12 K4, h6 +48 K4,
+//   h7 -30 K4, h8 +6 K4.   (c4w = 2 N_C4, k4 = K4; arithmetic mod 2^64.)
+__global__ void k_cyc_correct(unsigned long long *hist, int64_t off4, int64_t n4,
+                              const unsigned long long *c4w, const unsigned long long *k4) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n4;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long w = c4w[r], k = k4[r];
+        hist[off4 + 0 * n4 + r] += (unsigned long long)(-6ll) * w + (unsigned long long)(-36ll) * k;
+        hist[off4 + 1 * n4 + r] += (unsigned long long)(-12ll) * k;
+        hist[off4 + 2 * n4 + r] += 2ull * w + 12ull * k;
+        hist[off4 + 3 * n4 + r] += 48ull * k;
+        hist[off4 + 4 * n4 + r] += (unsigned long long)(-30ll) * k;
+        hist[off4 + 5 * n4 + r] += 6ull * k;
+    }
+}
+
+// ------------------------------------------------------ per-edge counts ----
+struct EdgeParams {
+    const int64_t *rowptr;
+    const uint32_t *adj;
+    const uint32_t *eid;
+    const int32_t *toff;
+    const uint8_t *ntype;
+    const int2 *edges;
+    const uint32_t *order;
+    const uint32_t *ustart;
+    uint32_t nunits;
+    const uint32_t *tau;
+    const uint32_t *theta;
+    const uint32_t *dsum;
+    const unsigned long long *c4e;
+    const unsigned long long *k4e;
+    int32_t L, P, k, level;
+    int64_t nbits;
+    unsigned long long *queue;
+    uint64_t *rows;
+    int64_t width;
+    unsigned long long *hist;
+    int64_t hist_len;
+    int32_t hist_smem;
+    int64_t off1, off2, off4, n4;
+    unsigned long long *work;  // [0]: Gamma_i entries, [3]: T members
+};
+
+// The inputs of the identities for one edge (see tg_reuse.cu).
+struct EdgeIn {
+    int L, ti, tj;
+    const unsigned long long *B, *C, *DT;  // ordered [a][b], this warp's shared memory
+    const unsigned long long *c4;          // ordered [a][b]
+    const unsigned long long *k4;          // unordered pairs
+    const uint32_t *thi, *thj, *dvi, *dvj; // ordered [a][b]
+    const uint32_t *tn;                    // tau of the edge: |T^t|
+    const int32_t *toi, *toj;
+};
+
+struct EdgeEval {
+    const EdgeIn &in;
+    __device__ long long deg_i(int b) const { return __ldg(in.toi + b + 1) - __ldg(in.toi + b); }
+    __device__ long long deg_j(int b) const { return __ldg(in.toj + b + 1) - __ldg(in.toj + b); }
+    __device__ long long Tn(int a) const { return (long long)__ldg(in.tn + a); }
+    __device__ long long Si(int a) const { return deg_i(a) - Tn(a) - (a == in.tj); }
+    __device__ long long Sj(int a) const { return deg_j(a) - Tn(a) - (a == in.ti); }
+    __device__ long long B(int a, int b) const { return (long long)in.B[a * in.L + b]; }
+    __device__ long long C(int a, int b) const { return (long long)in.C[a * in.L + b]; }
+    __device__ long long DT(int a, int b) const { return (long long)in.DT[a * in.L + b]; }
+    __device__ long long Q(int a, int b) const {
+        if (!in.k4) return 0;  // global mode: added from the 4-clique totals
+        const long long k = (long long)__ldg(in.k4 + pair_index(in.L, a, b));
+        return a == b ? 2 * k : k;
+    }
+    __device__ long long TSj(int a, int b) const {
+        return B(a, b) - Q(a, b) - (b == in.ti ? Tn(a) : 0);
+    }
+    __device__ long long TSi(int a, int b) const {
+        return C(a, b) - Q(a, b) - (b == in.tj ? Tn(a) : 0);
+    }
+    __device__ long long SSj(int a, int b) const {
+        return (long long)__ldg(in.thj + a * in.L + b) - B(a, b) - (a == in.ti ? Tn(b) : 0);
+    }
+    __device__ long long SSi(int a, int b) const {
+        return (long long)__ldg(in.thi + a * in.L + b) - C(a, b) - (a == in.tj ? Tn(b) : 0);
+    }
+    __device__ long long DSj(int a, int b) const {
+        return (long long)__ldg(in.dvj + a * in.L + b) - DT(a, b) - (a == in.ti ? deg_i(b) : 0);
+    }
+    __device__ long long DSi(int a, int b) const {
+        return (long long)__ldg(in.dvi + a * in.L + b) - DT(a, b) - (a == in.tj ? deg_j(b) : 0);
+    }
+    __device__ long long G6(int a, int b) const {
+        // global mode: C4 is added from the 4-cycle totals
+        const long long c4 = in.c4 ? (long long)__ldg(in.c4 + a * in.L + b) : 0;
+        const long long s6 = c4 - B(a, b) + (b == in.ti ? Tn(a) : 0);
+        return s6 - TSi(b, a);
+    }
+    __device__ long long Y(int a, int b) const {
+        return DSi(a, b) - (b == in.ti ? Si(a) : 0) - SSi(a, b) - G6(a, b) + DSj(a, b) -
+               (b == in.tj ? Sj(a) : 0) - SSj(a, b) - G6(b, a);
+    }
+    __device__ long long Z(int a, int b) const {
+        return DT(a, b) - Tn(a) * ((b == in.ti) + (b == in.tj)) - Q(a, b) - TSi(a, b) -
+               TSj(a, b);
+    }
+};
+
+// Orbits g3..g12 of the type pair (t, u), t <= u.
+__device__ __forceinline__ void pair_orbits(const EdgeEval &E, int t, int u, uint64_t g[10]) {
+    auto sym = [&](long long x_tu, long long x_ut) -> long long {
+        return t == u ? x_tu : x_tu + x_ut;
+    };
+    const long long q2 = sym(E.Q(t, u), E.Q(u, t));
+    const uint64_t g12 = (uint64_t)(q2 / 2);
+    const uint64_t g10 = (uint64_t)(sym(E.TSi(t, u) + E.TSj(t, u), E.TSi(u, t) + E.TSj(u, t)));
+    const long long sisi_tu = E.SSi(t, u) - E.TSi(u, t), sisi_ut = E.SSi(u, t) - E.TSi(t, u);
+    const long long sjsj_tu = E.SSj(t, u) - E.TSj(u, t), sjsj_ut = E.SSj(u, t) - E.TSj(t, u);
+    const uint64_t g7 = (uint64_t)(sym(sisi_tu + sjsj_tu, sisi_ut + sjsj_ut) / 2);
+    const uint64_t g6 = (uint64_t)sym(E.G6(t, u), E.G6(u, t));
+    const uint64_t g3 = (uint64_t)sym(E.Y(t, u), E.Y(u, t));
+    const uint64_t g8 = (uint64_t)sym(E.Z(t, u), E.Z(u, t));
+    const uint64_t sit = (uint64_t)E.Si(t), siu = (uint64_t)E.Si(u);
+    const uint64_t sjt = (uint64_t)E.Sj(t), sju = (uint64_t)E.Sj(u);
+    const uint64_t tt = (uint64_t)E.Tn(t), tu = (uint64_t)E.Tn(u);
+    uint64_t g4, g5, g9, g11;
+    if (t == u) {
+        g4 = sit * sjt - g6;
+        g5 = c2(sit) + c2(sjt) - g7;
+        g9 = tt * (sit + sjt) - g10;
+        g11 = c2(tt) - g12;
+    } else {
+        g4 = sit * sju + siu * sjt - g6;
+        g5 = sit * siu + sjt * sju - g7;
+        g9 = tt * (siu + sju) + tu * (sit + sjt) - g10;
+        g11 = tt * tu - g12;
+    }
+    g[0] = g3;
+    g[1] = g4;
+    g[2] = g5;
+    g[3] = g6;
+    g[4] = g7;
+    g[5] = g8;
+    g[6] = g9;
+    g[7] = g10;
+    g[8] = g11;
+    g[9] = g12;
+}
+
+__device__ __forceinline__ void hadd_e(const EdgeParams &p, unsigned long long *shist, int64_t x,
+                                       unsigned long long v) {
+    if (!v) return;
+    if (p.hist_smem)
+        atomicAdd(shist + x, v);
+    else
+        atomicAdd(p.hist + x, v);
+}
+
+constexpr int kEdgeMaxThreads = 512;
+
+__global__ void __launch_bounds__(kEdgeMaxThreads) k_cyc_edge(EdgeParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const int L = p.L, P = p.P, L2 = L * L;
+    size_t off = 0;
+    unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);
+    if (p.hist_smem) off += ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
+    const size_t wbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
+    unsigned long long *Bm = reinterpret_cast<unsigned long long *>(smem + off + warp * wbytes);
+    unsigned long long *Cm = Bm + L2;
+    unsigned long long *Dm = Cm + L2;
+    off += (size_t)W * wbytes;
+    unsigned long long *s_unit = reinterpret_cast<unsigned long long *>(smem + off);
+    off += 16;
+    uint32_t *bm = reinterpret_cast<uint32_t *>(smem + off);
+    const int64_t bwords = (p.nbits + 31) >> 5;
+    for (int64_t x = tid; x < bwords; x += blockDim.x) bm[x] = 0u;
+    if (p.hist_smem)
+        for (int64_t x = tid; x < p.hist_len; x += blockDim.x) shist[x] = 0;
+    const int64_t *__restrict__ rowptr = p.rowptr;
+    const uint32_t *__restrict__ adj = p.adj;
+    int cur_j = -1;
+    int64_t cur_bj = 0;
+    int cur_dj = 0;
+    unsigned long long wk_gamma = 0, wk_t = 0;
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) *s_unit = atomicAdd(p.queue, 1ull);
+        __syncthreads();
+        const unsigned long long un = *s_unit;
+        if (un >= p.nunits) break;
+        const uint32_t p0 = p.ustart[un], p1 = p.ustart[un + 1];
+        const int2 ab0 = p.edges[p.order[p0]];
+        const int j = min(ab0.x, ab0.y);
+        const int64_t bj = rowptr[j];
+        const int dj = (int)(rowptr[j + 1] - bj);
+        if (p.k == 4 && j != cur_j) {
+            for (int x = tid; x < cur_dj; x += blockDim.x) {
+                const uint32_t id = __ldg(adj + cur_bj + x) & TG_IDMASK;
+                if ((int64_t)id < p.nbits) atomicAnd(&bm[id >> 5], ~(1u << (id & 31u)));
+            }
+            __syncthreads();
+            for (int x = tid; x < dj; x += blockDim.x) {
+                const uint32_t id = __ldg(adj + bj + x) & TG_IDMASK;
+                if ((int64_t)id < p.nbits) atomicOr(&bm[id >> 5], 1u << (id & 31u));
+            }
+            cur_j = j;
+            cur_bj = bj;
+            cur_dj = dj;
+            __syncthreads();
+        }
+        for (uint32_t q = p0 + warp; q < p1; q += W) {
+            const int64_t e = p.order[q];
+            const int2 ab = p.edges[e];
+            const int i = max(ab.x, ab.y);
+            const int ti = p.ntype[i], tj = p.ntype[j];
+            const int64_t bi = rowptr[i];
+            const int di = (int)(rowptr[i + 1] - bi);
+            const int32_t *toi = p.toff + (int64_t)i * (L + 1);
+            const int32_t *toj = p.toff + (int64_t)j * (L + 1);
+            const uint32_t *tn = p.tau + e * L;
+            if (p.k == 4) {
+                for (int x = lane; x < 3 * L2; x += 32) Bm[x] = 0ull;
+                __syncwarp();
+                // T = Gamma_i n Gamma_j: sums of tau_jy, tau_iy and d_y by types
+                for (int c0 = 0; c0 < di; c0 += 32) {
+                    const int x = c0 + lane;
+                    bool isT = false;
+                    uint32_t w = 0;
+                    if (x < di) {
+                        w = __ldg(adj + bi + x);
+                        const uint32_t id = w & TG_IDMASK;
+                        if ((int)id != j)
+                            isT = (int64_t)id < p.nbits ? bm_test(bm, id)
+                                                        : contains(adj, bj, toj, w);
+                    }
+                    const int a = (int)(w >> TG_TSHIFT);
+                    const unsigned tm = __match_any_sync(kFull, isT ? a : -1);
+                    const bool lead = isT && lane == __ffs(tm) - 1;
+                    const uint32_t *tiy = p.tau, *tjy = p.tau;
+                    const int32_t *ty = p.toff;
+                    if (isT) {
+                        tiy = p.tau + (int64_t)__ldg(p.eid + bi + x) * L;
+                        const int pj = find_pos(adj, bj, toj, w);
+                        tjy = p.tau + (int64_t)__ldg(p.eid + bj + (pj < 0 ? 0 : pj)) * L;
+                        ty = p.toff + (int64_t)(w & TG_IDMASK) * (L + 1);
+                    }
+                    int prev = isT ? __ldg(ty) : 0;
+                    for (int b = 0; b < L; ++b) {
+                        uint32_t vb = 0, vc = 0, vd = 0;
+                        if (isT) {
+                            vb = __ldg(tjy + b);
+                            vc = __ldg(tiy + b);
+                            const int nx = __ldg(ty + b + 1);
+                            vd = (uint32_t)(nx - prev);
+                            prev = nx;
+                        }
+                        const uint32_t sb = __reduce_add_sync(tm, vb);
+                        const uint32_t sc = __reduce_add_sync(tm, vc);
+                        const uint32_t sd = __reduce_add_sync(tm, vd);
+                        if (lead) {
+                            Bm[a * L + b] += sb;
+                            Cm[a * L + b] += sc;
+                            Dm[a * L + b] += sd;
+                        }
+                    }
+                    const unsigned tb = __ballot_sync(kFull, isT);
+                    if (lane == 0) wk_t += (unsigned long long)__popc(tb);
+                }
+                __syncwarp();
+            }
+            if (lane == 0) wk_gamma += (unsigned long long)di;
+            // 2- and 3-node entries
+            if (p.rows) {
+                uint64_t *row = p.rows + e * p.width;
+                for (int t = lane; t < L; t += 32) {
+                    const uint32_t tt = __ldg(tn + t);
+                    const int64_t si = (int64_t)(__ldg(toi + t + 1) - __ldg(toi + t)) - tt - (t == tj);
+                    const int64_t sj = (int64_t)(__ldg(toj + t + 1) - __ldg(toj + t)) - tt - (t == ti);
+                    row[t] = (uint64_t)(si + sj);
+                    row[L + t] = tt;
+                }
+            } else {
+                if (lane == 0) {
+                    int a = ti, b = tj;
+                    sort2(a, b);
+                    hadd_e(p, shist, (int64_t)a + (int64_t)(b + 1) * b / 2, 1ull);
+                }
+                for (int t = lane; t < L; t += 32) {
+                    const uint32_t tt = __ldg(tn + t);
+                    const int64_t si = (int64_t)(__ldg(toi + t + 1) - __ldg(toi + t)) - tt - (t == tj);
+                    const int64_t sj = (int64_t)(__ldg(toj + t + 1) - __ldg(toj + t)) - tt - (t == ti);
+                    int a = ti, b = tj, cc = t;
+                    sort2(a, b);
+                    sort2(b, cc);
+                    sort2(a, b);
+                    const int64_t r = colex3(a, b, cc);
+                    hadd_e(p, shist, p.off1 + r, (unsigned long long)(si + sj));
+                    hadd_e(p, shist, p.off2 + r, (unsigned long long)tt);
+                }
+            }
+            if (p.k == 4) {
+                EdgeIn in;
+                in.L = L;
+                in.ti = ti;
+                in.tj = tj;
+                in.B = Bm;
+                in.C = Cm;
+                in.DT = Dm;
+                in.c4 = p.c4e ? p.c4e + e * L2 : nullptr;
+                in.k4 = p.k4e ? p.k4e + e * P : nullptr;
+                in.thi = p.theta + (int64_t)i * L2;
+                in.thj = p.theta + (int64_t)j * L2;
+                in.dvi = p.dsum + (int64_t)i * L2;
+                in.dvj = p.dsum + (int64_t)j * L2;
+                in.tn = tn;
+                in.toi = toi;
+                in.toj = toj;
+                const EdgeEval E{in};
+                for (int pr = lane; pr < P; pr += 32) {
+                    int t, u;
+                    unpair(L, pr, t, u);
+                    uint64_t g[10];
+                    pair_orbits(E, t, u, g);
+                    if (p.rows) {
+                        uint64_t *row = p.rows + e * p.width + 2 * L;
+                        if (p.level == TG_ORBIT) {
+#pragma unroll
+                            for (int o = 0; o < 10; ++o) row[o * P + pr] = g[o];
+                        } else {
+                            row[0 * P + pr] = g[0] + g[1];
+                            row[1 * P + pr] = g[2];
+                            row[2 * P + pr] = g[3];
+                            row[3 * P + pr] = g[4] + g[5] + g[6];
+                            row[4 * P + pr] = g[7] + g[8];
+                            row[5 * P + pr] = g[9];
+                        }
+                    } else {
+                        const uint64_t h[6] = {g[0] + g[1], g[2], g[3], g[4] + g[5] + g[6],
+                                               g[7] + g[8], g[9]};
+                        if (h[0] | h[1] | h[2] | h[3] | h[4] | h[5]) {
+                            int a = ti, b = tj, cc = t, d = u;
+                            sort2(a, b);
+                            sort2(cc, d);
+                            sort2(a, cc);
+                            sort2(b, d);
+                            sort2(b, cc);
+                            const int64_t r = colex4(a, b, cc, d);
+#pragma unroll
+                            for (int qq = 0; qq < 6; ++qq) hadd_e(p, shist, p.off4 + qq * p.n4 + r, h[qq]);
+                        }
+                    }
+                }
+            }
+            __syncwarp();  // this warp's matrices are cleared for the next edge
+        }
+    }
+    if (p.hist_smem) {
+        __syncthreads();
+        for (int64_t x = tid; x < p.hist_len; x += blockDim.x)
+            if (shist[x]) atomicAdd(p.hist + x, shist[x]);
+    }
+    if (p.work && lane == 0) {
+        atomicAdd(p.work + 0, wk_gamma);
+        atomicAdd(p.work + 3, wk_t);
+    }
+}
+
+int num_sms_c() {
+    int dev = 0, sms = 0;
+    (void)cudaGetDevice(&dev);
+    (void)cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+int smem_optin_c() {
+    int dev = 0, v = 0;
+    (void)cudaGetDevice(&dev);
+    (void)cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v > 0 ? v : 48 * 1024;
+}
+
+}  // namespace
+
+int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long *g4,
+                  unsigned long long *work, const tg_tune &t, cudaStream_t s) {
+    if (g->M == 0) return TG_OK;
+    const int L = g->L, L2 = L * L;
+    const int64_t n = g->n;
+    const bool global = g4 != nullptr;
+    const int64_t n4 = tg_binom(L + 3, 4);
+    const size_t avail = (size_t)smem_optin_c() - 1024;
+    // staged members per tile: their lists, ids and (a, u) accumulators
+    const size_t per_member = 8 + 8 + 4 + 4 + (global ? 0 : (size_t)L2 * 8);
+    const size_t fixed = 34 * 8 + 16 + 8 + (global ? (size_t)n4 * 8 : 0);
+    if (fixed + 32 * per_member > avail) return TG_EINVAL;
+    int TM = (int)std::min<size_t>(kC4Threads, (avail - fixed) / per_member);
+    TM &= ~31;
+    if (TM < 32) return TG_EINVAL;
+    const size_t smem = (size_t)TM * per_member + fixed;
+    TG_TRY(tg_allow_max_smem((const void *)k_c4));
+    TG_TRY(tg_allow_max_smem((const void *)k_c4_split));
+    int per_sm = 0;
+    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c4, kC4Threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t full_grid = (int64_t)num_sms_c() * per_sm;
+
+    // anchor costs; those above thr are split into units over the whole grid
+    DevBuf<unsigned long long> cost, total;
+    DevBuf<uint8_t> split;
+    DevBuf<uint32_t> flag, pos, list;
+    if (!cost.alloc(n, s) || !total.alloc(1, s) || !split.alloc(n, s) || !flag.alloc(n, s) ||
+        !pos.alloc(n, s))
+        return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(total.p, 0, 8, s));
+    const unsigned wgrid = (unsigned)std::min<int64_t>((n * 32 + 255) / 256, 65535LL * 16);
+    k_c4_cost<<<wgrid, 256, 0, s>>>(g->rowptr, g->adj, n, cost.p, total.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    unsigned long long tot = 0;
+    TG_TRY_CUDA(cudaMemcpyAsync(&tot, total.p, 8, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    // unroll selects the split rule: 1 none, 4 every anchor, else by cost
+    unsigned long long thr = std::max<unsigned long long>(tot / (unsigned long long)(2 * full_grid),
+                                                          (unsigned long long)1 << 16);
+    if (t.unroll == 1) thr = ~0ull;
+    if (t.unroll == 4) thr = 0ull;
+    const unsigned egrid = (unsigned)std::min<int64_t>((n + 255) / 256, 65535LL * 16);
+    k_c4_mark<<<egrid, 256, 0, s>>>(cost.p, n, thr, split.p, flag.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    TG_TRY(tg_scan_u32(flag.p, pos.p, n, s));
+    uint32_t lastp = 0, lastf = 0;
+    TG_TRY_CUDA(cudaMemcpyAsync(&lastp, pos.p + n - 1, 4, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaMemcpyAsync(&lastf, flag.p + n - 1, 4, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    const int64_t nheavy = (int64_t)lastp + lastf;
+    std::vector<uint32_t> heavy((size_t)nheavy);
+    std::vector<int64_t> hdeg((size_t)nheavy);
+    if (nheavy > 0) {
+        if (!list.alloc(nheavy, s)) return TG_ENOMEM;
+        k_c4_compact<<<egrid, 256, 0, s>>>(flag.p, pos.p, n, list.p); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+        TG_TRY_CUDA(cudaMemcpyAsync(heavy.data(), list.p, nheavy * 4, cudaMemcpyDeviceToHost, s));
+        TG_TRY_CUDA(cudaStreamSynchronize(s));
+        // degrees of the split anchors: the list is ascending, so one copy of
+        // rowptr up to the largest of them
+        const int64_t top = (int64_t)heavy[(size_t)nheavy - 1] + 2;
+        std::vector<int64_t> rp((size_t)top);
+        TG_TRY_CUDA(cudaMemcpyAsync(rp.data(), g->rowptr, top * 8, cudaMemcpyDeviceToHost, s));
+        TG_TRY_CUDA(cudaStreamSynchronize(s));
+        for (int64_t q = 0; q < nheavy; ++q) hdeg[q] = rp[heavy[q] + 1] - rp[heavy[q]];
+    }
+
+    // counter slots: one per CTA of the one-CTA kernel, one per split anchor of
+    // a wave; all within a quarter of free memory
+    const int64_t slot_words = n * L;
+    const size_t slot_bytes = (size_t)slot_words * 4;
+    size_t free_b = 0, total_b = 0;
+    TG_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    int64_t slots = (int64_t)(free_b / 4 / (slot_bytes ? slot_bytes : 1));
+    if (slots > full_grid) slots = full_grid;
+    if (slots > n) slots = n;
+    if (slots < 1) {
+        if (slot_bytes > free_b / 2) return TG_ENOMEM;
+        slots = 1;
+    }
+    DevBuf<uint32_t> scratch;
+    DevBuf<unsigned long long> queue;
+    if (!scratch.alloc((size_t)slots * slot_words, s) || !queue.alloc(1, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(scratch.p, 0, (size_t)slots * slot_bytes, s));
+    C4Params p{};
+    p.rowptr = g->rowptr;
+    p.adj = g->adj;
+    p.eid = g->eid;
+    p.ntype = g->ntype;
+    p.n = n;
+    p.L = L;
+    p.tile = TM;
+    p.acc_l2 = global ? 0 : L2;
+    p.scratch = scratch.p;
+    p.slot_words = slot_words;
+    p.queue = queue.p;
+    p.c4e = c4e;
+    p.g4 = g4;
+    p.n4 = n4;
+    p.split = split.p;
+    p.work = work;
+
+    // split anchors, in waves of at most `slots` anchors
+    if (nheavy > 0) {
+        std::vector<int4> units;
+        std::vector<int64_t> wave_start;
+        for (int64_t q0 = 0; q0 < nheavy; q0 += slots) {
+            wave_start.push_back((int64_t)units.size());
+            for (int64_t q = q0; q < std::min(nheavy, q0 + slots); ++q)
+                for (int64_t tl = 0; tl < hdeg[q]; tl += TM)
+                    units.push_back(make_int4((int)(q - q0), (int)heavy[q], (int)tl, 0));
+        }
+        wave_start.push_back((int64_t)units.size());
+        DevBuf<int4> du;
+        if (!du.alloc(units.size(), s)) return TG_ENOMEM;
+        TG_TRY_CUDA(cudaMemcpyAsync(du.p, units.data(), units.size() * sizeof(int4),
+                                    cudaMemcpyHostToDevice, s));
+        for (size_t w = 0; w + 1 < wave_start.size(); ++w) {
+            const int64_t u0 = wave_start[w], nu = wave_start[w + 1] - u0;
+            p.units = du.p + u0;
+            p.n_units = nu;
+            int64_t grid = std::min<int64_t>(full_grid, nu);
+            for (int ph = 0; ph < 3; ++ph) {
+                p.phase = ph;
+                TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
+                k_c4_split<<<(unsigned)grid, kC4Threads, smem, s>>>(p); tg_note_launch();
+                TG_TRY_CUDA(cudaGetLastError());
+            }
+        }
+        // the host vectors are read by the copy above before they go out of scope
+        TG_TRY_CUDA(cudaStreamSynchronize(s));
+    }
+    // the other anchors, one CTA each
+    p.units = nullptr;
+    p.n_units = 0;
+    p.phase = 0;
+    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
+    int64_t grid = slots;
+    k_c4<<<(unsigned)grid, kC4Threads, smem, s>>>(p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    return TG_OK;
+}
+
+int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long long *g4,
+                   unsigned long long *work, const tg_tune &t, cudaStream_t s) {
+    if (g->M == 0) return TG_OK;
+    const int L = g->L;
+    const bool global = g4 != nullptr;
+    const int64_t n4 = tg_binom(L + 3, 4);
+    const size_t hbytes = global ? (size_t)n4 * 8 : 0;
+    const size_t avail = (size_t)smem_optin_c() - 1024 - hbytes;
+    const size_t per_entry = (size_t)(3 + L) * 4;
+    // W entries staged per warp; hash_slots caps it (a small cap sends large W
+    // sets down the path that tests membership in the global lists instead)
+    int cap = (int)std::min<size_t>(std::min(512, t.hash_slots), avail / kK4Warps / per_entry);
+    cap &= ~31;
+    if (cap < 32) return TG_EINVAL;
+    const size_t smem = (size_t)kK4Warps * cap * per_entry + hbytes;
+    TG_TRY(tg_allow_max_smem((const void *)k_k4));
+    int per_sm = 0;
+    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_k4, kK4Warps * 32, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)num_sms_c() * per_sm;
+    const int64_t need = (g->n + kK4Warps - 1) / kK4Warps;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    // up lists: each edge once, at its lower-ranked end
+    DevBuf<int32_t> utoff;
+    DevBuf<int64_t> utot, uoff;
+    DevBuf<uint32_t> uadj, ueid;
+    const int64_t n = g->n;
+    if (!utoff.alloc((size_t)n * (L + 1), s) || !utot.alloc(n + 1, s) || !uoff.alloc(n + 1, s) ||
+        !uadj.alloc(g->M, s) || !ueid.alloc(g->M, s))
+        return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(utot.p + n, 0, 8, s));
+    const unsigned wgrid = (unsigned)std::min<int64_t>((n * 32 + 255) / 256, 65535LL * 16);
+    k_up_count<<<wgrid, 256, 0, s>>>(g->rowptr, g->adj, g->toff, n, L, utoff.p, utot.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    TG_TRY(tg_scan_i64(utot.p, uoff.p, n + 1, s));
+    k_up_fill<<<wgrid, 256, 0, s>>>(g->rowptr, g->adj, g->eid, g->toff, utoff.p, uoff.p, n, L,
+                                    uadj.p, ueid.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    DevBuf<unsigned long long> queue;
+    if (!queue.alloc(1, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
+    K4Params p{};
+    p.uoff = uoff.p;
+    p.uadj = uadj.p;
+    p.ueid = ueid.p;
+    p.utoff = utoff.p;
+    p.ntype = g->ntype;
+    p.n = g->n;
+    p.L = L;
+    p.P = L * (L + 1) / 2;
+    p.cap = cap;
+    p.queue = queue.p;
+    p.k4e = k4e;
+    p.g4 = g4;
+    p.n4 = n4;
+    p.work = work;
+    k_k4<<<(unsigned)grid, kK4Warps * 32, smem, s>>>(p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    return TG_OK;
+}
+
+int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order,
+                 const uint32_t *ustart, uint32_t nunits, uint64_t *rows, int64_t width,
+                 unsigned long long *hist, const uint32_t *tau, const uint32_t *theta,
+                 const uint32_t *dsum, const unsigned long long *c4e,
+                 const unsigned long long *k4e, unsigned long long *work, const tg_tune &t,
+                 cudaStream_t s) {
+    if (nunits == 0) return TG_OK;
+    const int L = g->L, L2 = L * L;
+    if (g->max_degree >= ((int64_t)1 << 27)) return TG_EOVERFLOW;  // 32-lane uint32 sums
+    EdgeParams p{};
+    p.rowptr = g->rowptr;
+    p.adj = g->adj;
+    p.eid = g->eid;
+    p.toff = g->toff;
+    p.ntype = g->ntype;
+    p.edges = g->edges;
+    p.order = order;
+    p.ustart = ustart;
+    p.nunits = nunits;
+    p.tau = tau;
+    p.theta = theta;
+    p.dsum = dsum;
+    p.c4e = c4e;
+    p.k4e = k4e;
+    p.L = L;
+    p.P = L * (L + 1) / 2;
+    p.k = k;
+    p.level = level;
+    p.rows = rows;
+    p.width = width;
+    p.hist = hist;
+    p.hist_len = tg_global_len(L, k);
+    p.off1 = tg_binom(L + 1, 2);
+    p.off2 = p.off1 + tg_binom(L + 2, 3);
+    p.off4 = p.off1 + 2 * tg_binom(L + 2, 3);
+    p.n4 = tg_binom(L + 3, 4);
+    p.work = work;
+    int threads = t.cta_threads;
+    if (threads > kEdgeMaxThreads) threads = kEdgeMaxThreads;
+    if (threads < 32) threads = 32;
+    const size_t avail = (size_t)smem_optin_c() - 1024;
+    const size_t hist_bytes = ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
+    p.hist_smem = (!rows && hist_bytes <= 48 * 1024) ? 1 : 0;
+    const size_t wbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
+    size_t fixed = (p.hist_smem ? hist_bytes : 0) + (size_t)(threads / 32) * wbytes + 16;
+    while (fixed + 4096 > avail && threads > 32) {
+        threads -= 32;
+        fixed = (p.hist_smem ? hist_bytes : 0) + (size_t)(threads / 32) * wbytes + 16;
+    }
+    if (fixed + 16 > avail) return TG_EINVAL;
+    int64_t nbits = k == 4 ? g->n_nonisolated : 0;
+    if (t.bitmap_bits > 0 && nbits > t.bitmap_bits) nbits = t.bitmap_bits;
+    const int64_t maxb = (int64_t)((avail - fixed) / 16) * 128;
+    if (nbits > maxb) nbits = maxb;
+    if (nbits < 0) nbits = 0;
+    p.nbits = nbits;
+    const size_t smem = fixed + ((((size_t)((nbits + 31) >> 5)) * 4 + 15) & ~(size_t)15);
+    DevBuf<unsigned long long> queue;
+    if (!queue.alloc(1, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
+    p.queue = queue.p;
+    TG_TRY(tg_allow_max_smem((const void *)k_cyc_edge));
+    int per_sm = 0;
+    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cyc_edge, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)num_sms_c() * per_sm;
+    if (grid > nunits) grid = nunits;
+    if (t.grid_limit > 0 && grid > t.grid_limit) grid = t.grid_limit;
+    if (grid < 1) grid = 1;
+    k_cyc_edge<<<(unsigned)grid, threads, smem, s>>>(p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    return TG_OK;
+}
+
+int tg_cyc_correct(unsigned long long *hist, int L, const unsigned long long *c4w,
+                   const unsigned long long *k4, cudaStream_t s) {
+    const int64_t n4 = tg_binom(L + 3, 4);
+    const int64_t off4 = tg_binom(L + 1, 2) + 2 * tg_binom(L + 2, 3);
+    k_cyc_correct<<<(unsigned)((n4 + 255) / 256), 256, 0, s>>>(hist, off4, n4, c4w, k4); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    return TG_OK;
+}

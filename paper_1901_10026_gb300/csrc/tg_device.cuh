@@ -67,6 +67,22 @@ constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr size_t kMiscBytes = 3 * 16 * 4 + 16;     // Tn, Si, Sj, work item
 constexpr size_t kStageBytes = 32 * 17;  // per-warp w_k slots (a multiple of 16 bytes)
 
+// Index of packed entry w in the list at adj + base (typed range search), -1 if absent
+__device__ __forceinline__ int find_pos(const uint32_t *__restrict__ adj, int64_t base,
+                                        const int32_t *__restrict__ to, uint32_t w) {
+    const int t = (int)(w >> TG_TSHIFT);
+    int lo = __ldg(to + t), hi = __ldg(to + t + 1);
+    const int end = hi;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(adj + base + mid) < w)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return (lo < end && __ldg(adj + base + lo) == w) ? lo : -1;
+}
+
 __device__ __forceinline__ uint32_t hslot(uint32_t id, int lg) {
     return (id * 2654435761u) >> (32 - lg);
 }

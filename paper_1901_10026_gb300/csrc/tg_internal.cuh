@@ -136,8 +136,28 @@ void tg_sched_free(tg_graph *g);
 void tg_sched_free_on(tg_graph *g, cudaStream_t s);
 int tg_free_graph_on(tg_graph *g, cudaStream_t s);
 
+// Whole-graph enumerations and the per-edge pass of the cycles kernel
+// (tg_cycles.cu).  Per-edge mode: c4e holds M x L x L and k4e M x L(L+1)/2
+// zeroed counters (g4 = NULL).  Global mode (c4e / k4e = NULL): g4 gets, by
+// type multiset (C(L+3,4) zeroed entries), twice the non-induced 4-cycles
+// (cycles) or the 4-cliques (cliques); tg_cyc_correct then adds their share
+// to undivided sums counted with Q = C4 = 0.
+int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long *g4,
+                  unsigned long long *work, const tg_tune &t, cudaStream_t s);
+int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long long *g4,
+                   unsigned long long *work, const tg_tune &t, cudaStream_t s);
+int tg_cyc_correct(unsigned long long *hist, int L, const unsigned long long *c4w,
+                   const unsigned long long *k4, cudaStream_t s);
+int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order,
+                 const uint32_t *ustart, uint32_t nunits, uint64_t *rows, int64_t width,
+                 unsigned long long *hist, const uint32_t *tau, const uint32_t *theta,
+                 const uint32_t *dsum, const unsigned long long *c4e,
+                 const unsigned long long *k4e, unsigned long long *work, const tg_tune &t,
+                 cudaStream_t s);
+
 // Counts through Alg. 1's typed triangle counts (tg_reuse.cu).  full_order is
-// the grouped order of all M edges; order[0..count) the edges to count.
+// the grouped order of all M edges; order[0..count) the edges to count.  With
+// TG_KERNEL_CYCLES (or AUTO) the per-edge pass is tg_cyc_*, else k_count_reuse.
 int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_order,
                    const uint32_t *order, int64_t count, uint64_t *rows, int64_t width,
                    unsigned long long *hist, const tg_tune &t, cudaStream_t s);

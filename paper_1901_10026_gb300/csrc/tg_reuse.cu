@@ -217,22 +217,6 @@ struct ReuseParams {
     unsigned long long *work;  // [Gamma_i entries, walked entries, probe pairs, T members]
 };
 
-// index of packed entry w in the list at adj + base (typed range search), -1 if absent
-__device__ __forceinline__ int find_pos(const uint32_t *__restrict__ adj, int64_t base,
-                                        const int32_t *__restrict__ to, uint32_t w) {
-    const int t = (int)(w >> TG_TSHIFT);
-    int lo = __ldg(to + t), hi = __ldg(to + t + 1);
-    const int end = hi;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(adj + base + mid) < w)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    return (lo < end && __ldg(adj + base + lo) == w) ? lo : -1;
-}
-
 __device__ __forceinline__ void hadd(const ReuseParams &p, unsigned long long *shist, int64_t x,
                                      unsigned long long v) {
     if (!v) return;
@@ -689,10 +673,17 @@ __global__ void __launch_bounds__(1024, 1) k_count_reuse(ReuseParams p) {
 // tg_last_timing).  One set per host thread, so counts run concurrently from
 // several threads (the serving loop's workers) neither reset nor mix each
 // other's counters.
+inline unsigned grid_r(int64_t n, int threads = 256) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 65535LL * 16) b = 65535LL * 16;
+    return (unsigned)b;
+}
+
 struct LastTiming {
     bool ready = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    unsigned long long *work = nullptr;  // device, 4 counters
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    unsigned long long *work = nullptr;  // device, kWorkCounters counters
     uint64_t edges = 0;
     ~LastTiming() {
         for (auto &e : ev)
@@ -701,15 +692,35 @@ struct LastTiming {
     }
 };
 thread_local LastTiming g_last;
+constexpr int kWorkCounters = 8;
 
 int timing_begin(cudaStream_t s, unsigned long long **work) {
     if (!g_last.ev[0]) {
         for (auto &e : g_last.ev) TG_TRY_CUDA(cudaEventCreate(&e));
-        TG_TRY_CUDA(cudaMalloc(&g_last.work, 4 * sizeof(unsigned long long)));
+        TG_TRY_CUDA(cudaMalloc(&g_last.work, kWorkCounters * sizeof(unsigned long long)));
     }
     g_last.ready = false;
-    TG_TRY_CUDA(cudaMemsetAsync(g_last.work, 0, 4 * sizeof(unsigned long long), s));
+    TG_TRY_CUDA(cudaMemsetAsync(g_last.work, 0, kWorkCounters * sizeof(unsigned long long), s));
     *work = g_last.work;
+    return TG_OK;
+}
+
+// Work units of the grouped order: runs of at most kTauUnit edges sharing j.
+int edge_units(const tg_graph *g, const uint32_t *ord, int64_t cnt, cudaStream_t s,
+               DevBuf<uint32_t> &ustart, uint32_t *nunits) {
+    DevBuf<uint32_t> flag, pos;
+    if (!flag.alloc(cnt, s) || !pos.alloc(cnt, s)) return TG_ENOMEM;
+    k_unit_flags<<<grid_r(cnt), 256, 0, s>>>(ord, g->edges, cnt, flag.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    TG_TRY(tg_scan_u32(flag.p, pos.p, cnt, s));
+    uint32_t lastp = 0, lastf = 0;
+    TG_TRY_CUDA(cudaMemcpyAsync(&lastp, pos.p + cnt - 1, 4, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaMemcpyAsync(&lastf, flag.p + cnt - 1, 4, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    *nunits = lastp + lastf;
+    if (!ustart.alloc((size_t)*nunits + 1, s)) return TG_ENOMEM;
+    k_unit_starts<<<grid_r(cnt), 256, 0, s>>>(flag.p, pos.p, cnt, ustart.p, *nunits); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
     return TG_OK;
 }
 
@@ -727,12 +738,6 @@ int smem_optin_r() {
     return v > 0 ? v : 48 * 1024;
 }
 
-inline unsigned grid_r(int64_t n, int threads = 256) {
-    int64_t b = (n + threads - 1) / threads;
-    if (b < 1) b = 1;
-    if (b > 65535LL * 16) b = 65535LL * 16;
-    return (unsigned)b;
-}
 
 template <int U>
 int launch_reuse_u(const ReuseParams &p, int threads, size_t smem, int grid_limit,
@@ -765,24 +770,13 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
     TG_TRY(timing_begin(s, &work));
     // tau for every edge of the graph (the identities need tau of edges
     // outside the counted range as well)
-    DevBuf<uint32_t> tau, theta, dsum, flag, pos, ustart;
+    DevBuf<uint32_t> tau, theta, dsum, ustart;
+    uint32_t nunits = 0;
     if (!tau.alloc((size_t)M * L, s)) return TG_ENOMEM;
     {
         // tau of every edge, in the grouped order of the whole graph
         const uint32_t *ord = full_order;
-        const int64_t cnt = M;
-        if (!flag.alloc(cnt, s) || !pos.alloc(cnt, s)) return TG_ENOMEM;
-        k_unit_flags<<<grid_r(cnt), 256, 0, s>>>(ord, g->edges, cnt, flag.p); tg_note_launch();
-        TG_TRY_CUDA(cudaGetLastError());
-        TG_TRY(tg_scan_u32(flag.p, pos.p, cnt, s));
-        uint32_t lastp = 0, lastf = 0;
-        TG_TRY_CUDA(cudaMemcpyAsync(&lastp, pos.p + cnt - 1, 4, cudaMemcpyDeviceToHost, s));
-        TG_TRY_CUDA(cudaMemcpyAsync(&lastf, flag.p + cnt - 1, 4, cudaMemcpyDeviceToHost, s));
-        TG_TRY_CUDA(cudaStreamSynchronize(s));
-        const uint32_t nunits = lastp + lastf;
-        if (!ustart.alloc((size_t)nunits + 1, s)) return TG_ENOMEM;
-        k_unit_starts<<<grid_r(cnt), 256, 0, s>>>(flag.p, pos.p, cnt, ustart.p, nunits); tg_note_launch();
-        TG_TRY_CUDA(cudaGetLastError());
+        TG_TRY(edge_units(g, ord, M, s, ustart, &nunits));
         DevBuf<unsigned long long> q;
         if (!q.alloc(1, s)) return TG_ENOMEM;
         TG_TRY_CUDA(cudaMemsetAsync(q.p, 0, 8, s));
@@ -798,7 +792,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
         TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tau, 512, smem));
         if (per_sm < 1) per_sm = 1;
         int64_t grid = (int64_t)num_sms_r() * per_sm;
-        if (grid > nunits) grid = nunits;
+        if (grid > (int64_t)nunits) grid = nunits;
         if (grid < 1) grid = 1;
         k_tau<<<(unsigned)grid, 512, smem, s>>>(g->rowptr, g->adj, g->toff, g->edges, ord,
                                                 ustart.p, nunits, L, nbits, q.p, tau.p); tg_note_launch();
@@ -812,6 +806,46 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
         TG_TRY_CUDA(cudaGetLastError());
     }
     TG_TRY_CUDA(cudaEventRecord(g_last.ev[2], s));
+    if (t.kernel == TG_KERNEL_CYCLES || t.kernel == TG_KERNEL_AUTO) {
+        // 4-cycles and 4-cliques per edge from whole-graph enumerations, then
+        // the per-edge identities (tg_cycles.cu)
+        DevBuf<unsigned long long> c4e, k4e, g4c, g4k;
+        // whole-graph global sums: the 4-cycle and 4-clique terms come from
+        // their type-multiset totals instead of per-edge counters
+        const bool fast = k == 4 && hist && !rows && order == full_order && count == M;
+        if (fast) {
+            const int64_t n4 = tg_binom(L + 3, 4);
+            if (!g4c.alloc(n4, s) || !g4k.alloc(n4, s)) return TG_ENOMEM;
+            TG_TRY_CUDA(cudaMemsetAsync(g4c.p, 0, n4 * 8, s));
+            TG_TRY_CUDA(cudaMemsetAsync(g4k.p, 0, n4 * 8, s));
+            TG_TRY(tg_cyc_cycles(g, nullptr, g4c.p, work, t, s));
+        } else if (k == 4) {
+            const int P = L * (L + 1) / 2;
+            if (!c4e.alloc((size_t)M * L2, s) || !k4e.alloc((size_t)M * P, s)) return TG_ENOMEM;
+            TG_TRY_CUDA(cudaMemsetAsync(c4e.p, 0, (size_t)M * L2 * 8, s));
+            TG_TRY_CUDA(cudaMemsetAsync(k4e.p, 0, (size_t)M * P * 8, s));
+            TG_TRY(tg_cyc_cycles(g, c4e.p, nullptr, work, t, s));
+        }
+        TG_TRY_CUDA(cudaEventRecord(g_last.ev[3], s));
+        if (k == 4) TG_TRY(tg_cyc_cliques(g, k4e.p, g4k.p, work, t, s));
+        TG_TRY_CUDA(cudaEventRecord(g_last.ev[4], s));
+        DevBuf<uint32_t> ust2;
+        const uint32_t *ust = ustart.p;
+        uint32_t nun = nunits;
+        if (order != full_order || count != M) {
+            TG_TRY(edge_units(g, order, count, s, ust2, &nun));
+            ust = ust2.p;
+        }
+        TG_TRY(tg_cyc_edges(g, k, level, order, ust, nun, rows, width, hist, tau.p, theta.p,
+                            dsum.p, c4e.p, k4e.p, work, t, s));
+        if (fast) TG_TRY(tg_cyc_correct(hist, L, g4c.p, g4k.p, s));
+        TG_TRY_CUDA(cudaEventRecord(g_last.ev[5], s));
+        g_last.edges = (uint64_t)count;
+        g_last.ready = true;
+        return TG_OK;
+    }
+    TG_TRY_CUDA(cudaEventRecord(g_last.ev[3], s));
+    TG_TRY_CUDA(cudaEventRecord(g_last.ev[4], s));
     DevBuf<unsigned long long> queue;
     if (!queue.alloc(1, s)) return TG_ENOMEM;
     TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
@@ -867,7 +901,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
         default: r = launch_reuse_u<2>(p, threads, smem, t.grid_limit, s); break;
     }
     if (r != TG_OK) return r;
-    TG_TRY_CUDA(cudaEventRecord(g_last.ev[3], s));
+    TG_TRY_CUDA(cudaEventRecord(g_last.ev[5], s));
     g_last.edges = (uint64_t)count;
     g_last.ready = true;
     return TG_OK;
@@ -876,20 +910,24 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
 extern "C" int tg_last_timing(tg_timing *out) {
     if (!out) return TG_EINVAL;
     if (!g_last.ready) return TG_ENOTFOUND;
-    TG_TRY_CUDA(cudaEventSynchronize(g_last.ev[3]));
-    float a = 0, b = 0, c = 0;
-    TG_TRY_CUDA(cudaEventElapsedTime(&a, g_last.ev[0], g_last.ev[1]));
-    TG_TRY_CUDA(cudaEventElapsedTime(&b, g_last.ev[1], g_last.ev[2]));
-    TG_TRY_CUDA(cudaEventElapsedTime(&c, g_last.ev[2], g_last.ev[3]));
-    unsigned long long w[4] = {0, 0, 0, 0};
+    TG_TRY_CUDA(cudaEventSynchronize(g_last.ev[5]));
+    float ms[5] = {0, 0, 0, 0, 0};
+    for (int q = 0; q < 5; ++q)
+        TG_TRY_CUDA(cudaEventElapsedTime(&ms[q], g_last.ev[q], g_last.ev[q + 1]));
+    unsigned long long w[kWorkCounters] = {};
     TG_TRY_CUDA(cudaMemcpy(w, g_last.work, sizeof(w), cudaMemcpyDeviceToHost));
-    out->tau_ms = a;
-    out->aggregate_ms = b;
-    out->count_ms = c;
+    out->tau_ms = ms[0];
+    out->aggregate_ms = ms[1];
+    out->cycles_ms = ms[2];
+    out->cliques_ms = ms[3];
+    out->count_ms = ms[4];
     out->edges = g_last.edges;
     out->gamma_entries = w[0];
     out->walked_entries = w[1];
     out->probe_pairs = w[2];
     out->t_members = w[3];
+    out->wedges = w[4];
+    out->clique_tests = w[5];
+    out->cliques = w[6];
     return TG_OK;
 }

@@ -9,11 +9,17 @@ from paper_1901_10026_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-# Kernel variants: the tuned defaults, the warp/binary-search kernel, and the
-# bitmap kernel squeezed so that its fallbacks (ids beyond the bitmap, lists
-# too long for the hash) carry most of the work.  Counts must not change.
+# Kernel variants: the tuned defaults (the cycles kernel), the warp/binary-
+# search kernel, the bitmap kernel and the reuse kernel, some squeezed so that
+# their fallbacks (ids beyond the bitmap, lists too long for the hash, 4-clique
+# candidate sets too large for shared memory) carry most of the work.  Counts
+# must not change.
 VARIANTS = {
     "default": dict(),
+    "cycles-small": dict(kernel=tg.TG_KERNEL_CYCLES, cta_threads=64, hash_slots=32, bitmap_bits=96,
+                         grid_limit=3, unroll=1),
+    "cycles-split": dict(kernel=tg.TG_KERNEL_CYCLES, unroll=4),
+    "reuse": dict(kernel=tg.TG_KERNEL_REUSE),
     "warp-search": dict(kernel=tg.TG_KERNEL_WARP_SEARCH),
     "cta-small": dict(kernel=tg.TG_KERNEL_CTA_BITMAP, cta_threads=128, unroll=1, hash_slots=32,
                       bitmap_bits=96),

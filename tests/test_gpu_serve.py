@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 import paper_1901_10026_gb300 as tg
+from oracle import o2
 from paper_1901_10026_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -20,6 +21,7 @@ def _built():
     from paper_1901_10026_gb300 import build
     build.build()
     oracle.build()
+    o2.build()
     torch.cuda.init()
 
 
@@ -48,7 +50,10 @@ def test_results_in_the_mix_equal_solo_counts():
     assert st["batched_launches"] >= 1 and st["grouped_requests"] >= 2  # small requests grouped
     assert st["peak_in_flight"] >= 2                                      # work overlapped
     assert st["p99_ms"] >= st["p50_ms"] > 0
-    # the smallest requests also against the oracle
+    # every request against the independent global oracle, the smallest also
+    # against the paper-method oracle
+    for G, want in zip(Gs, solo):
+        assert np.array_equal(o2.global_counts_of(G, 4), want), G.name
     for G, want in sorted(zip(Gs, solo), key=lambda x: x[0].m)[:4]:
         assert np.array_equal(oracle.OracleGraph.from_edges(G).global_counts(k=4), want)
 
