@@ -78,12 +78,14 @@ struct C4Params {
     int32_t L;
     int32_t tile;              // members staged per tile (<= blockDim.x)
     int32_t acc_l2;            // L * L in per-edge mode, 0 in global mode
-    uint32_t *scratch;         // counter slots of n * L, zero on entry and on exit
+    uint32_t *scratch;         // slots of n * (L + 1) counters (per type, then the total)
+                               // and an n-entry list of the far ends met; counters zero
+                               // on entry and on exit
     int64_t slot_words;
+    unsigned int *slot_nb;     // split kernel: far ends listed per slot of the wave
     unsigned long long *queue;
     unsigned long long *c4e;   // per-edge mode: M * L * L, [type next to i][type next to j]
-    unsigned long long *g4;    // global mode: C(L+3,4) sums over wedges of the cycles each
-                               // closes, by type multiset (twice the non-induced 4-cycles)
+    unsigned long long *g4;    // global mode: C(L+3,4) non-induced 4-cycles by type multiset
     int64_t n4;
     const uint8_t *split;      // one-CTA kernel: anchors marked here are skipped
     const int4 *units;         // split kernel: (slot, anchor, first list position, 0)
@@ -100,6 +102,7 @@ struct C4Smem {
     unsigned long long *acc;
     uint32_t *m_u, *m_e;
     unsigned long long *s_item, *h4;
+    unsigned int *s_nb;
 };
 
 __device__ __forceinline__ C4Smem c4_smem(unsigned char *smem, int TM, int acc_l2) {
@@ -111,20 +114,22 @@ __device__ __forceinline__ C4Smem c4_smem(unsigned char *smem, int TM, int acc_l
     m.m_u = reinterpret_cast<uint32_t *>(m.acc + (size_t)TM * acc_l2);
     m.m_e = m.m_u + TM;
     m.s_item = reinterpret_cast<unsigned long long *>(m.m_e + TM + (TM & 1));
+    m.s_nb = reinterpret_cast<unsigned int *>(m.s_item + 1);
     m.h4 = m.s_item + 2;  // global mode: n4 entries
     return m;
 }
 
 // One pass over one tile of anchor a's list: the members u (neighbours ranked
 // below a) of the tile and, for each, the entries b of u's list ranked below
-// a.  Pass 0 counts the middles per (b, type), pass 1 adds the closed cycles
-// (per edge, or by type multiset in global mode), pass 2 clears the counters.
-// Called by every thread of the CTA (it holds barriers).
+// a.  Pass 0 counts the middles per (b, type) and their total, and lists each
+// b the first time it is met (in `list`, count in *nb); pass 1 (per-edge mode
+// only) adds the cycles each wedge closes to its two edges.  Called by every
+// thread of the CTA (it holds barriers).
 __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta, int64_t ba,
-                        int da, int tile, int phase, uint32_t *cnt, unsigned long long &wk) {
+                        int da, int tile, int phase, uint32_t *cnt, uint32_t *list,
+                        unsigned int *nb, unsigned long long &wk) {
     const int tid = threadIdx.x;
     const int L = p.L, L2 = L * L, TM = p.tile;
-    const bool global = p.g4 != nullptr;
     const int x = tile + tid;
     bool mem = false;
     uint32_t wu = 0;
@@ -151,7 +156,7 @@ __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta,
         sm.m_u[r] = wu;
         sm.m_e[r] = __ldg(p.eid + ba + x);
     }
-    if (phase == 1 && !global)
+    if (phase == 1)
         for (int q = tid; q < nmem * L2; q += blockDim.x) sm.acc[q] = 0ull;
     __syncthreads();
     for (int64_t base = 0; base < total; base += blockDim.x) {
@@ -171,46 +176,18 @@ __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta,
         if (b <= a) continue;  // b must rank below a (and differ from it)
         const uint32_t wmu = sm.m_u[lo];
         const int tu = (int)(wmu >> TG_TSHIFT);
-        uint32_t *cb = cnt + (int64_t)b * L;
+        uint32_t *cb = cnt + (int64_t)b * (L + 1);
         if (phase == 0) {
             atomicAdd(cb + tu, 1u);
+            if (atomicAdd(cb + L, 1u) == 0u) list[atomicAdd(nb, 1u)] = b;
             ++wk;
             continue;
         }
-        if (phase == 2) {
-            cb[tu] = 0u;
-            continue;
-        }
+        if (__ldcg(cb + L) < 2u) continue;  // no other middle: no cycle
         uint32_t c[TG_MAX_TYPES];
-        uint32_t sum = 0;
 #pragma unroll
-        for (int t = 0; t < TG_MAX_TYPES; ++t) {
-            c[t] = t < L ? __ldcg(cb + t) : 0u;
-            sum += c[t];
-        }
-        if (sum < 2) continue;  // no other middle: no cycle
+        for (int t = 0; t < TG_MAX_TYPES; ++t) c[t] = t < L ? __ldcg(cb + t) : 0u;
         const int tb = (int)(wb >> TG_TSHIFT);
-        if (global) {
-            // cycles a-u-b-u' by the multiset {a, b, u, u'}
-            int s0 = ta, s1 = tb, s2 = tu;
-            sort2(s0, s1);
-            sort2(s1, s2);
-            sort2(s0, s1);
-#pragma unroll
-            for (int t = 0; t < TG_MAX_TYPES; ++t) {
-                if (t < L) {
-                    const uint32_t v = c[t] - (t == tu ? 1u : 0u);
-                    if (v) {
-                        int q0 = s0, q1 = s1, q2 = s2, q3 = t;
-                        sort2(q2, q3);
-                        sort2(q1, q2);
-                        sort2(q0, q1);
-                        atomicAdd(sm.h4 + colex4(q0, q1, q2, q3), (unsigned long long)v);
-                    }
-                }
-            }
-            continue;
-        }
         const uint32_t u = wmu & TG_IDMASK;
         unsigned long long *row_ub = p.c4e + (int64_t)__ldg(p.eid + at) * L2;
         unsigned long long *row_au = sm.acc + (int64_t)lo * L2 + tb * L;
@@ -229,12 +206,49 @@ __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta,
         }
     }
     __syncthreads();
-    if (phase == 1 && !global) {
+    if (phase == 1) {
         for (int q = tid; q < nmem * L2; q += blockDim.x) {
             const unsigned long long v = sm.acc[q];
             if (v) atomicAdd(p.c4e + (int64_t)sm.m_e[q / L2] * L2 + (q % L2), v);
         }
         __syncthreads();
+    }
+}
+
+// For the listed far ends b of anchor a (entries q0, q0 + step, ... < nb):
+// global mode adds the cycles per type pair of middles (C(c_t, 2) for t = t',
+// c_t c_t' for t < t') under the multiset {a, b, t, t'}; both modes then clear
+// b's counters.
+__device__ __forceinline__ void c4_pairs(const C4Params &p, const C4Smem &sm, int ta,
+                                         uint32_t *cnt, const uint32_t *list, unsigned int nb,
+                                         unsigned int q0, unsigned int step) {
+    const int L = p.L;
+    for (unsigned int q = q0; q < nb; q += step) {
+        const uint32_t b = __ldcg(list + q);  // written by other threads this anchor
+        uint32_t *cb = cnt + (int64_t)b * (L + 1);
+        if (p.g4 && __ldcg(cb + L) >= 2u) {
+            const int tb = p.ntype[b];
+            uint32_t c[TG_MAX_TYPES];
+#pragma unroll
+            for (int t = 0; t < TG_MAX_TYPES; ++t) c[t] = t < L ? __ldcg(cb + t) : 0u;
+            int s0 = ta, s1 = tb;
+            sort2(s0, s1);
+            for (int t = 0; t < L; ++t) {
+                if (!c[t]) continue;
+                for (int u = t; u < L; ++u) {
+                    const unsigned long long v =
+                        u == t ? (unsigned long long)c[t] * (c[t] - 1) / 2
+                               : (unsigned long long)c[t] * c[u];
+                    if (!v) continue;
+                    int q0s = s0, q1s = s1, q2s = t, q3s = u;
+                    sort2(q0s, q2s);
+                    sort2(q1s, q3s);
+                    sort2(q1s, q2s);
+                    atomicAdd(sm.h4 + colex4(q0s, q1s, q2s, q3s), v);
+                }
+            }
+        }
+        for (int t = 0; t <= L; ++t) cb[t] = 0u;
     }
 }
 
@@ -257,6 +271,7 @@ __global__ void __launch_bounds__(kC4Threads) k_c4(C4Params p) {
     if (p.g4)
         for (int64_t q = tid; q < p.n4; q += blockDim.x) sm.h4[q] = 0ull;
     uint32_t *cnt = p.scratch + (int64_t)blockIdx.x * p.slot_words;
+    uint32_t *list = cnt + p.n * (p.L + 1);
     unsigned long long wk = 0;
     for (;;) {
         __syncthreads();
@@ -270,9 +285,15 @@ __global__ void __launch_bounds__(kC4Threads) k_c4(C4Params p) {
         const int da = (int)(p.rowptr[a + 1] - ba);
         if (da < 2) continue;  // a cycle through a needs two of its neighbours
         const int ta = p.ntype[a];
-        for (int phase = 0; phase < 3; ++phase)
+        if (tid == 0) *sm.s_nb = 0u;
+        __syncthreads();
+        for (int tile = 0; tile < da; tile += p.tile)
+            c4_tile(p, sm, a, ta, ba, da, tile, 0, cnt, list, sm.s_nb, wk);
+        if (!p.g4)
             for (int tile = 0; tile < da; tile += p.tile)
-                c4_tile(p, sm, a, ta, ba, da, tile, phase, cnt, wk);
+                c4_tile(p, sm, a, ta, ba, da, tile, 1, cnt, list, sm.s_nb, wk);
+        __syncthreads();
+        c4_pairs(p, sm, ta, cnt, list, *sm.s_nb, tid, blockDim.x);
     }
     c4_finish(p, sm, wk);
 }
@@ -297,10 +318,27 @@ __global__ void __launch_bounds__(kC4Threads) k_c4_split(C4Params p) {
         const uint32_t a = (uint32_t)un.y;
         const int64_t ba = p.rowptr[a];
         const int da = (int)(p.rowptr[a + 1] - ba);
-        c4_tile(p, sm, a, p.ntype[a], ba, da, un.z, p.phase,
-                p.scratch + (int64_t)un.x * p.slot_words, wk);
+        uint32_t *cnt = p.scratch + (int64_t)un.x * p.slot_words;
+        c4_tile(p, sm, a, p.ntype[a], ba, da, un.z, p.phase, cnt, cnt + p.n * (p.L + 1),
+                p.slot_nb + un.x, wk);
     }
     c4_finish(p, sm, wk);
+}
+
+// The listed far ends of the wave's split anchors: blockIdx.y is the slot,
+// anchors[slot] its anchor; blockIdx.x strides through the slot's list.
+__global__ void __launch_bounds__(kC4Threads) k_c4_pairs(C4Params p, const uint32_t *anchors) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const C4Smem sm = c4_smem(smem, p.tile, p.acc_l2);
+    if (p.g4) {
+        for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x) sm.h4[q] = 0ull;
+        __syncthreads();
+    }
+    const int slot = blockIdx.y;
+    uint32_t *cnt = p.scratch + (int64_t)slot * p.slot_words;
+    c4_pairs(p, sm, p.ntype[anchors[slot]], cnt, cnt + p.n * (p.L + 1), p.slot_nb[slot],
+             blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    c4_finish(p, sm, 0ull);
 }
 
 // Walk cost of each anchor (sum of d_u over its neighbours u ranked below it)
@@ -643,15 +681,15 @@ __global__ void __launch_bounds__(kK4Warps * 32) k_k4(K4Params p) {
 // through the type-multiset totals of 4-cliques K4 and of non-induced
 // 4-cycles N_C4; added here to the undivided sums of h3..h8:
 //   h3 -12 N_C4 - 36 K4, h4 -12 K4, h5 +4 N_C4 + 12 K4, h6 +48 K4,
-//   h7 -30 K4, h8 +6 K4.   (c4w = 2 N_C4, k4 = K4; arithmetic mod 2^64.)
+//   h7 -30 K4, h8 +6 K4.   (c4 = N_C4, k4 = K4; arithmetic mod 2^64.)
 __global__ void k_cyc_correct(unsigned long long *hist, int64_t off4, int64_t n4,
-                              const unsigned long long *c4w, const unsigned long long *k4) {
+                              const unsigned long long *c4, const unsigned long long *k4) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n4;
          r += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long w = c4w[r], k = k4[r];
-        hist[off4 + 0 * n4 + r] += (unsigned long long)(-6ll) * w + (unsigned long long)(-36ll) * k;
+        const unsigned long long w = c4[r], k = k4[r];
+        hist[off4 + 0 * n4 + r] += (unsigned long long)(-12ll) * w + (unsigned long long)(-36ll) * k;
         hist[off4 + 1 * n4 + r] += (unsigned long long)(-12ll) * k;
-        hist[off4 + 2 * n4 + r] += 2ull * w + 12ull * k;
+        hist[off4 + 2 * n4 + r] += 4ull * w + 12ull * k;
         hist[off4 + 3 * n4 + r] += 48ull * k;
         hist[off4 + 4 * n4 + r] += (unsigned long long)(-30ll) * k;
         hist[off4 + 5 * n4 + r] += 6ull * k;
@@ -1041,6 +1079,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     const size_t smem = (size_t)TM * per_member + fixed;
     TG_TRY(tg_allow_max_smem((const void *)k_c4));
     TG_TRY(tg_allow_max_smem((const void *)k_c4_split));
+    TG_TRY(tg_allow_max_smem((const void *)k_c4_pairs));
     int per_sm = 0;
     TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c4, kC4Threads, smem));
     if (per_sm < 1) per_sm = 1;
@@ -1093,7 +1132,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
 
     // counter slots: one per CTA of the one-CTA kernel, one per split anchor of
     // a wave; all within a quarter of free memory
-    const int64_t slot_words = n * L;
+    const int64_t slot_words = n * (L + 2);
     const size_t slot_bytes = (size_t)slot_words * 4;
     size_t free_b = 0, total_b = 0;
     TG_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
@@ -1104,9 +1143,12 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
         if (slot_bytes > free_b / 2) return TG_ENOMEM;
         slots = 1;
     }
-    DevBuf<uint32_t> scratch;
+    DevBuf<uint32_t> scratch, wave_anchor;
+    DevBuf<unsigned int> slot_nb;
     DevBuf<unsigned long long> queue;
-    if (!scratch.alloc((size_t)slots * slot_words, s) || !queue.alloc(1, s)) return TG_ENOMEM;
+    if (!scratch.alloc((size_t)slots * slot_words, s) || !queue.alloc(1, s) ||
+        !slot_nb.alloc(slots, s))
+        return TG_ENOMEM;
     TG_TRY_CUDA(cudaMemsetAsync(scratch.p, 0, (size_t)slots * slot_bytes, s));
     C4Params p{};
     p.rowptr = g->rowptr;
@@ -1124,6 +1166,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     p.g4 = g4;
     p.n4 = n4;
     p.split = split.p;
+    p.slot_nb = slot_nb.p;
     p.work = work;
 
     // split anchors, in waves of at most `slots` anchors
@@ -1138,20 +1181,27 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
         }
         wave_start.push_back((int64_t)units.size());
         DevBuf<int4> du;
-        if (!du.alloc(units.size(), s)) return TG_ENOMEM;
+        if (!du.alloc(units.size(), s) || !wave_anchor.alloc(nheavy, s)) return TG_ENOMEM;
         TG_TRY_CUDA(cudaMemcpyAsync(du.p, units.data(), units.size() * sizeof(int4),
+                                    cudaMemcpyHostToDevice, s));
+        TG_TRY_CUDA(cudaMemcpyAsync(wave_anchor.p, heavy.data(), nheavy * 4,
                                     cudaMemcpyHostToDevice, s));
         for (size_t w = 0; w + 1 < wave_start.size(); ++w) {
             const int64_t u0 = wave_start[w], nu = wave_start[w + 1] - u0;
+            const int64_t a0 = (int64_t)w * slots, na = std::min<int64_t>(slots, nheavy - a0);
             p.units = du.p + u0;
             p.n_units = nu;
-            int64_t grid = std::min<int64_t>(full_grid, nu);
-            for (int ph = 0; ph < 3; ++ph) {
+            const int64_t grid = std::min<int64_t>(full_grid, nu);
+            TG_TRY_CUDA(cudaMemsetAsync(slot_nb.p, 0, (size_t)na * sizeof(unsigned int), s));
+            for (int ph = 0; ph < (global ? 1 : 2); ++ph) {
                 p.phase = ph;
                 TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
                 k_c4_split<<<(unsigned)grid, kC4Threads, smem, s>>>(p); tg_note_launch();
                 TG_TRY_CUDA(cudaGetLastError());
             }
+            const dim3 pg((unsigned)std::max<int64_t>(1, full_grid / na), (unsigned)na);
+            k_c4_pairs<<<pg, kC4Threads, smem, s>>>(p, wave_anchor.p + a0); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
         }
         // the host vectors are read by the copy above before they go out of scope
         TG_TRY_CUDA(cudaStreamSynchronize(s));

@@ -139,8 +139,8 @@ int tg_free_graph_on(tg_graph *g, cudaStream_t s);
 // Whole-graph enumerations and the per-edge pass of the cycles kernel
 // (tg_cycles.cu).  Per-edge mode: c4e holds M x L x L and k4e M x L(L+1)/2
 // zeroed counters (g4 = NULL).  Global mode (c4e / k4e = NULL): g4 gets, by
-// type multiset (C(L+3,4) zeroed entries), twice the non-induced 4-cycles
-// (cycles) or the 4-cliques (cliques); tg_cyc_correct then adds their share
+// type multiset (C(L+3,4) zeroed entries), the non-induced 4-cycles (cycles)
+// or the 4-cliques (cliques); tg_cyc_correct then adds their share
 // to undivided sums counted with Q = C4 = 0.
 int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long *g4,
                   unsigned long long *work, const tg_tune &t, cudaStream_t s);
