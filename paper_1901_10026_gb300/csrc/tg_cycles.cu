@@ -676,6 +676,210 @@ __global__ void __launch_bounds__(kK4Warps * 32) k_k4(K4Params p) {
     }
 }
 
+// Per-warp hash sets of node ids in shared memory (open addressing, linear
+// probing, id + 1 stored, 0 empty).  Reads are volatile: the table is written
+// by other lanes of the warp between a __syncwarp and the reads.
+__device__ __forceinline__ uint32_t hset_slot(uint32_t id, int lg) {
+    return (id * 0x9E3779B1u) >> (32 - lg);
+}
+__device__ __forceinline__ void hset_put(uint32_t *tab, int lg, uint32_t id) {
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = hset_slot(id, lg);
+    for (int probe = 0; probe < (1 << lg); ++probe) {
+        const uint32_t old = atomicCAS(tab + h, 0u, id + 1u);
+        if (old == 0u || old == id + 1u) return;
+        h = (h + 1u) & mask;
+    }
+}
+__device__ __forceinline__ bool hset_has(const uint32_t *tab, int lg, uint32_t id) {
+    const uint32_t mask = (1u << lg) - 1u;
+    const volatile uint32_t *t = tab;
+    uint32_t h = hset_slot(id, lg);
+    for (int probe = 0; probe < (1 << lg); ++probe) {
+        const uint32_t k = t[h];
+        if (k == id + 1u) return true;
+        if (k == 0u) return false;
+        h = (h + 1u) & mask;
+    }
+    return false;
+}
+
+// 4-cliques by type multiset only (global mode).  As k_k4, one warp per
+// lowest node x0; membership in up(x0) and in W = up(v) n up(x0) is a probe
+// of a per-warp hash set when the set fits (cap entries), else a search of
+// the sorted up lists.
+struct K4GParams {
+    const int64_t *uoff;
+    const uint32_t *uadj;
+    const int32_t *utoff;
+    const uint8_t *ntype;
+    int64_t n;
+    int32_t L;
+    int32_t cap;  // set entries per warp (tables of 2^hlg >= 2 cap slots)
+    int32_t hlg;
+    unsigned long long *queue;
+    unsigned long long *g4;
+    int64_t n4;
+    unsigned long long *work;
+};
+
+constexpr int kK4GWarps = 8;
+
+__global__ void __launch_bounds__(kK4GWarps * 32) k_k4_global(K4GParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int L = p.L, cap = p.cap, tsz = 1 << p.hlg;
+    unsigned long long *h4 = reinterpret_cast<unsigned long long *>(smem);
+    const size_t h4b = ((size_t)p.n4 * 8 + 15) & ~(size_t)15;
+    uint32_t *went = reinterpret_cast<uint32_t *>(smem + h4b) + (size_t)warp * (cap + 2 * tsz);
+    uint32_t *hx = went + cap;
+    uint32_t *hw = hx + tsz;
+    for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x) h4[q] = 0ull;
+    __syncthreads();
+    const uint32_t below = (1u << lane) - 1u;
+    unsigned long long wk_cand = 0, wk_k4 = 0;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(p.queue, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= (unsigned long long)p.n) break;
+        const uint32_t x0 = (uint32_t)item;
+        const int64_t b0 = p.uoff[x0];
+        const int d0 = (int)(p.uoff[x0 + 1] - b0);
+        if (d0 < 3) continue;  // x0 is the lowest node: three more above it
+        const int t0 = p.ntype[x0];
+        const int32_t *to0 = p.utoff + (int64_t)x0 * (L + 1);
+        const bool xh = d0 <= cap;
+        int lgx = 5;
+        while ((1 << lgx) < 2 * d0 && lgx < p.hlg) ++lgx;
+        if (xh) {
+            for (int q = lane; q < (1 << lgx); q += 32) hx[q] = 0u;
+            __syncwarp();
+            for (int q = lane; q < d0; q += 32) hset_put(hx, lgx, __ldg(p.uadj + b0 + q) & TG_IDMASK);
+            __syncwarp();
+        }
+        for (int c0 = 0; c0 < d0; c0 += 32) {
+            const uint32_t ev = c0 + lane < d0 ? __ldg(p.uadj + b0 + c0 + lane) : 0u;
+            unsigned upm = __ballot_sync(kFull, c0 + lane < d0);
+            while (upm) {
+                const int src = __ffs(upm) - 1;
+                upm &= upm - 1;
+                const uint32_t vent = __shfl_sync(kFull, ev, src);
+                const uint32_t v = vent & TG_IDMASK;
+                const int tv = (int)(vent >> TG_TSHIFT);
+                const int64_t bv = p.uoff[v];
+                const int dv = (int)(p.uoff[v + 1] - bv);
+                const int32_t *tov = p.utoff + (int64_t)v * (L + 1);
+                // W = up(v) n up(x0)
+                int nw = 0;
+                for (int c1 = 0; c1 < dv; c1 += 32) {
+                    const int q = c1 + lane;
+                    bool ok = false;
+                    uint32_t wq = 0;
+                    if (q < dv) {
+                        wq = __ldg(p.uadj + bv + q);
+                        ok = xh ? hset_has(hx, lgx, wq & TG_IDMASK) : find_pos(p.uadj, b0, to0, wq) >= 0;
+                    }
+                    const unsigned m = __ballot_sync(kFull, ok);
+                    const int r = nw + __popc(m & below);
+                    if (ok && r < cap) went[r] = wq;
+                    nw += __popc(m);
+                }
+                if (nw < 2) {
+                    __syncwarp();
+                    continue;
+                }
+                const bool staged = nw <= cap;
+                int lgw = 5;
+                while ((1 << lgw) < 2 * nw && lgw < p.hlg) ++lgw;
+                if (staged) {
+                    for (int q = lane; q < (1 << lgw); q += 32) hw[q] = 0u;
+                    __syncwarp();
+                    for (int q = lane; q < nw; q += 32) hset_put(hw, lgw, went[q] & TG_IDMASK);
+                }
+                __syncwarp();
+                for (int c1 = 0, k = 0; staged ? k < nw : c1 < dv;) {
+                    unsigned wm;
+                    uint32_t wlane = 0;
+                    if (staged) {
+                        wm = 1u;
+                    } else {
+                        const int q = c1 + lane;
+                        bool ok = false;
+                        if (q < dv) {
+                            wlane = __ldg(p.uadj + bv + q);
+                            ok = xh ? hset_has(hx, lgx, wlane & TG_IDMASK)
+                                    : find_pos(p.uadj, b0, to0, wlane) >= 0;
+                        }
+                        wm = __ballot_sync(kFull, ok);
+                    }
+                    while (wm) {
+                        const int sl = __ffs(wm) - 1;
+                        wm &= wm - 1;
+                        const uint32_t went_k = staged ? went[k] : __shfl_sync(kFull, wlane, sl);
+                        const uint32_t w = went_k & TG_IDMASK;
+                        const int tw = (int)(went_k >> TG_TSHIFT);
+                        const int64_t bw = p.uoff[w];
+                        const int dw = (int)(p.uoff[w + 1] - bw);
+                        int s0 = t0, s1 = tv, s2 = tw;
+                        sort2(s0, s1);
+                        sort2(s1, s2);
+                        sort2(s0, s1);
+                        for (int c2 = 0; c2 < dw; c2 += 32) {
+                            const int r = c2 + lane;
+                            int key = -1;
+                            if (r < dw) {
+                                const uint32_t xe = __ldg(p.uadj + bw + r);
+                                ++wk_cand;
+                                bool in;
+                                if (staged) {
+                                    in = hset_has(hw, lgw, xe & TG_IDMASK);
+                                } else {
+                                    in = (xh ? hset_has(hx, lgx, xe & TG_IDMASK)
+                                             : find_pos(p.uadj, b0, to0, xe) >= 0) &&
+                                         find_pos(p.uadj, bv, tov, xe) >= 0;
+                                }
+                                if (in) {
+                                    key = (int)(xe >> TG_TSHIFT);
+                                    ++wk_k4;
+                                }
+                            }
+                            const unsigned mm = __match_any_sync(kFull, key);
+                            if (key >= 0 && lane == __ffs(mm) - 1) {
+                                int q0 = s0, q1 = s1, q2 = s2, q3 = key;
+                                sort2(q2, q3);
+                                sort2(q1, q2);
+                                sort2(q0, q1);
+                                atomicAdd(h4 + colex4(q0, q1, q2, q3), (unsigned long long)__popc(mm));
+                            }
+                        }
+                        if (staged) ++k;
+                    }
+                    if (!staged) c1 += 32;
+                }
+                __syncwarp();
+            }
+        }
+    }
+    __syncthreads();
+    for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x)
+        if (h4[q]) atomicAdd(p.g4 + q, h4[q]);
+    if (p.work) {
+        if (wk_cand) atomicAdd(p.work + 5, wk_cand);
+        if (wk_k4) atomicAdd(p.work + 6, wk_k4);
+    }
+}
+
+__global__ void k_max_i64(const int64_t *x, int64_t n, unsigned long long *mx) {
+    unsigned long long m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)x[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, m);
+}
+
 // Global mode: the per-edge pass ran with Q = C4 = 0.  Summed over the edges,
 // Q and C4 enter the graphlet sums (each identity is linear in them) only
 // through the type-multiset totals of 4-cliques K4 and of non-induced
@@ -1259,6 +1463,54 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
     DevBuf<unsigned long long> queue;
     if (!queue.alloc(1, s)) return TG_ENOMEM;
     TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
+    if (global) {
+        // hash sets sized to the largest up list, within the hash_slots cap
+        DevBuf<unsigned long long> mx;
+        if (!mx.alloc(1, s)) return TG_ENOMEM;
+        TG_TRY_CUDA(cudaMemsetAsync(mx.p, 0, 8, s));
+        k_max_i64<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(utot.p, n, mx.p); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+        unsigned long long maxup = 0;
+        TG_TRY_CUDA(cudaMemcpyAsync(&maxup, mx.p, 8, cudaMemcpyDeviceToHost, s));
+        TG_TRY_CUDA(cudaStreamSynchronize(s));
+        int gcap = (int)std::min<unsigned long long>(std::min(1024, t.hash_slots), (maxup + 31) & ~31ull);
+        if (gcap < 32) gcap = 32;
+        int hlg = 5;
+        while ((1 << hlg) < 2 * gcap) ++hlg;
+        const size_t h4b = ((size_t)n4 * 8 + 15) & ~(size_t)15;
+        size_t gsmem = h4b + (size_t)kK4GWarps * (gcap + 2 * (1 << hlg)) * 4;
+        while (gsmem > avail + hbytes && gcap > 32) {
+            gcap -= 32;
+            hlg = 5;
+            while ((1 << hlg) < 2 * gcap) ++hlg;
+            gsmem = h4b + (size_t)kK4GWarps * (gcap + 2 * (1 << hlg)) * 4;
+        }
+        TG_TRY(tg_allow_max_smem((const void *)k_k4_global));
+        int gper = 0;
+        TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gper, k_k4_global,
+                                                                  kK4GWarps * 32, gsmem));
+        if (gper < 1) gper = 1;
+        int64_t ggrid = (int64_t)num_sms_c() * gper;
+        const int64_t gneed = (n + kK4GWarps - 1) / kK4GWarps;
+        if (ggrid > gneed) ggrid = gneed;
+        if (ggrid < 1) ggrid = 1;
+        K4GParams q{};
+        q.uoff = uoff.p;
+        q.uadj = uadj.p;
+        q.utoff = utoff.p;
+        q.ntype = g->ntype;
+        q.n = n;
+        q.L = L;
+        q.cap = gcap;
+        q.hlg = hlg;
+        q.queue = queue.p;
+        q.g4 = g4;
+        q.n4 = n4;
+        q.work = work;
+        k_k4_global<<<(unsigned)ggrid, kK4GWarps * 32, gsmem, s>>>(q); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+        return TG_OK;
+    }
     K4Params p{};
     p.uoff = uoff.p;
     p.uadj = uadj.p;
