@@ -918,6 +918,7 @@ struct EdgeParams {
     const unsigned long long *k4e;
     int32_t L, P, k, level;
     int64_t nbits;
+    uint32_t *emap;            // per CTA, nbits entries: edge id of (j, y) for y in Gamma_j
     unsigned long long *queue;
     uint64_t *rows;
     int64_t width;
@@ -1056,6 +1057,7 @@ __global__ void __launch_bounds__(kEdgeMaxThreads) k_cyc_edge(EdgeParams p) {
     off += 16;
     uint32_t *bm = reinterpret_cast<uint32_t *>(smem + off);
     const int64_t bwords = (p.nbits + 31) >> 5;
+    uint32_t *emap = p.emap + (int64_t)blockIdx.x * p.nbits;
     for (int64_t x = tid; x < bwords; x += blockDim.x) bm[x] = 0u;
     if (p.hist_smem)
         for (int64_t x = tid; x < p.hist_len; x += blockDim.x) shist[x] = 0;
@@ -1085,7 +1087,10 @@ __global__ void __launch_bounds__(kEdgeMaxThreads) k_cyc_edge(EdgeParams p) {
             __syncthreads();
             for (int x = tid; x < dj; x += blockDim.x) {
                 const uint32_t id = __ldg(adj + bj + x) & TG_IDMASK;
-                if ((int64_t)id < p.nbits) atomicOr(&bm[id >> 5], 1u << (id & 31u));
+                if ((int64_t)id < p.nbits) {
+                    atomicOr(&bm[id >> 5], 1u << (id & 31u));
+                    emap[id] = __ldg(p.eid + bj + x);
+                }
             }
             cur_j = j;
             cur_bj = bj;
@@ -1123,10 +1128,17 @@ __global__ void __launch_bounds__(kEdgeMaxThreads) k_cyc_edge(EdgeParams p) {
                     const uint32_t *tiy = p.tau, *tjy = p.tau;
                     const int32_t *ty = p.toff;
                     if (isT) {
+                        const uint32_t yid = w & TG_IDMASK;
                         tiy = p.tau + (int64_t)__ldg(p.eid + bi + x) * L;
-                        const int pj = find_pos(adj, bj, toj, w);
-                        tjy = p.tau + (int64_t)__ldg(p.eid + bj + (pj < 0 ? 0 : pj)) * L;
-                        ty = p.toff + (int64_t)(w & TG_IDMASK) * (L + 1);
+                        uint32_t ejy;
+                        if ((int64_t)yid < p.nbits) {
+                            ejy = __ldcg(emap + yid);  // written for this j before the barrier
+                        } else {
+                            const int pj = find_pos(adj, bj, toj, w);
+                            ejy = __ldg(p.eid + bj + (pj < 0 ? 0 : pj));
+                        }
+                        tjy = p.tau + (int64_t)ejy * L;
+                        ty = p.toff + (int64_t)yid * (L + 1);
                     }
                     int prev = isT ? __ldg(ty) : 0;
                     for (int b = 0; b < L; ++b) {
@@ -1600,6 +1612,9 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order,
     if (grid > nunits) grid = nunits;
     if (t.grid_limit > 0 && grid > t.grid_limit) grid = t.grid_limit;
     if (grid < 1) grid = 1;
+    DevBuf<uint32_t> emap;
+    if (!emap.alloc((size_t)std::max<int64_t>(1, grid * nbits), s)) return TG_ENOMEM;
+    p.emap = emap.p;
     k_cyc_edge<<<(unsigned)grid, threads, smem, s>>>(p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     return TG_OK;
