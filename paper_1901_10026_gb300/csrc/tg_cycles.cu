@@ -325,19 +325,41 @@ __global__ void __launch_bounds__(kC4Threads) k_c4_split(C4Params p) {
     c4_finish(p, sm, wk);
 }
 
-// The listed far ends of the wave's split anchors: blockIdx.y is the slot,
-// anchors[slot] its anchor; blockIdx.x strides through the slot's list.
-__global__ void __launch_bounds__(kC4Threads) k_c4_pairs(C4Params p, const uint32_t *anchors) {
+// The listed far ends of the wave's split anchors (na slots, anchors[slot]
+// the anchor of a slot): one grid-stride over the concatenated lists, so a
+// long list is shared by every CTA.
+__global__ void __launch_bounds__(kC4Threads) k_c4_pairs(C4Params p, const uint32_t *anchors,
+                                                         int na) {
     extern __shared__ __align__(16) unsigned char smem[];
     const C4Smem sm = c4_smem(smem, p.tile, p.acc_l2);
-    if (p.g4) {
-        for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x) sm.h4[q] = 0ull;
-        __syncthreads();
+    // inclusive prefix of the list lengths, in the member arrays of the smem
+    unsigned long long *pre = reinterpret_cast<unsigned long long *>(sm.m_end);
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int q = 0; q < na; ++q) {
+            run += p.slot_nb[q];
+            pre[q] = run;
+        }
     }
-    const int slot = blockIdx.y;
-    uint32_t *cnt = p.scratch + (int64_t)slot * p.slot_words;
-    c4_pairs(p, sm, p.ntype[anchors[slot]], cnt, cnt + p.n * (p.L + 1), p.slot_nb[slot],
-             blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+    if (p.g4)
+        for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x) sm.h4[q] = 0ull;
+    __syncthreads();
+    const unsigned long long total = pre[na - 1];
+    const int L = p.L;
+    for (unsigned long long g = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; g < total;
+         g += (unsigned long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = na - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (pre[mid] > g)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        const unsigned int q = (unsigned int)(g - (lo ? pre[lo - 1] : 0ull));
+        uint32_t *cnt = p.scratch + (int64_t)lo * p.slot_words;
+        c4_pairs(p, sm, p.ntype[anchors[lo]], cnt, cnt + p.n * (L + 1), q + 1, q, 1);
+    }
     c4_finish(p, sm, 0ull);
 }
 
@@ -704,16 +726,19 @@ __device__ __forceinline__ bool hset_has(const uint32_t *tab, int lg, uint32_t i
     return false;
 }
 
-// 4-cliques by type multiset only (global mode).  As k_k4, one warp per
-// lowest node x0; membership in up(x0) and in W = up(v) n up(x0) is a probe
-// of a per-warp hash set when the set fits (cap entries), else a search of
-// the sorted up lists.
+// 4-cliques by type multiset only (global mode).  As k_k4, each clique is met
+// from its lowest node x0 and the next one v; here a warp's work item is a
+// run of kK4GChunk oriented edges (x0, v) of the up lists, so the edges of a
+// costly x0 spread over many warps.  Membership in up(x0) and in
+// W = up(v) n up(x0) is a probe of a per-warp hash set when the set fits (cap
+// entries), else a search of the sorted up lists.
 struct K4GParams {
     const int64_t *uoff;
     const uint32_t *uadj;
     const int32_t *utoff;
     const uint8_t *ntype;
     int64_t n;
+    int64_t m;  // entries of the up lists (edges)
     int32_t L;
     int32_t cap;  // set entries per warp (tables of 2^hlg >= 2 cap slots)
     int32_t hlg;
@@ -724,6 +749,7 @@ struct K4GParams {
 };
 
 constexpr int kK4GWarps = 8;
+constexpr int kK4GChunk = 8;  // oriented edges (x0, v) per work item
 
 __global__ void __launch_bounds__(kK4GWarps * 32) k_k4_global(K4GParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -738,33 +764,53 @@ __global__ void __launch_bounds__(kK4GWarps * 32) k_k4_global(K4GParams p) {
     __syncthreads();
     const uint32_t below = (1u << lane) - 1u;
     unsigned long long wk_cand = 0, wk_k4 = 0;
+    const int64_t nchunks = (p.m + kK4GChunk - 1) / kK4GChunk;
+    int64_t cur = -1;  // x0 whose up list the hash set hx holds
+    int lgx = 5;
+    bool xh = false;
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(p.queue, 1ull);
         item = __shfl_sync(kFull, item, 0);
-        if (item >= (unsigned long long)p.n) break;
-        const uint32_t x0 = (uint32_t)item;
-        const int64_t b0 = p.uoff[x0];
-        const int d0 = (int)(p.uoff[x0 + 1] - b0);
+        if (item >= (unsigned long long)nchunks) break;
+        // the chunk's oriented edges (x0, v): positions q of the up lists
+        const int64_t q0 = (int64_t)item * kK4GChunk;
+        const int64_t q1 = min(p.m, q0 + kK4GChunk);
+        int64_t x0 = 0;
+        {
+            int64_t lo = 0, hi = p.n - 1;  // last x0 with uoff[x0] <= q0
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(p.uoff + mid) <= q0)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            x0 = lo;
+        }
+        for (int64_t qq = q0; qq < q1; ++qq) {
+        while (__ldg(p.uoff + x0 + 1) <= qq) ++x0;
+        const int64_t b0 = __ldg(p.uoff + x0);
+        const int d0 = (int)(__ldg(p.uoff + x0 + 1) - b0);
         if (d0 < 3) continue;  // x0 is the lowest node: three more above it
         const int t0 = p.ntype[x0];
-        const int32_t *to0 = p.utoff + (int64_t)x0 * (L + 1);
-        const bool xh = d0 <= cap;
-        int lgx = 5;
-        while ((1 << lgx) < 2 * d0 && lgx < p.hlg) ++lgx;
-        if (xh) {
-            for (int q = lane; q < (1 << lgx); q += 32) hx[q] = 0u;
+        const int32_t *to0 = p.utoff + x0 * (L + 1);
+        if (x0 != cur) {
+            cur = x0;
+            xh = d0 <= cap;
+            lgx = 5;
+            while ((1 << lgx) < 2 * d0 && lgx < p.hlg) ++lgx;
             __syncwarp();
-            for (int q = lane; q < d0; q += 32) hset_put(hx, lgx, __ldg(p.uadj + b0 + q) & TG_IDMASK);
-            __syncwarp();
+            if (xh) {
+                for (int q = lane; q < (1 << lgx); q += 32) hx[q] = 0u;
+                __syncwarp();
+                for (int q = lane; q < d0; q += 32) hset_put(hx, lgx, __ldg(p.uadj + b0 + q) & TG_IDMASK);
+                __syncwarp();
+            }
         }
-        for (int c0 = 0; c0 < d0; c0 += 32) {
-            const uint32_t ev = c0 + lane < d0 ? __ldg(p.uadj + b0 + c0 + lane) : 0u;
-            unsigned upm = __ballot_sync(kFull, c0 + lane < d0);
-            while (upm) {
-                const int src = __ffs(upm) - 1;
-                upm &= upm - 1;
-                const uint32_t vent = __shfl_sync(kFull, ev, src);
+        {
+            {
+                const uint32_t vent = __ldg(p.uadj + qq);
                 const uint32_t v = vent & TG_IDMASK;
                 const int tv = (int)(vent >> TG_TSHIFT);
                 const int64_t bv = p.uoff[v];
@@ -859,6 +905,7 @@ __global__ void __launch_bounds__(kK4GWarps * 32) k_k4_global(K4GParams p) {
                 }
                 __syncwarp();
             }
+        }
         }
     }
     __syncthreads();
@@ -1387,11 +1434,14 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
 
     // split anchors, in waves of at most `slots` anchors
     if (nheavy > 0) {
+        // a wave holds at most 2 TM anchors: k_c4_pairs keeps their list
+        // lengths' prefix in the 2 TM member words of its shared memory
+        const int64_t wave = std::min<int64_t>(slots, 2 * (int64_t)TM);
         std::vector<int4> units;
         std::vector<int64_t> wave_start;
-        for (int64_t q0 = 0; q0 < nheavy; q0 += slots) {
+        for (int64_t q0 = 0; q0 < nheavy; q0 += wave) {
             wave_start.push_back((int64_t)units.size());
-            for (int64_t q = q0; q < std::min(nheavy, q0 + slots); ++q)
+            for (int64_t q = q0; q < std::min(nheavy, q0 + wave); ++q)
                 for (int64_t tl = 0; tl < hdeg[q]; tl += TM)
                     units.push_back(make_int4((int)(q - q0), (int)heavy[q], (int)tl, 0));
         }
@@ -1404,7 +1454,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
                                     cudaMemcpyHostToDevice, s));
         for (size_t w = 0; w + 1 < wave_start.size(); ++w) {
             const int64_t u0 = wave_start[w], nu = wave_start[w + 1] - u0;
-            const int64_t a0 = (int64_t)w * slots, na = std::min<int64_t>(slots, nheavy - a0);
+            const int64_t a0 = (int64_t)w * wave, na = std::min<int64_t>(wave, nheavy - a0);
             p.units = du.p + u0;
             p.n_units = nu;
             const int64_t grid = std::min<int64_t>(full_grid, nu);
@@ -1415,8 +1465,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
                 k_c4_split<<<(unsigned)grid, kC4Threads, smem, s>>>(p); tg_note_launch();
                 TG_TRY_CUDA(cudaGetLastError());
             }
-            const dim3 pg((unsigned)std::max<int64_t>(1, full_grid / na), (unsigned)na);
-            k_c4_pairs<<<pg, kC4Threads, smem, s>>>(p, wave_anchor.p + a0); tg_note_launch();
+            k_c4_pairs<<<(unsigned)full_grid, kC4Threads, smem, s>>>(p, wave_anchor.p + a0, (int)na); tg_note_launch();
             TG_TRY_CUDA(cudaGetLastError());
         }
         // the host vectors are read by the copy above before they go out of scope
@@ -1503,7 +1552,7 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
                                                                   kK4GWarps * 32, gsmem));
         if (gper < 1) gper = 1;
         int64_t ggrid = (int64_t)num_sms_c() * gper;
-        const int64_t gneed = (n + kK4GWarps - 1) / kK4GWarps;
+        const int64_t gneed = (g->M / kK4GChunk + kK4GWarps) / kK4GWarps;
         if (ggrid > gneed) ggrid = gneed;
         if (ggrid < 1) ggrid = 1;
         K4GParams q{};
@@ -1512,6 +1561,7 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
         q.utoff = utoff.p;
         q.ntype = g->ntype;
         q.n = n;
+        q.m = g->M;
         q.L = L;
         q.cap = gcap;
         q.hlg = hlg;

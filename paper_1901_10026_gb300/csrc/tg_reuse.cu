@@ -44,18 +44,47 @@ constexpr int kTCap = 1024;    // T members kept in shared memory for probing
 constexpr int kProbeFactor = 4;
 
 // ---------------------------------------------------------------- units ----
+// Work units of a grouped order (edges sorted by their high-degree end j): a
+// unit is a run of edges sharing j.  A CTA rebuilds its Gamma_j bitmap when it
+// takes a unit of another j, so a group is cut by cost, not by count: with
+// c_e = d_i + kUnitEdgeCost per edge and C_j the group's total, the units hold
+// about max(C_j / kUnitSplit, kUnitMinCost) each.  A hub's list is then built
+// about kUnitSplit times, and its heavy edges (first in the group) are spread
+// over as many units instead of filling one.
+constexpr int kUnitSplit = 8;
+constexpr int64_t kUnitEdgeCost = 16;
+constexpr int64_t kUnitMinCost = 8192;
+
+__global__ void k_group_bounds(const uint32_t *order, const int2 *edges, const int64_t *rowptr,
+                               int64_t count, uint32_t *gs, uint32_t *ge, int64_t *cost) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < count;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int2 ab = edges[order[p]];
+        const int j = min(ab.x, ab.y), i = max(ab.x, ab.y);
+        if (p == 0 || min(edges[order[p - 1]].x, edges[order[p - 1]].y) != j) gs[j] = (uint32_t)p;
+        if (p == count - 1 || min(edges[order[p + 1]].x, edges[order[p + 1]].y) != j)
+            ge[j] = (uint32_t)(p + 1);
+        cost[p] = (rowptr[i + 1] - rowptr[i]) + kUnitEdgeCost;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) cost[count] = 0;
+}
+
+// cum: exclusive prefix of the edge costs (count + 1 entries)
 __global__ void k_unit_flags(const uint32_t *order, const int2 *edges, int64_t count,
+                             const uint32_t *gs, const uint32_t *ge, const int64_t *cum,
                              uint32_t *flag) {
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < count;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int2 ab = edges[order[p]];
         const int j = min(ab.x, ab.y);
-        bool start = p == 0 || (p % kTauUnit) == 0;
-        if (!start) {
-            const int2 pb = edges[order[p - 1]];
-            start = min(pb.x, pb.y) != j;
+        const uint32_t g0 = gs[j];
+        if ((uint32_t)p == g0) {
+            flag[p] = 1u;
+            continue;
         }
-        flag[p] = start ? 1u : 0u;
+        const int64_t base = cum[g0];
+        const int64_t ucost = max((cum[ge[j]] - base) / kUnitSplit, kUnitMinCost);
+        flag[p] = (cum[p] - base) / ucost != (cum[p - 1] - base) / ucost ? 1u : 0u;
     }
 }
 
@@ -705,12 +734,18 @@ int timing_begin(cudaStream_t s, unsigned long long **work) {
     return TG_OK;
 }
 
-// Work units of the grouped order: runs of at most kTauUnit edges sharing j.
+// Work units of the grouped order (see k_unit_flags).
 int edge_units(const tg_graph *g, const uint32_t *ord, int64_t cnt, cudaStream_t s,
                DevBuf<uint32_t> &ustart, uint32_t *nunits) {
-    DevBuf<uint32_t> flag, pos;
-    if (!flag.alloc(cnt, s) || !pos.alloc(cnt, s)) return TG_ENOMEM;
-    k_unit_flags<<<grid_r(cnt), 256, 0, s>>>(ord, g->edges, cnt, flag.p); tg_note_launch();
+    DevBuf<uint32_t> flag, pos, gs, ge;
+    DevBuf<int64_t> cost, cum;
+    if (!flag.alloc(cnt, s) || !pos.alloc(cnt, s) || !gs.alloc(g->n, s) || !ge.alloc(g->n, s) ||
+        !cost.alloc(cnt + 1, s) || !cum.alloc(cnt + 1, s))
+        return TG_ENOMEM;
+    k_group_bounds<<<grid_r(cnt), 256, 0, s>>>(ord, g->edges, g->rowptr, cnt, gs.p, ge.p, cost.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    TG_TRY(tg_scan_i64(cost.p, cum.p, cnt + 1, s));
+    k_unit_flags<<<grid_r(cnt), 256, 0, s>>>(ord, g->edges, cnt, gs.p, ge.p, cum.p, flag.p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     TG_TRY(tg_scan_u32(flag.p, pos.p, cnt, s));
     uint32_t lastp = 0, lastf = 0;
