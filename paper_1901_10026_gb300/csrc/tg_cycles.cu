@@ -966,6 +966,7 @@ struct EdgeParams {
     int32_t L, P, k, level;
     int64_t nbits;
     uint32_t *emap;            // per CTA, nbits entries: edge id of (j, y) for y in Gamma_j
+    unsigned long long *tsum;  // split mode: per edge id, B, C and DT (3 L^2 uint64)
     unsigned long long *queue;
     uint64_t *rows;
     int64_t width;
@@ -1086,9 +1087,109 @@ __device__ __forceinline__ void hadd_e(const EdgeParams &p, unsigned long long *
         atomicAdd(p.hist + x, v);
 }
 
-constexpr int kEdgeMaxThreads = 512;
+// The 2- and 3-node entries of edge e, then the identities and closed forms
+// per type pair (t, u) from B, C, DT (this warp's, in shared memory) and the
+// per-edge or per-node rows; written to the row of e or added to the
+// histogram.  Called by the 32 lanes of the edge's warp.
+__device__ void edge_finish(const EdgeParams &p, unsigned long long *shist, int64_t e, int i, int j,
+                            int ti, int tj, const int32_t *toi, const int32_t *toj,
+                            const uint32_t *tn, const unsigned long long *Bm,
+                            const unsigned long long *Cm, const unsigned long long *Dm) {
+    const int lane = threadIdx.x & 31;
+    const int L = p.L, P = p.P, L2 = L * L;
+    // 2- and 3-node entries
+    if (p.rows) {
+        uint64_t *row = p.rows + e * p.width;
+        for (int t = lane; t < L; t += 32) {
+            const uint32_t tt = __ldg(tn + t);
+            const int64_t si = (int64_t)(__ldg(toi + t + 1) - __ldg(toi + t)) - tt - (t == tj);
+            const int64_t sj = (int64_t)(__ldg(toj + t + 1) - __ldg(toj + t)) - tt - (t == ti);
+            row[t] = (uint64_t)(si + sj);
+            row[L + t] = tt;
+        }
+    } else {
+        if (lane == 0) {
+            int a = ti, b = tj;
+            sort2(a, b);
+            hadd_e(p, shist, (int64_t)a + (int64_t)(b + 1) * b / 2, 1ull);
+        }
+        for (int t = lane; t < L; t += 32) {
+            const uint32_t tt = __ldg(tn + t);
+            const int64_t si = (int64_t)(__ldg(toi + t + 1) - __ldg(toi + t)) - tt - (t == tj);
+            const int64_t sj = (int64_t)(__ldg(toj + t + 1) - __ldg(toj + t)) - tt - (t == ti);
+            int a = ti, b = tj, cc = t;
+            sort2(a, b);
+            sort2(b, cc);
+            sort2(a, b);
+            const int64_t r = colex3(a, b, cc);
+            hadd_e(p, shist, p.off1 + r, (unsigned long long)(si + sj));
+            hadd_e(p, shist, p.off2 + r, (unsigned long long)tt);
+        }
+    }
+    if (p.k == 4) {
+        EdgeIn in;
+        in.L = L;
+        in.ti = ti;
+        in.tj = tj;
+        in.B = Bm;
+        in.C = Cm;
+        in.DT = Dm;
+        in.c4 = p.c4e ? p.c4e + e * L2 : nullptr;
+        in.k4 = p.k4e ? p.k4e + e * P : nullptr;
+        in.thi = p.theta + (int64_t)i * L2;
+        in.thj = p.theta + (int64_t)j * L2;
+        in.dvi = p.dsum + (int64_t)i * L2;
+        in.dvj = p.dsum + (int64_t)j * L2;
+        in.tn = tn;
+        in.toi = toi;
+        in.toj = toj;
+        const EdgeEval E{in};
+        for (int pr = lane; pr < P; pr += 32) {
+            int t, u;
+            unpair(L, pr, t, u);
+            uint64_t g[10];
+            pair_orbits(E, t, u, g);
+            if (p.rows) {
+                uint64_t *row = p.rows + e * p.width + 2 * L;
+                if (p.level == TG_ORBIT) {
+#pragma unroll
+                    for (int o = 0; o < 10; ++o) row[o * P + pr] = g[o];
+                } else {
+                    row[0 * P + pr] = g[0] + g[1];
+                    row[1 * P + pr] = g[2];
+                    row[2 * P + pr] = g[3];
+                    row[3 * P + pr] = g[4] + g[5] + g[6];
+                    row[4 * P + pr] = g[7] + g[8];
+                    row[5 * P + pr] = g[9];
+                }
+            } else {
+                const uint64_t h[6] = {g[0] + g[1], g[2], g[3], g[4] + g[5] + g[6],
+                                       g[7] + g[8], g[9]};
+                if (h[0] | h[1] | h[2] | h[3] | h[4] | h[5]) {
+                    int a = ti, b = tj, cc = t, d = u;
+                    sort2(a, b);
+                    sort2(cc, d);
+                    sort2(a, cc);
+                    sort2(b, d);
+                    sort2(b, cc);
+                    const int64_t r = colex4(a, b, cc, d);
+#pragma unroll
+                    for (int qq = 0; qq < 6; ++qq) hadd_e(p, shist, p.off4 + qq * p.n4 + r, h[qq]);
+                }
+            }
+        }
+    }
+}
 
-__global__ void __launch_bounds__(kEdgeMaxThreads) k_cyc_edge(EdgeParams p) {
+constexpr int kEdgeMaxThreads = 512;
+constexpr int kTsumThreads = 1024;
+
+// One CTA per unit of edges sharing j (Gamma_j bitmap and edge-id map shared
+// by the CTA), one warp per edge: T = Gamma_i n Gamma_j gives B, C, DT.
+// kWrite: store them for k_cyc_finish (fewer registers, more warps in
+// flight for the gathers); else finish the edge here.
+template <bool kWrite>
+__global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc_edge(EdgeParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
     const int L = p.L, P = p.P, L2 = L * L;
@@ -1212,87 +1313,12 @@ __global__ void __launch_bounds__(kEdgeMaxThreads) k_cyc_edge(EdgeParams p) {
                 __syncwarp();
             }
             if (lane == 0) wk_gamma += (unsigned long long)di;
-            // 2- and 3-node entries
-            if (p.rows) {
-                uint64_t *row = p.rows + e * p.width;
-                for (int t = lane; t < L; t += 32) {
-                    const uint32_t tt = __ldg(tn + t);
-                    const int64_t si = (int64_t)(__ldg(toi + t + 1) - __ldg(toi + t)) - tt - (t == tj);
-                    const int64_t sj = (int64_t)(__ldg(toj + t + 1) - __ldg(toj + t)) - tt - (t == ti);
-                    row[t] = (uint64_t)(si + sj);
-                    row[L + t] = tt;
-                }
+            if (kWrite) {
+                // B, C, DT of this edge for the finishing kernel
+                unsigned long long *dst = p.tsum + (int64_t)q * 3 * L2;
+                for (int x = lane; x < 3 * L2; x += 32) dst[x] = Bm[x];
             } else {
-                if (lane == 0) {
-                    int a = ti, b = tj;
-                    sort2(a, b);
-                    hadd_e(p, shist, (int64_t)a + (int64_t)(b + 1) * b / 2, 1ull);
-                }
-                for (int t = lane; t < L; t += 32) {
-                    const uint32_t tt = __ldg(tn + t);
-                    const int64_t si = (int64_t)(__ldg(toi + t + 1) - __ldg(toi + t)) - tt - (t == tj);
-                    const int64_t sj = (int64_t)(__ldg(toj + t + 1) - __ldg(toj + t)) - tt - (t == ti);
-                    int a = ti, b = tj, cc = t;
-                    sort2(a, b);
-                    sort2(b, cc);
-                    sort2(a, b);
-                    const int64_t r = colex3(a, b, cc);
-                    hadd_e(p, shist, p.off1 + r, (unsigned long long)(si + sj));
-                    hadd_e(p, shist, p.off2 + r, (unsigned long long)tt);
-                }
-            }
-            if (p.k == 4) {
-                EdgeIn in;
-                in.L = L;
-                in.ti = ti;
-                in.tj = tj;
-                in.B = Bm;
-                in.C = Cm;
-                in.DT = Dm;
-                in.c4 = p.c4e ? p.c4e + e * L2 : nullptr;
-                in.k4 = p.k4e ? p.k4e + e * P : nullptr;
-                in.thi = p.theta + (int64_t)i * L2;
-                in.thj = p.theta + (int64_t)j * L2;
-                in.dvi = p.dsum + (int64_t)i * L2;
-                in.dvj = p.dsum + (int64_t)j * L2;
-                in.tn = tn;
-                in.toi = toi;
-                in.toj = toj;
-                const EdgeEval E{in};
-                for (int pr = lane; pr < P; pr += 32) {
-                    int t, u;
-                    unpair(L, pr, t, u);
-                    uint64_t g[10];
-                    pair_orbits(E, t, u, g);
-                    if (p.rows) {
-                        uint64_t *row = p.rows + e * p.width + 2 * L;
-                        if (p.level == TG_ORBIT) {
-#pragma unroll
-                            for (int o = 0; o < 10; ++o) row[o * P + pr] = g[o];
-                        } else {
-                            row[0 * P + pr] = g[0] + g[1];
-                            row[1 * P + pr] = g[2];
-                            row[2 * P + pr] = g[3];
-                            row[3 * P + pr] = g[4] + g[5] + g[6];
-                            row[4 * P + pr] = g[7] + g[8];
-                            row[5 * P + pr] = g[9];
-                        }
-                    } else {
-                        const uint64_t h[6] = {g[0] + g[1], g[2], g[3], g[4] + g[5] + g[6],
-                                               g[7] + g[8], g[9]};
-                        if (h[0] | h[1] | h[2] | h[3] | h[4] | h[5]) {
-                            int a = ti, b = tj, cc = t, d = u;
-                            sort2(a, b);
-                            sort2(cc, d);
-                            sort2(a, cc);
-                            sort2(b, d);
-                            sort2(b, cc);
-                            const int64_t r = colex4(a, b, cc, d);
-#pragma unroll
-                            for (int qq = 0; qq < 6; ++qq) hadd_e(p, shist, p.off4 + qq * p.n4 + r, h[qq]);
-                        }
-                    }
-                }
+                edge_finish(p, shist, e, i, j, ti, tj, toi, toj, tn, Bm, Cm, Dm);
             }
             __syncwarp();  // this warp's matrices are cleared for the next edge
         }
@@ -1305,6 +1331,39 @@ __global__ void __launch_bounds__(kEdgeMaxThreads) k_cyc_edge(EdgeParams p) {
     if (p.work && lane == 0) {
         atomicAdd(p.work + 0, wk_gamma);
         atomicAdd(p.work + 3, wk_t);
+    }
+}
+
+// Warp per edge: B, C, DT from k_cyc_edge<true>, then edge_finish.
+__global__ void __launch_bounds__(256) k_cyc_finish(EdgeParams p, int64_t count) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int L = p.L, L2 = L * L;
+    size_t off = 0;
+    unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);
+    if (p.hist_smem) off += ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
+    const size_t wbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
+    unsigned long long *Bm = reinterpret_cast<unsigned long long *>(smem + off + warp * wbytes);
+    if (p.hist_smem) {
+        for (int64_t x = tid; x < p.hist_len; x += blockDim.x) shist[x] = 0;
+        __syncthreads();
+    }
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5; q < count; q += nw) {
+        const int64_t e = p.order[q];
+        const int2 ab = p.edges[e];
+        const int j = min(ab.x, ab.y), i = max(ab.x, ab.y);
+        const unsigned long long *src = p.tsum + q * 3 * L2;
+        for (int x = lane; x < 3 * L2; x += 32) Bm[x] = __ldg(src + x);
+        __syncwarp();
+        edge_finish(p, shist, e, i, j, p.ntype[i], p.ntype[j], p.toff + (int64_t)i * (L + 1),
+                    p.toff + (int64_t)j * (L + 1), p.tau + e * L, Bm, Bm + L2, Bm + 2 * L2);
+        __syncwarp();
+    }
+    if (p.hist_smem) {
+        __syncthreads();
+        for (int64_t x = tid; x < p.hist_len; x += blockDim.x)
+            if (shist[x]) atomicAdd(p.hist + x, shist[x]);
     }
 }
 
@@ -1593,13 +1652,13 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
     return TG_OK;
 }
 
-int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order,
+int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int64_t count,
                  const uint32_t *ustart, uint32_t nunits, uint64_t *rows, int64_t width,
                  unsigned long long *hist, const uint32_t *tau, const uint32_t *theta,
                  const uint32_t *dsum, const unsigned long long *c4e,
                  const unsigned long long *k4e, unsigned long long *work, const tg_tune &t,
                  cudaStream_t s) {
-    if (nunits == 0) return TG_OK;
+    if (nunits == 0 || count <= 0) return TG_OK;
     const int L = g->L, L2 = L * L;
     if (g->max_degree >= ((int64_t)1 << 27)) return TG_EOVERFLOW;  // 32-lane uint32 sums
     EdgeParams p{};
@@ -1630,13 +1689,19 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order,
     p.off4 = p.off1 + 2 * tg_binom(L + 2, 3);
     p.n4 = tg_binom(L + 3, 4);
     p.work = work;
-    int threads = t.cta_threads;
-    if (threads > kEdgeMaxThreads) threads = kEdgeMaxThreads;
-    if (threads < 32) threads = 32;
     const size_t avail = (size_t)smem_optin_c() - 1024;
     const size_t hist_bytes = ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
-    p.hist_smem = (!rows && hist_bytes <= 48 * 1024) ? 1 : 0;
+    const int hist_smem = (!rows && hist_bytes <= 48 * 1024) ? 1 : 0;
     const size_t wbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
+    // B, C, DT through memory when they fit in a quarter of free memory
+    const size_t tsum_bytes = (size_t)count * 3 * L2 * 8;
+    size_t free_b = 0, total_b = 0;
+    TG_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    const bool split = k == 4 && tsum_bytes <= free_b / 4;
+    int threads = t.cta_threads;
+    if (threads > (split ? kTsumThreads : kEdgeMaxThreads)) threads = split ? kTsumThreads : kEdgeMaxThreads;
+    if (threads < 32) threads = 32;
+    p.hist_smem = split ? 0 : hist_smem;
     size_t fixed = (p.hist_smem ? hist_bytes : 0) + (size_t)(threads / 32) * wbytes + 16;
     while (fixed + 4096 > avail && threads > 32) {
         threads -= 32;
@@ -1650,13 +1715,16 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order,
     if (nbits < 0) nbits = 0;
     p.nbits = nbits;
     const size_t smem = fixed + ((((size_t)((nbits + 31) >> 5)) * 4 + 15) & ~(size_t)15);
-    DevBuf<unsigned long long> queue;
+    DevBuf<unsigned long long> queue, tsum;
     if (!queue.alloc(1, s)) return TG_ENOMEM;
+    if (split && !tsum.alloc((size_t)count * 3 * L2, s)) return TG_ENOMEM;
     TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
     p.queue = queue.p;
-    TG_TRY(tg_allow_max_smem((const void *)k_cyc_edge));
+    p.tsum = tsum.p;
+    const void *kfn = split ? (const void *)k_cyc_edge<true> : (const void *)k_cyc_edge<false>;
+    TG_TRY(tg_allow_max_smem(kfn));
     int per_sm = 0;
-    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cyc_edge, threads, smem));
+    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem));
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)num_sms_c() * per_sm;
     if (grid > nunits) grid = nunits;
@@ -1665,7 +1733,25 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order,
     DevBuf<uint32_t> emap;
     if (!emap.alloc((size_t)std::max<int64_t>(1, grid * nbits), s)) return TG_ENOMEM;
     p.emap = emap.p;
-    k_cyc_edge<<<(unsigned)grid, threads, smem, s>>>(p); tg_note_launch();
+    if (split)
+        k_cyc_edge<true><<<(unsigned)grid, threads, smem, s>>>(p);
+    else
+        k_cyc_edge<false><<<(unsigned)grid, threads, smem, s>>>(p);
+    tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    if (!split) return TG_OK;
+    // finishing pass: warp per edge
+    p.hist_smem = hist_smem;
+    const size_t fsmem = (hist_smem ? hist_bytes : 0) + (256 / 32) * wbytes;
+    TG_TRY(tg_allow_max_smem((const void *)k_cyc_finish));
+    int fper = 0;
+    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, k_cyc_finish, 256, fsmem));
+    if (fper < 1) fper = 1;
+    int64_t fgrid = (int64_t)num_sms_c() * fper;
+    if (fgrid > (count + 7) / 8) fgrid = (count + 7) / 8;
+    if (t.grid_limit > 0 && fgrid > t.grid_limit) fgrid = t.grid_limit;
+    if (fgrid < 1) fgrid = 1;
+    k_cyc_finish<<<(unsigned)fgrid, 256, fsmem, s>>>(p, count); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     return TG_OK;
 }

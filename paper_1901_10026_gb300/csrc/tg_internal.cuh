@@ -148,7 +148,7 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
                    unsigned long long *work, const tg_tune &t, cudaStream_t s);
 int tg_cyc_correct(unsigned long long *hist, int L, const unsigned long long *c4w,
                    const unsigned long long *k4, cudaStream_t s);
-int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order,
+int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int64_t count,
                  const uint32_t *ustart, uint32_t nunits, uint64_t *rows, int64_t width,
                  unsigned long long *hist, const uint32_t *tau, const uint32_t *theta,
                  const uint32_t *dsum, const unsigned long long *c4e,

@@ -871,7 +871,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
             TG_TRY(edge_units(g, order, count, s, ust2, &nun));
             ust = ust2.p;
         }
-        TG_TRY(tg_cyc_edges(g, k, level, order, ust, nun, rows, width, hist, tau.p, theta.p,
+        TG_TRY(tg_cyc_edges(g, k, level, order, count, ust, nun, rows, width, hist, tau.p, theta.p,
                             dsum.p, c4e.p, k4e.p, work, t, s));
         if (fast) TG_TRY(tg_cyc_correct(hist, L, g4c.p, g4k.p, s));
         TG_TRY_CUDA(cudaEventRecord(g_last.ev[5], s));
