@@ -698,34 +698,6 @@ __global__ void __launch_bounds__(kK4Warps * 32) k_k4(K4Params p) {
     }
 }
 
-// Per-warp hash sets of node ids in shared memory (open addressing, linear
-// probing, id + 1 stored, 0 empty).  Reads are volatile: the table is written
-// by other lanes of the warp between a __syncwarp and the reads.
-__device__ __forceinline__ uint32_t hset_slot(uint32_t id, int lg) {
-    return (id * 0x9E3779B1u) >> (32 - lg);
-}
-__device__ __forceinline__ void hset_put(uint32_t *tab, int lg, uint32_t id) {
-    const uint32_t mask = (1u << lg) - 1u;
-    uint32_t h = hset_slot(id, lg);
-    for (int probe = 0; probe < (1 << lg); ++probe) {
-        const uint32_t old = atomicCAS(tab + h, 0u, id + 1u);
-        if (old == 0u || old == id + 1u) return;
-        h = (h + 1u) & mask;
-    }
-}
-__device__ __forceinline__ bool hset_has(const uint32_t *tab, int lg, uint32_t id) {
-    const uint32_t mask = (1u << lg) - 1u;
-    const volatile uint32_t *t = tab;
-    uint32_t h = hset_slot(id, lg);
-    for (int probe = 0; probe < (1 << lg); ++probe) {
-        const uint32_t k = t[h];
-        if (k == id + 1u) return true;
-        if (k == 0u) return false;
-        h = (h + 1u) & mask;
-    }
-    return false;
-}
-
 // 4-cliques by type multiset only (global mode).  As k_k4, each clique is met
 // from its lowest node x0 and the next one v; here a warp's work item is a
 // run of kK4GChunk oriented edges (x0, v) of the up lists, so the edges of a
@@ -957,6 +929,7 @@ struct EdgeParams {
     const int2 *edges;
     const uint32_t *order;
     const uint32_t *ustart;
+    const uint32_t *ulist;     // units this launch takes (NULL: units 0 .. nunits - 1)
     uint32_t nunits;
     const uint32_t *tau;
     const uint32_t *theta;
@@ -1181,6 +1154,46 @@ __device__ void edge_finish(const EdgeParams &p, unsigned long long *shist, int6
     }
 }
 
+// One chunk of Gamma_i (one entry per lane): the lanes holding a T member y
+// (packed entry w, edge ids eiy of (i, y) and ejy of (j, y)) add tau_jy,
+// tau_iy and y's typed degrees, by the type of y, to this warp's B, C, DT.
+// All 32 lanes call it.
+__device__ __forceinline__ void tsum_chunk(const EdgeParams &p, bool isT, uint32_t w, uint32_t eiy,
+                                           uint32_t ejy, unsigned long long *Bm,
+                                           unsigned long long *Cm, unsigned long long *Dm) {
+    const int L = p.L;
+    const int lane = threadIdx.x & 31;
+    const int a = (int)(w >> TG_TSHIFT);
+    const unsigned tm = __match_any_sync(kFull, isT ? a : -1);
+    const bool lead = isT && lane == __ffs(tm) - 1;
+    const uint32_t *tiy = p.tau, *tjy = p.tau;
+    const int32_t *ty = p.toff;
+    if (isT) {
+        tiy = p.tau + (int64_t)eiy * L;
+        tjy = p.tau + (int64_t)ejy * L;
+        ty = p.toff + (int64_t)(w & TG_IDMASK) * (L + 1);
+    }
+    int prev = isT ? __ldg(ty) : 0;
+    for (int b = 0; b < L; ++b) {
+        uint32_t vb = 0, vc = 0, vd = 0;
+        if (isT) {
+            vb = __ldg(tjy + b);
+            vc = __ldg(tiy + b);
+            const int nx = __ldg(ty + b + 1);
+            vd = (uint32_t)(nx - prev);
+            prev = nx;
+        }
+        const uint32_t sb = __reduce_add_sync(tm, vb);
+        const uint32_t sc = __reduce_add_sync(tm, vc);
+        const uint32_t sd = __reduce_add_sync(tm, vd);
+        if (lead) {
+            Bm[a * L + b] += sb;
+            Cm[a * L + b] += sc;
+            Dm[a * L + b] += sd;
+        }
+    }
+}
+
 constexpr int kEdgeMaxThreads = 512;
 constexpr int kTsumThreads = 1024;
 
@@ -1220,8 +1233,9 @@ __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc
         __syncthreads();
         if (tid == 0) *s_unit = atomicAdd(p.queue, 1ull);
         __syncthreads();
-        const unsigned long long un = *s_unit;
-        if (un >= p.nunits) break;
+        const unsigned long long item = *s_unit;
+        if (item >= p.nunits) break;
+        const uint32_t un = p.ulist ? p.ulist[item] : (uint32_t)item;
         const uint32_t p0 = p.ustart[un], p1 = p.ustart[un + 1];
         const int2 ab0 = p.edges[p.order[p0]];
         const int j = min(ab0.x, ab0.y);
@@ -1270,43 +1284,18 @@ __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc
                             isT = (int64_t)id < p.nbits ? bm_test(bm, id)
                                                         : contains(adj, bj, toj, w);
                     }
-                    const int a = (int)(w >> TG_TSHIFT);
-                    const unsigned tm = __match_any_sync(kFull, isT ? a : -1);
-                    const bool lead = isT && lane == __ffs(tm) - 1;
-                    const uint32_t *tiy = p.tau, *tjy = p.tau;
-                    const int32_t *ty = p.toff;
+                    uint32_t eiy = 0, ejy = 0;
                     if (isT) {
                         const uint32_t yid = w & TG_IDMASK;
-                        tiy = p.tau + (int64_t)__ldg(p.eid + bi + x) * L;
-                        uint32_t ejy;
+                        eiy = __ldg(p.eid + bi + x);
                         if ((int64_t)yid < p.nbits) {
                             ejy = __ldcg(emap + yid);  // written for this j before the barrier
                         } else {
                             const int pj = find_pos(adj, bj, toj, w);
                             ejy = __ldg(p.eid + bj + (pj < 0 ? 0 : pj));
                         }
-                        tjy = p.tau + (int64_t)ejy * L;
-                        ty = p.toff + (int64_t)yid * (L + 1);
                     }
-                    int prev = isT ? __ldg(ty) : 0;
-                    for (int b = 0; b < L; ++b) {
-                        uint32_t vb = 0, vc = 0, vd = 0;
-                        if (isT) {
-                            vb = __ldg(tjy + b);
-                            vc = __ldg(tiy + b);
-                            const int nx = __ldg(ty + b + 1);
-                            vd = (uint32_t)(nx - prev);
-                            prev = nx;
-                        }
-                        const uint32_t sb = __reduce_add_sync(tm, vb);
-                        const uint32_t sc = __reduce_add_sync(tm, vc);
-                        const uint32_t sd = __reduce_add_sync(tm, vd);
-                        if (lead) {
-                            Bm[a * L + b] += sb;
-                            Cm[a * L + b] += sc;
-                            Dm[a * L + b] += sd;
-                        }
-                    }
+                    tsum_chunk(p, isT, w, eiy, ejy, Bm, Cm, Dm);
                     const unsigned tb = __ballot_sync(kFull, isT);
                     if (lane == 0) wk_t += (unsigned long long)__popc(tb);
                 }
@@ -1327,6 +1316,78 @@ __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc
         __syncthreads();
         for (int64_t x = tid; x < p.hist_len; x += blockDim.x)
             if (shist[x]) atomicAdd(p.hist + x, shist[x]);
+    }
+    if (p.work && lane == 0) {
+        atomicAdd(p.work + 0, wk_gamma);
+        atomicAdd(p.work + 3, wk_t);
+    }
+}
+
+// T sums of light units (Gamma_j of at most TG_LIGHT_DEGREE entries): one warp
+// per unit, Gamma_j in a per-warp hash map from node id to the edge id of
+// (j, y); the unit's edges one after the other, no CTA barrier.
+constexpr int kTsumLightWarps = 8;
+
+__global__ void __launch_bounds__(kTsumLightWarps * 32) k_cyc_tsum_light(EdgeParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int L = p.L, L2 = L * L;
+    const size_t wbytes = (((size_t)3 * L2 * 8 + 15) & ~(size_t)15) + (size_t)2 * 4 * (1 << TG_LIGHT_LG);
+    unsigned long long *Bm = reinterpret_cast<unsigned long long *>(smem + warp * wbytes);
+    unsigned long long *Cm = Bm + L2;
+    unsigned long long *Dm = Cm + L2;
+    uint32_t *hk = reinterpret_cast<uint32_t *>(smem + warp * wbytes + (((size_t)3 * L2 * 8 + 15) & ~(size_t)15));
+    uint32_t *hv = hk + (1 << TG_LIGHT_LG);
+    const int64_t *__restrict__ rowptr = p.rowptr;
+    const uint32_t *__restrict__ adj = p.adj;
+    unsigned long long wk_gamma = 0, wk_t = 0;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(p.queue, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= p.nunits) break;
+        const uint32_t un = p.ulist[item];
+        const uint32_t p0 = p.ustart[un], p1 = p.ustart[un + 1];
+        const int2 ab0 = p.edges[p.order[p0]];
+        const int j = min(ab0.x, ab0.y);
+        const int64_t bj = rowptr[j];
+        const int dj = (int)(rowptr[j + 1] - bj);
+        for (int q = lane; q < (1 << TG_LIGHT_LG); q += 32) hk[q] = 0u;
+        __syncwarp();
+        for (int x = lane; x < dj; x += 32)
+            hmap_put(hk, hv, TG_LIGHT_LG, __ldg(adj + bj + x) & TG_IDMASK, __ldg(p.eid + bj + x));
+        __syncwarp();
+        for (uint32_t q = p0; q < p1; ++q) {
+            const int64_t e = p.order[q];
+            const int2 ab = p.edges[e];
+            const int i = max(ab.x, ab.y);
+            const int64_t bi = rowptr[i];
+            const int di = (int)(rowptr[i + 1] - bi);
+            for (int x = lane; x < 3 * L2; x += 32) Bm[x] = 0ull;
+            __syncwarp();
+            for (int c0 = 0; c0 < di; c0 += 32) {
+                const int x = c0 + lane;
+                bool isT = false;
+                uint32_t w = 0, eiy = 0, ejy = 0;
+                if (x < di) {
+                    w = __ldg(adj + bi + x);
+                    const uint32_t id = w & TG_IDMASK;
+                    if ((int)id != j) {
+                        ejy = hmap_get(hk, hv, TG_LIGHT_LG, id);
+                        isT = ejy != 0xffffffffu;
+                        if (isT) eiy = __ldg(p.eid + bi + x);
+                    }
+                }
+                tsum_chunk(p, isT, w, eiy, ejy, Bm, Cm, Dm);
+                const unsigned tb = __ballot_sync(kFull, isT);
+                if (lane == 0) wk_t += (unsigned long long)__popc(tb);
+            }
+            __syncwarp();
+            if (lane == 0) wk_gamma += (unsigned long long)di;
+            unsigned long long *dst = p.tsum + (int64_t)q * 3 * L2;
+            for (int x = lane; x < 3 * L2; x += 32) dst[x] = Bm[x];
+            __syncwarp();
+        }
     }
     if (p.work && lane == 0) {
         atomicAdd(p.work + 0, wk_gamma);
@@ -1653,12 +1714,12 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
 }
 
 int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int64_t count,
-                 const uint32_t *ustart, uint32_t nunits, uint64_t *rows, int64_t width,
+                 const tg_units &un, uint64_t *rows, int64_t width,
                  unsigned long long *hist, const uint32_t *tau, const uint32_t *theta,
                  const uint32_t *dsum, const unsigned long long *c4e,
                  const unsigned long long *k4e, unsigned long long *work, const tg_tune &t,
                  cudaStream_t s) {
-    if (nunits == 0 || count <= 0) return TG_OK;
+    if (un.nunits == 0 || count <= 0) return TG_OK;
     const int L = g->L, L2 = L * L;
     if (g->max_degree >= ((int64_t)1 << 27)) return TG_EOVERFLOW;  // 32-lane uint32 sums
     EdgeParams p{};
@@ -1669,8 +1730,7 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
     p.ntype = g->ntype;
     p.edges = g->edges;
     p.order = order;
-    p.ustart = ustart;
-    p.nunits = nunits;
+    p.ustart = un.ustart.p;
     p.tau = tau;
     p.theta = theta;
     p.dsum = dsum;
@@ -1721,25 +1781,53 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
     TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
     p.queue = queue.p;
     p.tsum = tsum.p;
-    const void *kfn = split ? (const void *)k_cyc_edge<true> : (const void *)k_cyc_edge<false>;
-    TG_TRY(tg_allow_max_smem(kfn));
-    int per_sm = 0;
-    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem));
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)num_sms_c() * per_sm;
-    if (grid > nunits) grid = nunits;
-    if (t.grid_limit > 0 && grid > t.grid_limit) grid = t.grid_limit;
-    if (grid < 1) grid = 1;
-    DevBuf<uint32_t> emap;
-    if (!emap.alloc((size_t)std::max<int64_t>(1, grid * nbits), s)) return TG_ENOMEM;
-    p.emap = emap.p;
-    if (split)
-        k_cyc_edge<true><<<(unsigned)grid, threads, smem, s>>>(p);
-    else
-        k_cyc_edge<false><<<(unsigned)grid, threads, smem, s>>>(p);
-    tg_note_launch();
-    TG_TRY_CUDA(cudaGetLastError());
+    // heavy units (all units when fused): one CTA each, Gamma_j bitmap
+    p.ulist = split ? un.heavy.p : nullptr;
+    p.nunits = split ? un.nheavy : un.nunits;
+    if (p.nunits > 0) {
+        const void *kfn = split ? (const void *)k_cyc_edge<true> : (const void *)k_cyc_edge<false>;
+        TG_TRY(tg_allow_max_smem(kfn));
+        int per_sm = 0;
+        TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem));
+        if (per_sm < 1) per_sm = 1;
+        int64_t grid = (int64_t)num_sms_c() * per_sm;
+        if (grid > p.nunits) grid = p.nunits;
+        if (t.grid_limit > 0 && grid > t.grid_limit) grid = t.grid_limit;
+        if (grid < 1) grid = 1;
+        DevBuf<uint32_t> emap;
+        if (!emap.alloc((size_t)std::max<int64_t>(1, grid * nbits), s)) return TG_ENOMEM;
+        p.emap = emap.p;
+        if (split)
+            k_cyc_edge<true><<<(unsigned)grid, threads, smem, s>>>(p);
+        else
+            k_cyc_edge<false><<<(unsigned)grid, threads, smem, s>>>(p);
+        tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
     if (!split) return TG_OK;
+    // light units: one warp each, Gamma_j in a per-warp hash map
+    if (un.nlight > 0) {
+        DevBuf<unsigned long long> lq;
+        if (!lq.alloc(1, s)) return TG_ENOMEM;
+        TG_TRY_CUDA(cudaMemsetAsync(lq.p, 0, 8, s));
+        EdgeParams lp = p;
+        lp.queue = lq.p;
+        lp.ulist = un.light.p;
+        lp.nunits = un.nlight;
+        const size_t lw = (((size_t)3 * L2 * 8 + 15) & ~(size_t)15) + (size_t)2 * 4 * (1 << TG_LIGHT_LG);
+        const size_t lsmem = (size_t)kTsumLightWarps * lw;
+        TG_TRY(tg_allow_max_smem((const void *)k_cyc_tsum_light));
+        int lper = 0;
+        TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lper, k_cyc_tsum_light,
+                                                                  kTsumLightWarps * 32, lsmem));
+        if (lper < 1) lper = 1;
+        int64_t lgrid = (int64_t)num_sms_c() * lper;
+        const int64_t need = ((int64_t)un.nlight + kTsumLightWarps - 1) / kTsumLightWarps;
+        if (lgrid > need) lgrid = need;
+        if (t.grid_limit > 0 && lgrid > t.grid_limit) lgrid = t.grid_limit;
+        k_cyc_tsum_light<<<(unsigned)lgrid, kTsumLightWarps * 32, lsmem, s>>>(lp); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
     // finishing pass: warp per edge
     p.hist_smem = hist_smem;
     const size_t fsmem = (hist_smem ? hist_bytes : 0) + (256 / 32) * wbytes;

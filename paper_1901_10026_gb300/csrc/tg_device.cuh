@@ -83,6 +83,66 @@ __device__ __forceinline__ int find_pos(const uint32_t *__restrict__ adj, int64_
     return (lo < end && __ldg(adj + base + lo) == w) ? lo : -1;
 }
 
+// Per-warp hash sets of node ids in shared memory (open addressing, linear
+// probing, id + 1 stored, 0 empty).  Reads are volatile: the table is written
+// by other lanes of the warp between a __syncwarp and the reads.
+__device__ __forceinline__ uint32_t hset_slot(uint32_t id, int lg) {
+    return (id * 0x9E3779B1u) >> (32 - lg);
+}
+__device__ __forceinline__ void hset_put(uint32_t *tab, int lg, uint32_t id) {
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = hset_slot(id, lg);
+    for (int probe = 0; probe < (1 << lg); ++probe) {
+        const uint32_t old = atomicCAS(tab + h, 0u, id + 1u);
+        if (old == 0u || old == id + 1u) return;
+        h = (h + 1u) & mask;
+    }
+}
+__device__ __forceinline__ bool hset_has(const uint32_t *tab, int lg, uint32_t id) {
+    const uint32_t mask = (1u << lg) - 1u;
+    const volatile uint32_t *t = tab;
+    uint32_t h = hset_slot(id, lg);
+    for (int probe = 0; probe < (1 << lg); ++probe) {
+        const uint32_t k = t[h];
+        if (k == id + 1u) return true;
+        if (k == 0u) return false;
+        h = (h + 1u) & mask;
+    }
+    return false;
+}
+
+// Per-warp hash map of node ids to 32-bit values in shared memory (keys as
+// in hset, values beside them; a value is written after its key is claimed and
+// read after a __syncwarp).
+__device__ __forceinline__ void hmap_put(uint32_t *keys, uint32_t *vals, int lg, uint32_t id,
+                                         uint32_t val) {
+    const uint32_t mask = (1u << lg) - 1u;
+    uint32_t h = hset_slot(id, lg);
+    for (int probe = 0; probe < (1 << lg); ++probe) {
+        const uint32_t old = atomicCAS(keys + h, 0u, id + 1u);
+        if (old == 0u || old == id + 1u) {
+            vals[h] = val;
+            return;
+        }
+        h = (h + 1u) & mask;
+    }
+}
+// the value of id, or 0xffffffff when absent
+__device__ __forceinline__ uint32_t hmap_get(const uint32_t *keys, const uint32_t *vals, int lg,
+                                             uint32_t id) {
+    const uint32_t mask = (1u << lg) - 1u;
+    const volatile uint32_t *k = keys;
+    const volatile uint32_t *v = vals;
+    uint32_t h = hset_slot(id, lg);
+    for (int probe = 0; probe < (1 << lg); ++probe) {
+        const uint32_t x = k[h];
+        if (x == id + 1u) return v[h];
+        if (x == 0u) return 0xffffffffu;
+        h = (h + 1u) & mask;
+    }
+    return 0xffffffffu;
+}
+
 __device__ __forceinline__ uint32_t hslot(uint32_t id, int lg) {
     return (id * 2654435761u) >> (32 - lg);
 }

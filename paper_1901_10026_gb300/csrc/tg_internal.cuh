@@ -136,6 +136,18 @@ void tg_sched_free(tg_graph *g);
 void tg_sched_free_on(tg_graph *g, cudaStream_t s);
 int tg_free_graph_on(tg_graph *g, cudaStream_t s);
 
+// Work units of a grouped order (runs of edges sharing their high-degree end
+// j, tg_reuse.cu): unit u is order[ustart[u] .. ustart[u+1]).  Units whose j
+// has at most TG_LIGHT_DEGREE neighbours are listed in `light` (one warp each,
+// Gamma_j in a per-warp hash), the others in `heavy` (one CTA each, Gamma_j
+// in a shared-memory bitmap).
+#define TG_LIGHT_DEGREE 256
+#define TG_LIGHT_LG 9  // log2 of the per-warp hash slots (2 x TG_LIGHT_DEGREE)
+struct tg_units {
+    DevBuf<uint32_t> ustart, heavy, light;
+    uint32_t nunits = 0, nheavy = 0, nlight = 0;
+};
+
 // Whole-graph enumerations and the per-edge pass of the cycles kernel
 // (tg_cycles.cu).  Per-edge mode: c4e holds M x L x L and k4e M x L(L+1)/2
 // zeroed counters (g4 = NULL).  Global mode (c4e / k4e = NULL): g4 gets, by
@@ -149,7 +161,7 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
 int tg_cyc_correct(unsigned long long *hist, int L, const unsigned long long *c4w,
                    const unsigned long long *k4, cudaStream_t s);
 int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int64_t count,
-                 const uint32_t *ustart, uint32_t nunits, uint64_t *rows, int64_t width,
+                 const tg_units &un, uint64_t *rows, int64_t width,
                  unsigned long long *hist, const uint32_t *tau, const uint32_t *theta,
                  const uint32_t *dsum, const unsigned long long *c4e,
                  const unsigned long long *k4e, unsigned long long *work, const tg_tune &t,

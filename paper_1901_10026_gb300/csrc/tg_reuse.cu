@@ -96,6 +96,28 @@ __global__ void k_unit_starts(const uint32_t *flag, const uint32_t *pos, int64_t
     if (blockIdx.x == 0 && threadIdx.x == 0) ustart[nunits] = (uint32_t)count;
 }
 
+// flag[u] = unit u's j has at most TG_LIGHT_DEGREE neighbours
+__global__ void k_unit_class(const uint32_t *order, const int2 *edges, const int64_t *rowptr,
+                             const uint32_t *ustart, uint32_t nunits, uint32_t *flag) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nunits;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        const int2 ab = edges[order[ustart[u]]];
+        const int j = min(ab.x, ab.y);
+        flag[u] = (rowptr[j + 1] - rowptr[j]) <= TG_LIGHT_DEGREE ? 1u : 0u;
+    }
+}
+
+__global__ void k_unit_lists(const uint32_t *flag, const uint32_t *pos, uint32_t nunits,
+                             uint32_t *light, uint32_t *heavy) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nunits;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        if (flag[u])
+            light[pos[u]] = (uint32_t)u;
+        else
+            heavy[u - pos[u]] = (uint32_t)u;
+    }
+}
+
 // ------------------------------------------------------------ tau (Alg. 1) --
 // One CTA per unit (edges sharing j); Gamma_j is a shared-memory bitmap that
 // stays set while the CTA's units keep the same j; one warp per edge counts
@@ -103,8 +125,9 @@ __global__ void k_unit_starts(const uint32_t *flag, const uint32_t *pos, int64_t
 __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32_t *adj,
                                              const int32_t *toff, const int2 *edges,
                                              const uint32_t *order, const uint32_t *ustart,
-                                             uint32_t nunits, int32_t L, int64_t nbits,
-                                             unsigned long long *queue, uint32_t *tau) {
+                                             const uint32_t *ulist, uint32_t nunits, int32_t L,
+                                             int64_t nbits, unsigned long long *queue,
+                                             uint32_t *tau) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
     const int64_t bwords = (nbits + 31) >> 5;
@@ -119,8 +142,9 @@ __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32
         __syncthreads();
         if (tid == 0) *s_unit = atomicAdd(queue, 1ull);
         __syncthreads();
-        const unsigned long long u = *s_unit;
-        if (u >= nunits) break;
+        const unsigned long long item = *s_unit;
+        if (item >= nunits) break;
+        const uint32_t u = ulist[item];
         const uint32_t p0 = ustart[u], p1 = ustart[u + 1];
         const int2 ab0 = edges[order[p0]];
         const int j = min(ab0.x, ab0.y);
@@ -167,6 +191,60 @@ __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32
             }
             if (lane < L) tau[(int64_t)e * L + lane] = mine;
         }
+    }
+}
+
+// Light units: one warp per unit, Gamma_j (at most TG_LIGHT_DEGREE entries)
+// in a per-warp hash set, the unit's edges one after the other; no CTA barrier.
+constexpr int kLightWarps = 8;
+
+__global__ void __launch_bounds__(kLightWarps * 32) k_tau_light(
+    const int64_t *rowptr, const uint32_t *adj, const int2 *edges, const uint32_t *order,
+    const uint32_t *ustart, const uint32_t *ulist, uint32_t nlist, int32_t L,
+    unsigned long long *queue, uint32_t *tau) {
+    __shared__ uint32_t keys[kLightWarps][1 << TG_LIGHT_LG];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *hk = keys[warp];
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(queue, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= nlist) break;
+        const uint32_t u = ulist[item];
+        const uint32_t p0 = ustart[u], p1 = ustart[u + 1];
+        const int2 ab0 = edges[order[p0]];
+        const int j = min(ab0.x, ab0.y);
+        const int64_t bj = rowptr[j];
+        const int dj = (int)(rowptr[j + 1] - bj);
+        for (int q = lane; q < (1 << TG_LIGHT_LG); q += 32) hk[q] = 0u;
+        __syncwarp();
+        for (int x = lane; x < dj; x += 32) hset_put(hk, TG_LIGHT_LG, __ldg(adj + bj + x) & TG_IDMASK);
+        __syncwarp();
+        for (uint32_t p = p0; p < p1; ++p) {
+            const uint32_t e = order[p];
+            const int2 ab = edges[e];
+            const int i = max(ab.x, ab.y);
+            const int64_t bi = rowptr[i];
+            const int di = (int)(rowptr[i + 1] - bi);
+            unsigned mine = 0;  // lane t keeps the count of type t
+            for (int c0 = 0; c0 < di; c0 += 32) {
+                const int x = c0 + lane;
+                bool hit = false;
+                int t = 0;
+                if (x < di) {
+                    const uint32_t w = __ldg(adj + bi + x);
+                    const uint32_t id = w & TG_IDMASK;
+                    t = (int)(w >> TG_TSHIFT);
+                    hit = (int)id != j && hset_has(hk, TG_LIGHT_LG, id);
+                }
+                for (int q = 0; q < L; ++q) {
+                    const unsigned c = __popc(__ballot_sync(kFull, hit && t == q));
+                    if (lane == q) mine += c;
+                }
+            }
+            if (lane < L) tau[(int64_t)e * L + lane] = mine;
+        }
+        __syncwarp();
     }
 }
 
@@ -734,9 +812,9 @@ int timing_begin(cudaStream_t s, unsigned long long **work) {
     return TG_OK;
 }
 
-// Work units of the grouped order (see k_unit_flags).
+// Work units of the grouped order (see k_unit_flags), split by class.
 int edge_units(const tg_graph *g, const uint32_t *ord, int64_t cnt, cudaStream_t s,
-               DevBuf<uint32_t> &ustart, uint32_t *nunits) {
+               tg_units &un) {
     DevBuf<uint32_t> flag, pos, gs, ge;
     DevBuf<int64_t> cost, cum;
     if (!flag.alloc(cnt, s) || !pos.alloc(cnt, s) || !gs.alloc(g->n, s) || !ge.alloc(g->n, s) ||
@@ -752,10 +830,27 @@ int edge_units(const tg_graph *g, const uint32_t *ord, int64_t cnt, cudaStream_t
     TG_TRY_CUDA(cudaMemcpyAsync(&lastp, pos.p + cnt - 1, 4, cudaMemcpyDeviceToHost, s));
     TG_TRY_CUDA(cudaMemcpyAsync(&lastf, flag.p + cnt - 1, 4, cudaMemcpyDeviceToHost, s));
     TG_TRY_CUDA(cudaStreamSynchronize(s));
-    *nunits = lastp + lastf;
-    if (!ustart.alloc((size_t)*nunits + 1, s)) return TG_ENOMEM;
-    k_unit_starts<<<grid_r(cnt), 256, 0, s>>>(flag.p, pos.p, cnt, ustart.p, *nunits); tg_note_launch();
+    un.nunits = lastp + lastf;
+    if (!un.ustart.alloc((size_t)un.nunits + 1, s)) return TG_ENOMEM;
+    k_unit_starts<<<grid_r(cnt), 256, 0, s>>>(flag.p, pos.p, cnt, un.ustart.p, un.nunits); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
+    // classes: light (one warp each) and heavy (one CTA each)
+    DevBuf<uint32_t> cflag, cpos;
+    if (!cflag.alloc(un.nunits, s) || !cpos.alloc(un.nunits, s) ||
+        !un.light.alloc(un.nunits, s) || !un.heavy.alloc(un.nunits, s))
+        return TG_ENOMEM;
+    k_unit_class<<<grid_r(un.nunits), 256, 0, s>>>(ord, g->edges, g->rowptr, un.ustart.p, un.nunits,
+                                                   cflag.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    TG_TRY(tg_scan_u32(cflag.p, cpos.p, un.nunits, s));
+    k_unit_lists<<<grid_r(un.nunits), 256, 0, s>>>(cflag.p, cpos.p, un.nunits, un.light.p,
+                                                   un.heavy.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    TG_TRY_CUDA(cudaMemcpyAsync(&lastp, cpos.p + un.nunits - 1, 4, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaMemcpyAsync(&lastf, cflag.p + un.nunits - 1, 4, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    un.nlight = lastp + lastf;
+    un.nheavy = un.nunits - un.nlight;
     return TG_OK;
 }
 
@@ -805,33 +900,49 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
     TG_TRY(timing_begin(s, &work));
     // tau for every edge of the graph (the identities need tau of edges
     // outside the counted range as well)
-    DevBuf<uint32_t> tau, theta, dsum, ustart;
-    uint32_t nunits = 0;
+    DevBuf<uint32_t> tau, theta, dsum;
+    tg_units un;
     if (!tau.alloc((size_t)M * L, s)) return TG_ENOMEM;
     {
         // tau of every edge, in the grouped order of the whole graph
         const uint32_t *ord = full_order;
-        TG_TRY(edge_units(g, ord, M, s, ustart, &nunits));
+        TG_TRY(edge_units(g, ord, M, s, un));
         DevBuf<unsigned long long> q;
-        if (!q.alloc(1, s)) return TG_ENOMEM;
-        TG_TRY_CUDA(cudaMemsetAsync(q.p, 0, 8, s));
+        if (!q.alloc(2, s)) return TG_ENOMEM;
+        TG_TRY_CUDA(cudaMemsetAsync(q.p, 0, 16, s));
         TG_TRY_CUDA(cudaEventRecord(g_last.ev[0], s));
-        const size_t avail = (size_t)smem_optin_r();
-        int64_t nbits = g->n_nonisolated;
-        if (t.bitmap_bits > 0 && nbits > t.bitmap_bits) nbits = t.bitmap_bits;
-        const int64_t maxb = (int64_t)((avail - 64) / 16) * 128;
-        if (nbits > maxb) nbits = maxb;
-        const size_t smem = ((((size_t)((nbits + 31) >> 5)) * 4 + 15) & ~(size_t)15) + 16;
-        TG_TRY(tg_allow_max_smem((const void *)k_tau));
-        int per_sm = 0;
-        TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tau, 512, smem));
-        if (per_sm < 1) per_sm = 1;
-        int64_t grid = (int64_t)num_sms_r() * per_sm;
-        if (grid > (int64_t)nunits) grid = nunits;
-        if (grid < 1) grid = 1;
-        k_tau<<<(unsigned)grid, 512, smem, s>>>(g->rowptr, g->adj, g->toff, g->edges, ord,
-                                                ustart.p, nunits, L, nbits, q.p, tau.p); tg_note_launch();
-        TG_TRY_CUDA(cudaGetLastError());
+        if (un.nheavy > 0) {
+            const size_t avail = (size_t)smem_optin_r();
+            int64_t nbits = g->n_nonisolated;
+            if (t.bitmap_bits > 0 && nbits > t.bitmap_bits) nbits = t.bitmap_bits;
+            const int64_t maxb = (int64_t)((avail - 64) / 16) * 128;
+            if (nbits > maxb) nbits = maxb;
+            const size_t smem = ((((size_t)((nbits + 31) >> 5)) * 4 + 15) & ~(size_t)15) + 16;
+            TG_TRY(tg_allow_max_smem((const void *)k_tau));
+            int per_sm = 0;
+            TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tau, 512, smem));
+            if (per_sm < 1) per_sm = 1;
+            int64_t grid = (int64_t)num_sms_r() * per_sm;
+            if (grid > (int64_t)un.nheavy) grid = un.nheavy;
+            if (grid < 1) grid = 1;
+            k_tau<<<(unsigned)grid, 512, smem, s>>>(g->rowptr, g->adj, g->toff, g->edges, ord,
+                                                    un.ustart.p, un.heavy.p, un.nheavy, L, nbits,
+                                                    q.p, tau.p); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+        }
+        if (un.nlight > 0) {
+            int per_sm = 0;
+            TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tau_light,
+                                                                      kLightWarps * 32, 0));
+            if (per_sm < 1) per_sm = 1;
+            int64_t grid = (int64_t)num_sms_r() * per_sm;
+            const int64_t need = ((int64_t)un.nlight + kLightWarps - 1) / kLightWarps;
+            if (grid > need) grid = need;
+            k_tau_light<<<(unsigned)grid, kLightWarps * 32, 0, s>>>(
+                g->rowptr, g->adj, g->edges, ord, un.ustart.p, un.light.p, un.nlight, L, q.p + 1,
+                tau.p); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+        }
     }
     TG_TRY_CUDA(cudaEventRecord(g_last.ev[1], s));
     if (k == 4) {
@@ -864,14 +975,13 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
         TG_TRY_CUDA(cudaEventRecord(g_last.ev[3], s));
         if (k == 4) TG_TRY(tg_cyc_cliques(g, k4e.p, g4k.p, work, t, s));
         TG_TRY_CUDA(cudaEventRecord(g_last.ev[4], s));
-        DevBuf<uint32_t> ust2;
-        const uint32_t *ust = ustart.p;
-        uint32_t nun = nunits;
+        tg_units un2;
+        tg_units *ue = &un;
         if (order != full_order || count != M) {
-            TG_TRY(edge_units(g, order, count, s, ust2, &nun));
-            ust = ust2.p;
+            TG_TRY(edge_units(g, order, count, s, un2));
+            ue = &un2;
         }
-        TG_TRY(tg_cyc_edges(g, k, level, order, count, ust, nun, rows, width, hist, tau.p, theta.p,
+        TG_TRY(tg_cyc_edges(g, k, level, order, count, *ue, rows, width, hist, tau.p, theta.p,
                             dsum.p, c4e.p, k4e.p, work, t, s));
         if (fast) TG_TRY(tg_cyc_correct(hist, L, g4c.p, g4k.p, s));
         TG_TRY_CUDA(cudaEventRecord(g_last.ev[5], s));
