@@ -82,7 +82,6 @@ struct C4Params {
                                // and an n-entry list of the far ends met; counters zero
                                // on entry and on exit
     int64_t slot_words;
-    unsigned int *slot_nb;     // split kernel: far ends listed per slot of the wave
     unsigned long long *queue;
     unsigned long long *c4e;   // per-edge mode: M * L * L, [type next to i][type next to j]
     unsigned long long *g4;    // global mode: C(L+3,4) non-induced 4-cycles by type multiset
@@ -179,7 +178,11 @@ __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta,
         uint32_t *cb = cnt + (int64_t)b * (L + 1);
         if (phase == 0) {
             atomicAdd(cb + tu, 1u);
-            if (atomicAdd(cb + L, 1u) == 0u) list[atomicAdd(nb, 1u)] = b;
+            if (list) {
+                if (atomicAdd(cb + L, 1u) == 0u) list[atomicAdd(nb, 1u)] = b;
+            } else {
+                atomicAdd(cb + L, 1u);  // result unused: no round trip
+            }
             ++wk;
             continue;
         }
@@ -215,40 +218,44 @@ __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta,
     }
 }
 
-// For the listed far ends b of anchor a (entries q0, q0 + step, ... < nb):
-// global mode adds the cycles per type pair of middles (C(c_t, 2) for t = t',
-// c_t c_t' for t < t') under the multiset {a, b, t, t'}; both modes then clear
-// b's counters.
+// Far end b of anchor a (counters cb: per type, then the total): global mode
+// adds the cycles per type pair of middles (C(c_t, 2) for t = t', c_t c_t'
+// for t < t') under the multiset {a, b, t, t'}; both modes then clear b's
+// counters.
+__device__ __forceinline__ void c4_one(const C4Params &p, const C4Smem &sm, int ta, uint32_t *cb,
+                                       uint32_t b) {
+    const int L = p.L;
+    if (p.g4 && __ldcg(cb + L) >= 2u) {
+        const int tb = p.ntype[b];
+        uint32_t c[TG_MAX_TYPES];
+#pragma unroll
+        for (int t = 0; t < TG_MAX_TYPES; ++t) c[t] = t < L ? __ldcg(cb + t) : 0u;
+        int s0 = ta, s1 = tb;
+        sort2(s0, s1);
+        for (int t = 0; t < L; ++t) {
+            if (!c[t]) continue;
+            for (int u = t; u < L; ++u) {
+                const unsigned long long v =
+                    u == t ? (unsigned long long)c[t] * (c[t] - 1) / 2 : (unsigned long long)c[t] * c[u];
+                if (!v) continue;
+                int q0s = s0, q1s = s1, q2s = t, q3s = u;
+                sort2(q0s, q2s);
+                sort2(q1s, q3s);
+                sort2(q1s, q2s);
+                atomicAdd(sm.h4 + colex4(q0s, q1s, q2s, q3s), v);
+            }
+        }
+    }
+    for (int t = 0; t <= L; ++t) cb[t] = 0u;
+}
+
+// The listed far ends of anchor a (entries q0, q0 + step, ... < nb).
 __device__ __forceinline__ void c4_pairs(const C4Params &p, const C4Smem &sm, int ta,
                                          uint32_t *cnt, const uint32_t *list, unsigned int nb,
                                          unsigned int q0, unsigned int step) {
-    const int L = p.L;
     for (unsigned int q = q0; q < nb; q += step) {
         const uint32_t b = __ldcg(list + q);  // written by other threads this anchor
-        uint32_t *cb = cnt + (int64_t)b * (L + 1);
-        if (p.g4 && __ldcg(cb + L) >= 2u) {
-            const int tb = p.ntype[b];
-            uint32_t c[TG_MAX_TYPES];
-#pragma unroll
-            for (int t = 0; t < TG_MAX_TYPES; ++t) c[t] = t < L ? __ldcg(cb + t) : 0u;
-            int s0 = ta, s1 = tb;
-            sort2(s0, s1);
-            for (int t = 0; t < L; ++t) {
-                if (!c[t]) continue;
-                for (int u = t; u < L; ++u) {
-                    const unsigned long long v =
-                        u == t ? (unsigned long long)c[t] * (c[t] - 1) / 2
-                               : (unsigned long long)c[t] * c[u];
-                    if (!v) continue;
-                    int q0s = s0, q1s = s1, q2s = t, q3s = u;
-                    sort2(q0s, q2s);
-                    sort2(q1s, q3s);
-                    sort2(q1s, q2s);
-                    atomicAdd(sm.h4 + colex4(q0s, q1s, q2s, q3s), v);
-                }
-            }
-        }
-        for (int t = 0; t <= L; ++t) cb[t] = 0u;
+        c4_one(p, sm, ta, cnt + (int64_t)b * (p.L + 1), b);
     }
 }
 
@@ -319,46 +326,32 @@ __global__ void __launch_bounds__(kC4Threads) k_c4_split(C4Params p) {
         const int64_t ba = p.rowptr[a];
         const int da = (int)(p.rowptr[a + 1] - ba);
         uint32_t *cnt = p.scratch + (int64_t)un.x * p.slot_words;
-        c4_tile(p, sm, a, p.ntype[a], ba, da, un.z, p.phase, cnt, cnt + p.n * (p.L + 1),
-                p.slot_nb + un.x, wk);
+        c4_tile(p, sm, a, p.ntype[a], ba, da, un.z, p.phase, cnt, nullptr, nullptr, wk);
     }
     c4_finish(p, sm, wk);
 }
 
-// The listed far ends of the wave's split anchors (na slots, anchors[slot]
-// the anchor of a slot): one grid-stride over the concatenated lists, so a
-// long list is shared by every CTA.
+// The far ends of the wave's split anchors (na slots, anchors[slot] the
+// anchor of a slot): one coalesced grid-stride over the slots' counters, so a
+// long list of far ends is shared by every CTA and pass 0 needs no returning
+// atomic to list them.
 __global__ void __launch_bounds__(kC4Threads) k_c4_pairs(C4Params p, const uint32_t *anchors,
                                                          int na) {
     extern __shared__ __align__(16) unsigned char smem[];
     const C4Smem sm = c4_smem(smem, p.tile, p.acc_l2);
-    // inclusive prefix of the list lengths, in the member arrays of the smem
-    unsigned long long *pre = reinterpret_cast<unsigned long long *>(sm.m_end);
-    if (threadIdx.x == 0) {
-        unsigned long long run = 0;
-        for (int q = 0; q < na; ++q) {
-            run += p.slot_nb[q];
-            pre[q] = run;
-        }
-    }
-    if (p.g4)
+    if (p.g4) {
         for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x) sm.h4[q] = 0ull;
-    __syncthreads();
-    const unsigned long long total = pre[na - 1];
+        __syncthreads();
+    }
     const int L = p.L;
-    for (unsigned long long g = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; g < total;
-         g += (unsigned long long)gridDim.x * blockDim.x) {
-        int lo = 0, hi = na - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (pre[mid] > g)
-                hi = mid;
-            else
-                lo = mid + 1;
-        }
-        const unsigned int q = (unsigned int)(g - (lo ? pre[lo - 1] : 0ull));
-        uint32_t *cnt = p.scratch + (int64_t)lo * p.slot_words;
-        c4_pairs(p, sm, p.ntype[anchors[lo]], cnt, cnt + p.n * (L + 1), q + 1, q, 1);
+    const int64_t total = (int64_t)na * p.n;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = g / p.n;
+        const uint32_t b = (uint32_t)(g - slot * p.n);
+        uint32_t *cb = p.scratch + slot * p.slot_words + (int64_t)b * (L + 1);
+        if (__ldcg(cb + L) == 0u) continue;
+        c4_one(p, sm, p.ntype[anchors[slot]], cb, b);
     }
     c4_finish(p, sm, 0ull);
 }
@@ -1527,10 +1520,8 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
         slots = 1;
     }
     DevBuf<uint32_t> scratch, wave_anchor;
-    DevBuf<unsigned int> slot_nb;
     DevBuf<unsigned long long> queue;
-    if (!scratch.alloc((size_t)slots * slot_words, s) || !queue.alloc(1, s) ||
-        !slot_nb.alloc(slots, s))
+    if (!scratch.alloc((size_t)slots * slot_words, s) || !queue.alloc(1, s))
         return TG_ENOMEM;
     TG_TRY_CUDA(cudaMemsetAsync(scratch.p, 0, (size_t)slots * slot_bytes, s));
     C4Params p{};
@@ -1549,14 +1540,11 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     p.g4 = g4;
     p.n4 = n4;
     p.split = split.p;
-    p.slot_nb = slot_nb.p;
     p.work = work;
 
     // split anchors, in waves of at most `slots` anchors
     if (nheavy > 0) {
-        // a wave holds at most 2 TM anchors: k_c4_pairs keeps their list
-        // lengths' prefix in the 2 TM member words of its shared memory
-        const int64_t wave = std::min<int64_t>(slots, 2 * (int64_t)TM);
+        const int64_t wave = slots;
         std::vector<int4> units;
         std::vector<int64_t> wave_start;
         for (int64_t q0 = 0; q0 < nheavy; q0 += wave) {
@@ -1578,7 +1566,6 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
             p.units = du.p + u0;
             p.n_units = nu;
             const int64_t grid = std::min<int64_t>(full_grid, nu);
-            TG_TRY_CUDA(cudaMemsetAsync(slot_nb.p, 0, (size_t)na * sizeof(unsigned int), s));
             for (int ph = 0; ph < (global ? 1 : 2); ++ph) {
                 p.phase = ph;
                 TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
