@@ -424,7 +424,8 @@ typedef struct {
     double cycles_ms;         /* CYCLES: 4-cycle enumeration                 */
     double cliques_ms;        /* CYCLES: 4-clique enumeration                */
     uint64_t wedges;          /* CYCLES: degree-ordered wedges (per pass)    */
-    uint64_t clique_tests;    /* CYCLES: candidate tests of the clique search */
+    uint64_t clique_tests;    /* CYCLES: candidate tests of the clique search
+                                 (pairs (v, w) for the bitmap kernels)       */
     uint64_t cliques;         /* CYCLES: 4-cliques found                     */
 } tg_timing;
 

@@ -78,9 +78,9 @@ struct C4Params {
     int32_t L;
     int32_t tile;              // members staged per tile (<= blockDim.x)
     int32_t acc_l2;            // L * L in per-edge mode, 0 in global mode
-    uint32_t *scratch;         // slots of n * (L + 1) counters (per type, then the total)
-                               // and an n-entry list of the far ends met; counters zero
-                               // on entry and on exit
+    uint32_t *scratch;         // slots of n * (L + 1) counters (per type, then the total),
+                               // an n-entry list of the far ends met and a bitmap of them
+                               // (n bits); counters and bitmap zero on entry and on exit
     int64_t slot_words;
     unsigned long long *queue;
     unsigned long long *c4e;   // per-edge mode: M * L * L, [type next to i][type next to j]
@@ -181,7 +181,9 @@ __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta,
             if (list) {
                 if (atomicAdd(cb + L, 1u) == 0u) list[atomicAdd(nb, 1u)] = b;
             } else {
-                atomicAdd(cb + L, 1u);  // result unused: no round trip
+                // results unused: no round trip; the bitmap marks b for the scan
+                atomicAdd(cb + L, 1u);
+                atomicOr(cnt + p.n * (L + 2) + (b >> 5), 1u << (b & 31u));
             }
             ++wk;
             continue;
@@ -332,9 +334,9 @@ __global__ void __launch_bounds__(kC4Threads) k_c4_split(C4Params p) {
 }
 
 // The far ends of the wave's split anchors (na slots, anchors[slot] the
-// anchor of a slot): one coalesced grid-stride over the slots' counters, so a
+// anchor of a slot): one grid-stride over the slots' bitmaps of far ends, so a
 // long list of far ends is shared by every CTA and pass 0 needs no returning
-// atomic to list them.
+// atomic to list them.  Clears the bitmap words it reads.
 __global__ void __launch_bounds__(kC4Threads) k_c4_pairs(C4Params p, const uint32_t *anchors,
                                                          int na) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -344,14 +346,22 @@ __global__ void __launch_bounds__(kC4Threads) k_c4_pairs(C4Params p, const uint3
         __syncthreads();
     }
     const int L = p.L;
-    const int64_t total = (int64_t)na * p.n;
+    const int64_t words = (p.n + 31) >> 5;
+    const int64_t total = (int64_t)na * words;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t slot = g / p.n;
-        const uint32_t b = (uint32_t)(g - slot * p.n);
-        uint32_t *cb = p.scratch + slot * p.slot_words + (int64_t)b * (L + 1);
-        if (__ldcg(cb + L) == 0u) continue;
-        c4_one(p, sm, p.ntype[anchors[slot]], cb, b);
+        const int64_t slot = g / words, wi = g - slot * words;
+        uint32_t *cnt = p.scratch + slot * p.slot_words;
+        uint32_t *bw = cnt + p.n * (L + 2) + wi;
+        uint32_t m = __ldcg(bw);
+        if (!m) continue;
+        *bw = 0u;
+        const int ta = p.ntype[anchors[slot]];
+        while (m) {
+            const uint32_t b = (uint32_t)(wi * 32 + __ffs(m) - 1);
+            m &= m - 1;
+            c4_one(p, sm, ta, cnt + (int64_t)b * (L + 1), b);
+        }
     }
     c4_finish(p, sm, 0ull);
 }
@@ -707,6 +717,7 @@ struct K4GParams {
     int32_t L;
     int32_t cap;  // set entries per warp (tables of 2^hlg >= 2 cap slots)
     int32_t hlg;
+    int32_t min_d0;  // k_k4_global: only x0 with up lists longer than this
     unsigned long long *queue;
     unsigned long long *g4;
     int64_t n4;
@@ -757,7 +768,7 @@ __global__ void __launch_bounds__(kK4GWarps * 32) k_k4_global(K4GParams p) {
         while (__ldg(p.uoff + x0 + 1) <= qq) ++x0;
         const int64_t b0 = __ldg(p.uoff + x0);
         const int d0 = (int)(__ldg(p.uoff + x0 + 1) - b0);
-        if (d0 < 3) continue;  // x0 is the lowest node: three more above it
+        if (d0 < 3 || d0 <= p.min_d0) continue;  // three more above x0; or a bitmap kernel's
         const int t0 = p.ntype[x0];
         const int32_t *to0 = p.utoff + x0 * (L + 1);
         if (x0 != cur) {
@@ -879,6 +890,193 @@ __global__ void __launch_bounds__(kK4GWarps * 32) k_k4_global(K4GParams p) {
     if (p.work) {
         if (wk_cand) atomicAdd(p.work + 5, wk_cand);
         if (wk_k4) atomicAdd(p.work + 6, wk_k4);
+    }
+}
+
+// 4-cliques by type multiset (global mode) from bitmaps.  The cliques whose
+// lowest node is x0 are the triangles of the graph on up(x0): with bm_v the
+// set of positions (in x0's up list) of up(v) n up(x0), every clique
+// x0 < v < w < x is met once, at the pair (v, w in bm_v), as a bit of
+// bm_v & bm_w; up(x0) is sorted by (type, id), so the bits of one type form a
+// contiguous range and popc(bm_v & bm_w & mask_t) counts the cliques whose
+// fourth node has type t.
+constexpr int kBitsWarpMax = 32;    // up lists of at most 32: one word, one warp
+constexpr int kBitsCtaMax = 1024;   // up to 1024: shared-memory bitmaps, one CTA
+constexpr int kBitsWarps = 8;
+
+__device__ __forceinline__ uint32_t range_mask(int lo, int hi) {  // bits [lo, hi) of a word
+    lo = max(0, min(32, lo));
+    hi = max(0, min(32, hi));
+    if (hi <= lo) return 0u;
+    const uint32_t h = hi == 32 ? 0xffffffffu : ((1u << hi) - 1u);
+    const uint32_t l = lo == 32 ? 0xffffffffu : ((1u << lo) - 1u);
+    return h & ~l;
+}
+
+__device__ __forceinline__ void k4_hist_add(unsigned long long *h4, int a, int b, int c, int d,
+                                            unsigned long long v) {
+    sort2(a, b);
+    sort2(c, d);
+    sort2(a, c);
+    sort2(b, d);
+    sort2(b, c);
+    atomicAdd(h4 + colex4(a, b, c, d), v);
+}
+
+__global__ void __launch_bounds__(kBitsWarps * 32) k_k4_bits_warp(K4GParams p) {
+    __shared__ uint32_t hk[kBitsWarps][2 * kBitsWarpMax], hv[kBitsWarps][2 * kBitsWarpMax];
+    __shared__ uint32_t tmask[kBitsWarps][TG_MAX_TYPES];
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *h4 = reinterpret_cast<unsigned long long *>(smem);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int L = p.L;
+    for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x) h4[q] = 0ull;
+    __syncthreads();
+    unsigned long long wk = 0, wpairs = 0;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(p.queue, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= (unsigned long long)p.n) break;
+        const uint32_t x0 = (uint32_t)item;
+        const int64_t b0 = __ldg(p.uoff + x0);
+        const int d0 = (int)(__ldg(p.uoff + x0 + 1) - b0);
+        if (d0 < 3 || d0 > kBitsWarpMax) continue;
+        const int t0 = p.ntype[x0];
+        const int32_t *to0 = p.utoff + (int64_t)x0 * (L + 1);
+        // position of every up(x0) member, and the type ranges as masks
+        hk[warp][lane] = 0u;
+        hk[warp][lane + 32] = 0u;
+        if (lane < L) tmask[warp][lane] = range_mask(__ldg(to0 + lane), __ldg(to0 + lane + 1));
+        __syncwarp();
+        const uint32_t ve = lane < d0 ? __ldg(p.uadj + b0 + lane) : 0u;
+        if (lane < d0) hmap_put(hk[warp], hv[warp], 6, ve & TG_IDMASK, (uint32_t)lane);
+        __syncwarp();
+        // bm of the member at position pv, one member at a time
+        uint32_t mine = 0;
+        for (int pv = 0; pv < d0; ++pv) {
+            const uint32_t v = __shfl_sync(kFull, ve, pv) & TG_IDMASK;
+            const int64_t bv = __ldg(p.uoff + v);
+            const int dv = (int)(__ldg(p.uoff + v + 1) - bv);
+            uint32_t acc = 0;
+            for (int c = lane; c < dv; c += 32) {
+                const uint32_t y = __ldg(p.uadj + bv + c) & TG_IDMASK;
+                const uint32_t pos = hmap_get(hk[warp], hv[warp], 6, y);
+                if (pos != 0xffffffffu) acc |= 1u << pos;
+            }
+            acc = __reduce_or_sync(kFull, acc);
+            if (lane == pv) mine = acc;
+        }
+        // pairs (v, w in bm_v): lane pv takes the members w of its bitmap in turn
+        const int tv = (int)(ve >> TG_TSHIFT);
+        uint32_t m = lane < d0 ? mine : 0u;
+        while (__any_sync(kFull, m != 0u)) {
+            const int q = m ? __ffs(m) - 1 : 0;
+            const uint32_t bw = __shfl_sync(kFull, mine, q);
+            const int tw = (int)(__shfl_sync(kFull, ve, q) >> TG_TSHIFT);
+            if (m) {
+                const uint32_t both = mine & bw;
+                for (int t = 0; t < L; ++t) {
+                    const int c = __popc(both & tmask[warp][t]);
+                    if (c) k4_hist_add(h4, t0, tv, tw, t, (unsigned long long)c);
+                }
+                wk += __popc(both);
+                ++wpairs;
+                m &= m - 1;
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x)
+        if (h4[q]) atomicAdd(p.g4 + q, h4[q]);
+    if (p.work && wk) atomicAdd(p.work + 6, wk);
+    if (p.work && wpairs) atomicAdd(p.work + 5, wpairs);
+}
+
+// Up lists of 33..kBitsCtaMax: one CTA per x0 (from `list`), bitmaps in shared
+// memory.
+__global__ void __launch_bounds__(256) k_k4_bits_cta(K4GParams p, const uint32_t *list,
+                                                    uint32_t nlist) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const int L = p.L;
+    unsigned long long *h4 = reinterpret_cast<unsigned long long *>(smem);
+    const size_t h4b = ((size_t)p.n4 * 8 + 15) & ~(size_t)15;
+    constexpr int kLg = 11;  // 2048 slots for up to 1024 members
+    uint32_t *hk = reinterpret_cast<uint32_t *>(smem + h4b);
+    uint32_t *hv = hk + (1 << kLg);
+    uint32_t *tm = hv + (1 << kLg);          // TG_MAX_TYPES x 32 words
+    uint32_t *ty = tm + TG_MAX_TYPES * 32;   // types of the positions
+    uint32_t *bm = ty + kBitsCtaMax;         // d0 x words
+    __shared__ unsigned long long s_item;
+    for (int64_t q = tid; q < p.n4; q += blockDim.x) h4[q] = 0ull;
+    unsigned long long wk = 0, wpairs = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_item = atomicAdd(p.queue, 1ull);
+        __syncthreads();
+        const unsigned long long item = s_item;
+        if (item >= nlist) break;
+        const uint32_t x0 = list[item];
+        const int64_t b0 = __ldg(p.uoff + x0);
+        const int d0 = (int)(__ldg(p.uoff + x0 + 1) - b0);
+        const int words = (d0 + 31) >> 5;
+        const int t0 = p.ntype[x0];
+        const int32_t *to0 = p.utoff + (int64_t)x0 * (L + 1);
+        for (int q = tid; q < (1 << kLg); q += blockDim.x) hk[q] = 0u;
+        for (int q = tid; q < d0 * words; q += blockDim.x) bm[q] = 0u;
+        for (int q = tid; q < L * words; q += blockDim.x) {
+            const int t = q / words, k = q % words;
+            tm[t * 32 + k] = range_mask(__ldg(to0 + t) - 32 * k, __ldg(to0 + t + 1) - 32 * k);
+        }
+        __syncthreads();
+        for (int q = tid; q < d0; q += blockDim.x) {
+            const uint32_t e = __ldg(p.uadj + b0 + q);
+            hmap_put(hk, hv, kLg, e & TG_IDMASK, (uint32_t)q);
+            ty[q] = e >> TG_TSHIFT;
+        }
+        __syncthreads();
+        for (int pv = warp; pv < d0; pv += W) {
+            const uint32_t v = __ldg(p.uadj + b0 + pv) & TG_IDMASK;
+            const int64_t bv = __ldg(p.uoff + v);
+            const int dv = (int)(__ldg(p.uoff + v + 1) - bv);
+            for (int c = lane; c < dv; c += 32) {
+                const uint32_t pos = hmap_get(hk, hv, kLg, __ldg(p.uadj + bv + c) & TG_IDMASK);
+                if (pos != 0xffffffffu) atomicOr(bm + pv * words + (pos >> 5), 1u << (pos & 31u));
+            }
+        }
+        __syncthreads();
+        // pairs: warp per v, lanes over the positions w of its bitmap
+        for (int pv = warp; pv < d0; pv += W) {
+            const volatile uint32_t *bv = bm + pv * words;
+            const int tv = (int)ty[pv];
+            for (int q = lane; q < d0; q += 32) {
+                if (!((bv[q >> 5] >> (q & 31)) & 1u)) continue;
+                const volatile uint32_t *bq = bm + q * words;
+                const int tw = (int)ty[q];
+                for (int t = 0; t < L; ++t) {
+                    int c = 0;
+                    for (int k = 0; k < words; ++k) c += __popc(bv[k] & bq[k] & tm[t * 32 + k]);
+                    if (c) k4_hist_add(h4, t0, tv, tw, t, (unsigned long long)c);
+                    wk += (unsigned long long)c;
+                }
+                ++wpairs;
+            }
+        }
+    }
+    __syncthreads();
+    for (int64_t q = tid; q < p.n4; q += blockDim.x)
+        if (h4[q]) atomicAdd(p.g4 + q, h4[q]);
+    if (p.work && wk) atomicAdd(p.work + 6, wk);
+    if (p.work && wpairs) atomicAdd(p.work + 5, wpairs);
+}
+
+__global__ void k_flag_range(const int64_t *uoff, int64_t n, int lo, int hi, uint32_t *flag) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = uoff[v + 1] - uoff[v];
+        flag[v] = (d >= lo && d <= hi) ? 1u : 0u;
     }
 }
 
@@ -1476,8 +1674,8 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     TG_TRY_CUDA(cudaMemcpyAsync(&tot, total.p, 8, cudaMemcpyDeviceToHost, s));
     TG_TRY_CUDA(cudaStreamSynchronize(s));
     // unroll selects the split rule: 1 none, 4 every anchor, else by cost
-    unsigned long long thr = std::max<unsigned long long>(tot / (unsigned long long)(2 * full_grid),
-                                                          (unsigned long long)1 << 16);
+    unsigned long long thr = std::max<unsigned long long>(tot / (unsigned long long)(16 * full_grid),
+                                                          (unsigned long long)1 << 12);
     if (t.unroll == 1) thr = ~0ull;
     if (t.unroll == 4) thr = 0ull;
     const unsigned egrid = (unsigned)std::min<int64_t>((n + 255) / 256, 65535LL * 16);
@@ -1508,7 +1706,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
 
     // counter slots: one per CTA of the one-CTA kernel, one per split anchor of
     // a wave; all within a quarter of free memory
-    const int64_t slot_words = n * (L + 2);
+    const int64_t slot_words = n * (L + 2) + (n + 31) / 32;
     const size_t slot_bytes = (size_t)slot_words * 4;
     size_t free_b = 0, total_b = 0;
     TG_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
@@ -1641,11 +1839,72 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
         unsigned long long maxup = 0;
         TG_TRY_CUDA(cudaMemcpyAsync(&maxup, mx.p, 8, cudaMemcpyDeviceToHost, s));
         TG_TRY_CUDA(cudaStreamSynchronize(s));
+        const size_t h4b = ((size_t)n4 * 8 + 15) & ~(size_t)15;
+        K4GParams q{};
+        q.uoff = uoff.p;
+        q.uadj = uadj.p;
+        q.utoff = utoff.p;
+        q.ntype = g->ntype;
+        q.n = n;
+        q.m = g->M;
+        q.L = L;
+        q.queue = queue.p;
+        q.g4 = g4;
+        q.n4 = n4;
+        q.work = work;
+        // bitmap kernels for up lists up to kBitsCtaMax (a hash_slots cap
+        // below 64 sends every x0 to the hash-set kernel instead)
+        const int bits_max = t.hash_slots >= 64 ? kBitsCtaMax : 0;
+        if (bits_max > 0) {
+            TG_TRY(tg_allow_max_smem((const void *)k_k4_bits_warp));
+            int wper = 0;
+            TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_k4_bits_warp,
+                                                                      kBitsWarps * 32, h4b));
+            if (wper < 1) wper = 1;
+            int64_t wgrid2 = (int64_t)num_sms_c() * wper;
+            if (wgrid2 > (n + kBitsWarps - 1) / kBitsWarps) wgrid2 = (n + kBitsWarps - 1) / kBitsWarps;
+            if (wgrid2 < 1) wgrid2 = 1;
+            k_k4_bits_warp<<<(unsigned)wgrid2, kBitsWarps * 32, h4b, s>>>(q); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+            if (maxup > (unsigned long long)kBitsWarpMax) {
+                DevBuf<uint32_t> flag, pos, list;
+                if (!flag.alloc(n, s) || !pos.alloc(n, s) || !list.alloc(n, s)) return TG_ENOMEM;
+                const unsigned egrid = (unsigned)std::min<int64_t>((n + 255) / 256, 65535LL * 16);
+                k_flag_range<<<egrid, 256, 0, s>>>(uoff.p, n, kBitsWarpMax + 1, bits_max, flag.p); tg_note_launch();
+                TG_TRY_CUDA(cudaGetLastError());
+                TG_TRY(tg_scan_u32(flag.p, pos.p, n, s));
+                k_c4_compact<<<egrid, 256, 0, s>>>(flag.p, pos.p, n, list.p); tg_note_launch();
+                TG_TRY_CUDA(cudaGetLastError());
+                uint32_t lastp = 0, lastf = 0;
+                TG_TRY_CUDA(cudaMemcpyAsync(&lastp, pos.p + n - 1, 4, cudaMemcpyDeviceToHost, s));
+                TG_TRY_CUDA(cudaMemcpyAsync(&lastf, flag.p + n - 1, 4, cudaMemcpyDeviceToHost, s));
+                TG_TRY_CUDA(cudaStreamSynchronize(s));
+                const uint32_t nlist = lastp + lastf;
+                if (nlist > 0) {
+                    const int dmax = (int)std::min<unsigned long long>(maxup, (unsigned long long)bits_max);
+                    const int wmax = (dmax + 31) / 32;
+                    const size_t csmem = h4b + (size_t)(2 * 2048 + TG_MAX_TYPES * 32 + kBitsCtaMax) * 4 +
+                                         (size_t)dmax * wmax * 4;
+                    TG_TRY(tg_allow_max_smem((const void *)k_k4_bits_cta));
+                    int cper = 0;
+                    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cper, k_k4_bits_cta, 256,
+                                                                              csmem));
+                    if (cper < 1) cper = 1;
+                    int64_t cgrid = (int64_t)num_sms_c() * cper;
+                    if (cgrid > nlist) cgrid = nlist;
+                    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
+                    k_k4_bits_cta<<<(unsigned)cgrid, 256, csmem, s>>>(q, list.p, nlist); tg_note_launch();
+                    TG_TRY_CUDA(cudaGetLastError());
+                }
+            }
+        }
+        if (maxup <= (unsigned long long)bits_max) return TG_OK;
+        // hash sets for the longer up lists, sized to the largest one, within
+        // the hash_slots cap
         int gcap = (int)std::min<unsigned long long>(std::min(1024, t.hash_slots), (maxup + 31) & ~31ull);
         if (gcap < 32) gcap = 32;
         int hlg = 5;
         while ((1 << hlg) < 2 * gcap) ++hlg;
-        const size_t h4b = ((size_t)n4 * 8 + 15) & ~(size_t)15;
         size_t gsmem = h4b + (size_t)kK4GWarps * (gcap + 2 * (1 << hlg)) * 4;
         while (gsmem > avail + hbytes && gcap > 32) {
             gcap -= 32;
@@ -1662,20 +1921,10 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
         const int64_t gneed = (g->M / kK4GChunk + kK4GWarps) / kK4GWarps;
         if (ggrid > gneed) ggrid = gneed;
         if (ggrid < 1) ggrid = 1;
-        K4GParams q{};
-        q.uoff = uoff.p;
-        q.uadj = uadj.p;
-        q.utoff = utoff.p;
-        q.ntype = g->ntype;
-        q.n = n;
-        q.m = g->M;
-        q.L = L;
         q.cap = gcap;
         q.hlg = hlg;
-        q.queue = queue.p;
-        q.g4 = g4;
-        q.n4 = n4;
-        q.work = work;
+        q.min_d0 = bits_max;
+        TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
         k_k4_global<<<(unsigned)ggrid, kK4GWarps * 32, gsmem, s>>>(q); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
         return TG_OK;
