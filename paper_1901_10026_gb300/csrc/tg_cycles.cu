@@ -78,8 +78,8 @@ struct C4Params {
     int32_t L;
     int32_t tile;              // members staged per tile (<= blockDim.x)
     int32_t acc_l2;            // L * L in per-edge mode, 0 in global mode
-    uint32_t *scratch;         // slots of n * (L + 1) counters (per type, then the total),
-                               // an n-entry list of the far ends met and a bitmap of them
+    uint32_t *scratch;         // slots of n * L counters (per far end, per type), an
+                               // n-entry list of the far ends met and a bitmap of them
                                // (n bits); counters and bitmap zero on entry and on exit
     int64_t slot_words;
     unsigned long long *queue;
@@ -175,23 +175,28 @@ __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta,
         if (b <= a) continue;  // b must rank below a (and differ from it)
         const uint32_t wmu = sm.m_u[lo];
         const int tu = (int)(wmu >> TG_TSHIFT);
-        uint32_t *cb = cnt + (int64_t)b * (L + 1);
+        uint32_t *cb = cnt + (int64_t)b * L;
         if (phase == 0) {
-            atomicAdd(cb + tu, 1u);
+            atomicAdd(cb + tu, 1u);  // result unused: no round trip
+            uint32_t *bw = cnt + p.n * (L + 1) + (b >> 5);
+            const uint32_t bit = 1u << (b & 31u);
             if (list) {
-                if (atomicAdd(cb + L, 1u) == 0u) list[atomicAdd(nb, 1u)] = b;
+                // the first wedge to reach b lists it
+                if (!(atomicOr(bw, bit) & bit)) list[atomicAdd(nb, 1u)] = b;
             } else {
-                // results unused: no round trip; the bitmap marks b for the scan
-                atomicAdd(cb + L, 1u);
-                atomicOr(cnt + p.n * (L + 2) + (b >> 5), 1u << (b & 31u));
+                atomicOr(bw, bit);  // marks b for the scan of k_c4_pairs
             }
             ++wk;
             continue;
         }
-        if (__ldcg(cb + L) < 2u) continue;  // no other middle: no cycle
         uint32_t c[TG_MAX_TYPES];
+        uint32_t sum = 0;
 #pragma unroll
-        for (int t = 0; t < TG_MAX_TYPES; ++t) c[t] = t < L ? __ldcg(cb + t) : 0u;
+        for (int t = 0; t < TG_MAX_TYPES; ++t) {
+            c[t] = t < L ? __ldcg(cb + t) : 0u;
+            sum += c[t];
+        }
+        if (sum < 2u) continue;  // no other middle: no cycle
         const int tb = (int)(wb >> TG_TSHIFT);
         const uint32_t u = wmu & TG_IDMASK;
         unsigned long long *row_ub = p.c4e + (int64_t)__ldg(p.eid + at) * L2;
@@ -220,14 +225,13 @@ __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta,
     }
 }
 
-// Far end b of anchor a (counters cb: per type, then the total): global mode
-// adds the cycles per type pair of middles (C(c_t, 2) for t = t', c_t c_t'
-// for t < t') under the multiset {a, b, t, t'}; both modes then clear b's
-// counters.
+// Far end b of anchor a (counters cb, per type): global mode adds the cycles
+// per type pair of middles (C(c_t, 2) for t = t', c_t c_t' for t < t') under
+// the multiset {a, b, t, t'}; both modes then clear b's counters.
 __device__ __forceinline__ void c4_one(const C4Params &p, const C4Smem &sm, int ta, uint32_t *cb,
                                        uint32_t b) {
     const int L = p.L;
-    if (p.g4 && __ldcg(cb + L) >= 2u) {
+    if (p.g4) {
         const int tb = p.ntype[b];
         uint32_t c[TG_MAX_TYPES];
 #pragma unroll
@@ -248,7 +252,7 @@ __device__ __forceinline__ void c4_one(const C4Params &p, const C4Smem &sm, int 
             }
         }
     }
-    for (int t = 0; t <= L; ++t) cb[t] = 0u;
+    for (int t = 0; t < L; ++t) cb[t] = 0u;
 }
 
 // The listed far ends of anchor a (entries q0, q0 + step, ... < nb).
@@ -257,7 +261,8 @@ __device__ __forceinline__ void c4_pairs(const C4Params &p, const C4Smem &sm, in
                                          unsigned int q0, unsigned int step) {
     for (unsigned int q = q0; q < nb; q += step) {
         const uint32_t b = __ldcg(list + q);  // written by other threads this anchor
-        c4_one(p, sm, ta, cnt + (int64_t)b * (p.L + 1), b);
+        c4_one(p, sm, ta, cnt + (int64_t)b * p.L, b);
+        cnt[p.n * (p.L + 1) + (b >> 5)] = 0u;  // every set bit of the word is listed
     }
 }
 
@@ -280,7 +285,7 @@ __global__ void __launch_bounds__(kC4Threads) k_c4(C4Params p) {
     if (p.g4)
         for (int64_t q = tid; q < p.n4; q += blockDim.x) sm.h4[q] = 0ull;
     uint32_t *cnt = p.scratch + (int64_t)blockIdx.x * p.slot_words;
-    uint32_t *list = cnt + p.n * (p.L + 1);
+    uint32_t *list = cnt + p.n * p.L;
     unsigned long long wk = 0;
     for (;;) {
         __syncthreads();
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(kC4Threads) k_c4_pairs(C4Params p, const uint3
          g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t slot = g / words, wi = g - slot * words;
         uint32_t *cnt = p.scratch + slot * p.slot_words;
-        uint32_t *bw = cnt + p.n * (L + 2) + wi;
+        uint32_t *bw = cnt + p.n * (L + 1) + wi;
         uint32_t m = __ldcg(bw);
         if (!m) continue;
         *bw = 0u;
@@ -360,7 +365,7 @@ __global__ void __launch_bounds__(kC4Threads) k_c4_pairs(C4Params p, const uint3
         while (m) {
             const uint32_t b = (uint32_t)(wi * 32 + __ffs(m) - 1);
             m &= m - 1;
-            c4_one(p, sm, ta, cnt + (int64_t)b * (L + 1), b);
+            c4_one(p, sm, ta, cnt + (int64_t)b * L, b);
         }
     }
     c4_finish(p, sm, 0ull);
@@ -1706,7 +1711,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
 
     // counter slots: one per CTA of the one-CTA kernel, one per split anchor of
     // a wave; all within a quarter of free memory
-    const int64_t slot_words = n * (L + 2) + (n + 31) / 32;
+    const int64_t slot_words = n * (L + 1) + (n + 31) / 32;
     const size_t slot_bytes = (size_t)slot_words * 4;
     size_t free_b = 0, total_b = 0;
     TG_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
