@@ -360,6 +360,7 @@ struct tg_batch {
     int ordered = 1;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    bool no_graph = false;  // enqueue the launches directly instead of replaying a graph
     std::mutex mu;
 };
 
@@ -395,8 +396,9 @@ static int batch_config(tg_batch *b, int64_t *grid, size_t *smem) {
     return TG_OK;
 }
 
-// Enqueue one run (reset, persistent count, finalize) on stream s.
-static int batch_enqueue(tg_batch *b, cudaStream_t s, int64_t grid, size_t smem) {
+// Enqueue one run (reset, persistent count, finalize) on stream s.  `note`:
+// count the launches (false while capturing: a replay counts them).
+static int batch_enqueue(tg_batch *b, cudaStream_t s, int64_t grid, size_t smem, bool note = true) {
     TG_TRY_CUDA(cudaMemsetAsync(b->d_queue, 0, 8, s));
     if (b->mode == TG_BATCH_GLOBAL) {
         TG_TRY_CUDA(cudaMemsetAsync(b->d_sums, 0, (size_t)b->sums_len * 8, s));
@@ -414,12 +416,14 @@ static int batch_enqueue(tg_batch *b, cudaStream_t s, int64_t grid, size_t smem)
         p.global = b->mode == TG_BATCH_GLOBAL;
         p.Pmax = b->Pmax;
         p.queue = b->d_queue;
-        k_batch_warp<<<(unsigned)grid, b->warps * 32, smem, s>>>(p); tg_note_launch();
+        k_batch_warp<<<(unsigned)grid, b->warps * 32, smem, s>>>(p);
+        if (note) tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
     }
     if (b->mode == TG_BATCH_GLOBAL && b->G > 0) {
         dim3 grid(4, (unsigned)b->G);
-        k_batch_finalize<<<grid, 256, 0, s>>>(b->d_gs, b->G, b->d_err); tg_note_launch();
+        k_batch_finalize<<<grid, 256, 0, s>>>(b->d_gs, b->G, b->d_err);
+        if (note) tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
     }
     return TG_OK;
@@ -443,7 +447,7 @@ static int batch_capture(tg_batch *b, cudaStream_t s) {
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         r = TG_ECUDA;
     } else {
-        const int r2 = batch_enqueue(b, cs, grid, smem);
+        const int r2 = batch_enqueue(b, cs, grid, smem, false);
         const cudaError_t e = cudaStreamEndCapture(cs, &b->graph);
         if (r2 != TG_OK) r = r2;
         else if (e != cudaSuccess) r = TG_ECUDA;
@@ -569,10 +573,19 @@ extern "C" int tg_batch_run(tg_batch *b, void *stream) {
     if (!b) return TG_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(b->mu);
-    if (!b->exec) TG_TRY(batch_capture(b, s));
-    TG_TRY_CUDA(cudaGraphLaunch(b->exec, s));
-    if (b->count > 0) tg_note_launch();                      // persistent count kernel
-    if (b->mode == TG_BATCH_GLOBAL && b->G > 0) tg_note_launch();  // finalize
+    // replay of the captured graph; when a capture cannot be made (or the plan
+    // asks for none) the same launches are enqueued directly
+    if (!b->exec && !b->no_graph && batch_capture(b, s) != TG_OK) b->no_graph = true;
+    if (b->exec && !b->no_graph) {
+        TG_TRY_CUDA(cudaGraphLaunch(b->exec, s));
+        if (b->count > 0) tg_note_launch();                      // persistent count kernel
+        if (b->mode == TG_BATCH_GLOBAL && b->G > 0) tg_note_launch();  // finalize
+    } else {
+        int64_t grid = 1;
+        size_t smem = 0;
+        TG_TRY(batch_config(b, &grid, &smem));
+        TG_TRY(batch_enqueue(b, s, grid, smem));
+    }
     if (b->mode == TG_BATCH_GLOBAL) {
         unsigned herr = 0;
         TG_TRY_CUDA(cudaMemcpyAsync(&herr, b->d_err, 4, cudaMemcpyDeviceToHost, s));
@@ -625,7 +638,8 @@ extern "C" int tg_batch_tune(tg_batch *b, void *stream, int32_t *best_threads) {
     b->warps = bw;
     b->ordered = bo;
     if (r != TG_OK) return r;
-    TG_TRY(batch_capture(b, s));
+    // the chosen configuration as a graph (runs enqueue directly if it fails)
+    if (!b->no_graph && batch_capture(b, s) != TG_OK) b->no_graph = true;
     if (best_threads) *best_threads = bw * 32 * (bo ? 1 : -1);
     return TG_OK;
 }
@@ -640,6 +654,7 @@ extern "C" int tg_count_batch(int32_t G, tg_graph *const *gs, int32_t k, int32_t
     tg_batch *b = nullptr;
     TG_TRY(tg_batch_create(G, gs, k, mode, outs, tune, stream, &b));
     int r = tune ? TG_OK : tg_batch_tune(b, stream, nullptr);
+    b->no_graph = true;  // one run: a graph would only add the capture
     if (r == TG_OK) r = tg_batch_run(b, stream);
     tg_batch_destroy(b);
     return r;
