@@ -1190,15 +1190,13 @@ struct EdgeEval {
     __device__ long long DSi(int a, int b) const {
         return (long long)__ldg(in.dvi + a * in.L + b) - DT(a, b) - (a == in.tj ? deg_j(b) : 0);
     }
-    __device__ long long G6(int a, int b) const {
-        // global mode: C4 is added from the 4-cycle totals
+    __device__ long long S6(int a, int b) const {
         const long long c4 = in.c4 ? (long long)__ldg(in.c4 + a * in.L + b) : 0;
-        const long long s6 = c4 - B(a, b) + (b == in.ti ? Tn(a) : 0);
-        return s6 - TSi(b, a);
+        return c4 - B(a, b) + (b == in.ti ? Tn(a) : 0);
     }
-    __device__ long long Y(int a, int b) const {
-        return DSi(a, b) - (b == in.ti ? Si(a) : 0) - SSi(a, b) - G6(a, b) + DSj(a, b) -
-               (b == in.tj ? Sj(a) : 0) - SSj(a, b) - G6(b, a);
+    __device__ long long Ypart(int a, int b) const {  // Y without its G6 terms
+        return DSi(a, b) - (b == in.ti ? Si(a) : 0) - SSi(a, b) + DSj(a, b) -
+               (b == in.tj ? Sj(a) : 0) - SSj(a, b);
     }
     __device__ long long Z(int a, int b) const {
         return DT(a, b) - Tn(a) * ((b == in.ti) + (b == in.tj)) - Q(a, b) - TSi(a, b) -
@@ -1206,23 +1204,51 @@ struct EdgeEval {
     }
 };
 
-// Orbits g3..g12 of the type pair (t, u), t <= u.
-__device__ __forceinline__ void pair_orbits(const EdgeEval &E, int t, int u, uint64_t g[10]) {
-    auto sym = [&](long long x_tu, long long x_ut) -> long long {
-        return t == u ? x_tu : x_tu + x_ut;
-    };
-    const long long q2 = sym(E.Q(t, u), E.Q(u, t));
-    const uint64_t g12 = (uint64_t)(q2 / 2);
-    const uint64_t g10 = (uint64_t)(sym(E.TSi(t, u) + E.TSj(t, u), E.TSi(u, t) + E.TSj(u, t)));
-    const long long sisi_tu = E.SSi(t, u) - E.TSi(u, t), sisi_ut = E.SSi(u, t) - E.TSi(t, u);
-    const long long sjsj_tu = E.SSj(t, u) - E.TSj(u, t), sjsj_ut = E.SSj(u, t) - E.TSj(t, u);
-    const uint64_t g7 = (uint64_t)(sym(sisi_tu + sjsj_tu, sisi_ut + sjsj_ut) / 2);
-    const uint64_t g6 = (uint64_t)sym(E.G6(t, u), E.G6(u, t));
-    const uint64_t g3 = (uint64_t)sym(E.Y(t, u), E.Y(u, t));
-    const uint64_t g8 = (uint64_t)sym(E.Z(t, u), E.Z(u, t));
-    const uint64_t sit = (uint64_t)E.Si(t), siu = (uint64_t)E.Si(u);
-    const uint64_t sjt = (uint64_t)E.Sj(t), sju = (uint64_t)E.Sj(u);
-    const uint64_t tt = (uint64_t)E.Tn(t), tu = (uint64_t)E.Tn(u);
+// Per-edge table of the identities' ordered L x L terms (one warp fills it,
+// one lane per entry), so a type pair reads its terms instead of re-deriving
+// them: TSi, TSj, SSi, SSj, G6 = S6 - TSi^T, Y without its G6 terms, Z, Q.
+enum { XT_TSI = 0, XT_TSJ, XT_SSI, XT_SSJ, XT_G6, XT_YP, XT_Z, XT_Q, XT_N };
+
+__device__ __forceinline__ void fill_terms(const EdgeEval &E, int L, long long *xt) {
+    const int lane = threadIdx.x & 31, L2 = L * L;
+    for (int m = lane; m < L2; m += 32) {
+        const int a = m / L, b = m % L;
+        xt[XT_TSI * L2 + m] = E.TSi(a, b);
+        xt[XT_TSJ * L2 + m] = E.TSj(a, b);
+        xt[XT_SSI * L2 + m] = E.SSi(a, b);
+        xt[XT_SSJ * L2 + m] = E.SSj(a, b);
+        xt[XT_YP * L2 + m] = E.Ypart(a, b);
+        xt[XT_Z * L2 + m] = E.Z(a, b);
+        xt[XT_Q * L2 + m] = E.Q(a, b);
+        xt[XT_G6 * L2 + m] = E.S6(a, b);
+    }
+    __syncwarp();
+    for (int m = lane; m < L2; m += 32) {
+        const int a = m / L, b = m % L;
+        xt[XT_G6 * L2 + m] -= xt[XT_TSI * L2 + b * L + a];
+    }
+    __syncwarp();
+}
+
+// Orbits g3..g12 of the type pair (t, u), t <= u, from the table.
+__device__ __forceinline__ void pair_orbits_tab(const long long *xt, int L, int t, int u,
+                                                uint64_t sit, uint64_t siu, uint64_t sjt,
+                                                uint64_t sju, uint64_t tt, uint64_t tu,
+                                                uint64_t g[10]) {
+    const int L2 = L * L, m = t * L + u, mt = u * L + t;
+    auto X = [&](int k, int mm) -> long long { return xt[k * L2 + mm]; };
+    auto sym = [&](int k) -> long long { return t == u ? X(k, m) : X(k, m) + X(k, mt); };
+    const uint64_t g12 = (uint64_t)(sym(XT_Q) / 2);
+    const uint64_t g10 = (uint64_t)(sym(XT_TSI) + sym(XT_TSJ));
+    const long long sisi_tu = X(XT_SSI, m) - X(XT_TSI, mt), sisi_ut = X(XT_SSI, mt) - X(XT_TSI, m);
+    const long long sjsj_tu = X(XT_SSJ, m) - X(XT_TSJ, mt), sjsj_ut = X(XT_SSJ, mt) - X(XT_TSJ, m);
+    const uint64_t g7 =
+        (uint64_t)((t == u ? sisi_tu + sjsj_tu : sisi_tu + sjsj_tu + sisi_ut + sjsj_ut) / 2);
+    const uint64_t g6 = (uint64_t)sym(XT_G6);
+    const long long y_tu = X(XT_YP, m) - X(XT_G6, m) - X(XT_G6, mt);
+    const long long y_ut = X(XT_YP, mt) - X(XT_G6, mt) - X(XT_G6, m);
+    const uint64_t g3 = (uint64_t)(t == u ? y_tu : y_tu + y_ut);
+    const uint64_t g8 = (uint64_t)sym(XT_Z);
     uint64_t g4, g5, g9, g11;
     if (t == u) {
         g4 = sit * sjt - g6;
@@ -1263,7 +1289,8 @@ __device__ __forceinline__ void hadd_e(const EdgeParams &p, unsigned long long *
 __device__ void edge_finish(const EdgeParams &p, unsigned long long *shist, int64_t e, int i, int j,
                             int ti, int tj, const int32_t *toi, const int32_t *toj,
                             const uint32_t *tn, const unsigned long long *Bm,
-                            const unsigned long long *Cm, const unsigned long long *Dm) {
+                            const unsigned long long *Cm, const unsigned long long *Dm,
+                            long long *xt) {
     const int lane = threadIdx.x & 31;
     const int L = p.L, P = p.P, L2 = L * L;
     // 2- and 3-node entries
@@ -1313,11 +1340,13 @@ __device__ void edge_finish(const EdgeParams &p, unsigned long long *shist, int6
         in.toi = toi;
         in.toj = toj;
         const EdgeEval E{in};
+        fill_terms(E, L, xt);
         for (int pr = lane; pr < P; pr += 32) {
             int t, u;
             unpair(L, pr, t, u);
             uint64_t g[10];
-            pair_orbits(E, t, u, g);
+            pair_orbits_tab(xt, L, t, u, (uint64_t)E.Si(t), (uint64_t)E.Si(u), (uint64_t)E.Sj(t),
+                            (uint64_t)E.Sj(u), (uint64_t)E.Tn(t), (uint64_t)E.Tn(u), g);
             if (p.rows) {
                 uint64_t *row = p.rows + e * p.width + 2 * L;
                 if (p.level == TG_ORBIT) {
@@ -1405,10 +1434,13 @@ __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc
     size_t off = 0;
     unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);
     if (p.hist_smem) off += ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
-    const size_t wbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
+    // per warp: B, C, DT, then (finishing here) the table of identity terms
+    const size_t tbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
+    const size_t wbytes = tbytes + (kWrite ? 0 : (size_t)XT_N * L2 * 8);
     unsigned long long *Bm = reinterpret_cast<unsigned long long *>(smem + off + warp * wbytes);
     unsigned long long *Cm = Bm + L2;
     unsigned long long *Dm = Cm + L2;
+    long long *xt = reinterpret_cast<long long *>(smem + off + warp * wbytes + tbytes);
     off += (size_t)W * wbytes;
     unsigned long long *s_unit = reinterpret_cast<unsigned long long *>(smem + off);
     off += 16;
@@ -1503,7 +1535,7 @@ __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc
                 unsigned long long *dst = p.tsum + (int64_t)q * 3 * L2;
                 for (int x = lane; x < 3 * L2; x += 32) dst[x] = Bm[x];
             } else {
-                edge_finish(p, shist, e, i, j, ti, tj, toi, toj, tn, Bm, Cm, Dm);
+                edge_finish(p, shist, e, i, j, ti, tj, toi, toj, tn, Bm, Cm, Dm, xt);
             }
             __syncwarp();  // this warp's matrices are cleared for the next edge
         }
@@ -1599,8 +1631,10 @@ __global__ void __launch_bounds__(256) k_cyc_finish(EdgeParams p, int64_t count)
     size_t off = 0;
     unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);
     if (p.hist_smem) off += ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
-    const size_t wbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
+    const size_t tbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
+    const size_t wbytes = tbytes + (size_t)XT_N * L2 * 8;
     unsigned long long *Bm = reinterpret_cast<unsigned long long *>(smem + off + warp * wbytes);
+    long long *xt = reinterpret_cast<long long *>(smem + off + warp * wbytes + tbytes);
     if (p.hist_smem) {
         for (int64_t x = tid; x < p.hist_len; x += blockDim.x) shist[x] = 0;
         __syncthreads();
@@ -1614,7 +1648,7 @@ __global__ void __launch_bounds__(256) k_cyc_finish(EdgeParams p, int64_t count)
         for (int x = lane; x < 3 * L2; x += 32) Bm[x] = __ldg(src + x);
         __syncwarp();
         edge_finish(p, shist, e, i, j, p.ntype[i], p.ntype[j], p.toff + (int64_t)i * (L + 1),
-                    p.toff + (int64_t)j * (L + 1), p.tau + e * L, Bm, Bm + L2, Bm + 2 * L2);
+                    p.toff + (int64_t)j * (L + 1), p.tau + e * L, Bm, Bm + L2, Bm + 2 * L2, xt);
         __syncwarp();
     }
     if (p.hist_smem) {
@@ -1993,7 +2027,9 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
     const size_t avail = (size_t)smem_optin_c() - 1024;
     const size_t hist_bytes = ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
     const int hist_smem = (!rows && hist_bytes <= 48 * 1024) ? 1 : 0;
-    const size_t wbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
+    // per warp: B, C, DT; the kernels that finish edges add the term table
+    const size_t tbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
+    const size_t xbytes = tbytes + (size_t)XT_N * L2 * 8;
     // B, C, DT through memory when they fit in a quarter of free memory
     const size_t tsum_bytes = (size_t)count * 3 * L2 * 8;
     size_t free_b = 0, total_b = 0;
@@ -2003,6 +2039,7 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
     if (threads > (split ? kTsumThreads : kEdgeMaxThreads)) threads = split ? kTsumThreads : kEdgeMaxThreads;
     if (threads < 32) threads = 32;
     p.hist_smem = split ? 0 : hist_smem;
+    const size_t wbytes = split ? tbytes : xbytes;
     size_t fixed = (p.hist_smem ? hist_bytes : 0) + (size_t)(threads / 32) * wbytes + 16;
     while (fixed + 4096 > avail && threads > 32) {
         threads -= 32;
@@ -2071,7 +2108,7 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
     }
     // finishing pass: warp per edge
     p.hist_smem = hist_smem;
-    const size_t fsmem = (hist_smem ? hist_bytes : 0) + (256 / 32) * wbytes;
+    const size_t fsmem = (hist_smem ? hist_bytes : 0) + (256 / 32) * xbytes;
     TG_TRY(tg_allow_max_smem((const void *)k_cyc_finish));
     int fper = 0;
     TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, k_cyc_finish, 256, fsmem));
