@@ -267,7 +267,10 @@ typedef struct {
                             grid: 1 none, 4 all, 2 (default) the costly ones */
     int32_t hash_slots;  /* slots of the per-edge Gamma_i hash (power of 2);
                             CYCLES kernel: cap on the 4-clique candidates
-                            staged per warp                                 */
+                            staged per warp and on the per-warp far-end
+                            table of the lightest 4-cycle anchors (global
+                            counts); below 64 the costly 4-cycle anchors are
+                            walked in member tiles instead of warp units    */
     int64_t bitmap_bits; /* cap on the node ids covered by the bitmap       */
     int32_t grid_limit;  /* cap on the CTAs of one counting launch          */
     int32_t reserved;

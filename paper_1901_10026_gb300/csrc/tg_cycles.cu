@@ -15,12 +15,15 @@
 //                 4-cliques through the edge.
 // Here both are accumulated per edge from enumerations of the whole graph in
 // degree order (a node ranks higher when its new id is smaller):
-//   4-cycles (k_c4): each non-induced 4-cycle a-u-b-u' is met once, at its
+//   4-cycles: each non-induced 4-cycle a-u-b-u' is met once, at its
 //     highest-ranked node a, as two wedges a-u-b and a-u'-b whose other nodes
 //     rank below a.  Per anchor a, pass 1 counts the middles u of the wedges
 //     ending at each b by type (c_t(b)); pass 2 adds, for every wedge, the
-//     cycles it closes with the other middles to its two edges; pass 3 clears
-//     the counters.
+//     cycles it closes with the other middles to its two edges (per-edge
+//     mode); the far ends then add C(c_t, 2) and c_t c_t' (global mode) and
+//     clear the counters.  Global mode keeps the counters of light anchors in
+//     shared memory (k_c4_warp, k_c4_cta) and walks costly ones in warp units
+//     over L2-sized waves of counter slots (k_c4_walk, k_c4_pairs).
 //   4-cliques (k_k4): each 4-clique x0 < v < w < x (by rank) is met once from
 //     its lowest node along "up" lists (neighbours of higher rank) and adds one
 //     to each of its six edges, keyed by the unordered types of the two nodes
@@ -86,14 +89,31 @@ struct C4Params {
     unsigned long long *c4e;   // per-edge mode: M * L * L, [type next to i][type next to j]
     unsigned long long *g4;    // global mode: C(L+3,4) non-induced 4-cycles by type multiset
     int64_t n4;
-    const uint8_t *split;      // one-CTA kernel: anchors marked here are skipped
-    const int4 *units;         // split kernel: (slot, anchor, first list position, 0)
+    const int4 *units;         // split kernel: (slot, anchor, first member, end member)
+    const struct C4Unit *wunits;  // walk kernel: position ranges of the split anchors
     int64_t n_units;
     int32_t phase;             // split kernel: the pass of this launch
+    int32_t mark;              // pass 0 marks far ends in the slot's bitmap
     unsigned long long *work;  // [4]: wedges
+    // dense waves (global mode): the costly anchors heavy[q], their walk
+    // positions (member costs d_u, exclusive prefix per anchor at pbase[q]),
+    // and the first anchor index of the wave (slot = q - q0)
+    const uint32_t *heavy;
+    const int64_t *mprefix;
+    const int64_t *pbase;
+    int64_t q0;
+};
+
+// A warp unit of k_c4_walk: positions [lo, hi) of the walk of split anchor
+// q, starting in the list of its member m.
+struct C4Unit {
+    int64_t lo, hi;
+    int32_t q, m;
 };
 
 constexpr int kC4Threads = 256;
+constexpr int64_t kWaveMax = 128;       // costly anchors of one wave (global mode), at most
+constexpr int64_t kWalkUnitMin = 512;    // walk positions of a warp unit, at least
 
 struct C4Smem {
     int64_t *m_end, *m_org;
@@ -118,15 +138,19 @@ __device__ __forceinline__ C4Smem c4_smem(unsigned char *smem, int TM, int acc_l
     return m;
 }
 
-// One pass over one tile of anchor a's list: the members u (neighbours ranked
-// below a) of the tile and, for each, the entries b of u's list ranked below
-// a.  Pass 0 counts the middles per (b, type) and their total, and lists each
-// b the first time it is met (in `list`, count in *nb); pass 1 (per-edge mode
-// only) adds the cycles each wedge closes to its two edges.  Called by every
-// thread of the CTA (it holds barriers).
-__device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta, int64_t ba,
-                        int da, int tile, int phase, uint32_t *cnt, uint32_t *list,
-                        unsigned int *nb, unsigned long long &wk) {
+// One pass over one tile of anchor a's list (list positions [tile, tile_end),
+// at most p.tile of them): the members u (neighbours ranked below a) of the
+// tile and, for each, the entries b of u's list ranked below a.  The members'
+// lists are walked as one sequence of positions, of which only [pos_lo, pos_hi)
+// is taken.  Pass 0 counts the middles per (b, type), and lists each b the
+// first time it is met (in `list`, count in *nb) or marks it in the slot's
+// bitmap (p.mark); pass 1 (per-edge mode only) adds the cycles each wedge
+// closes to its two edges.  Returns the length of the tile's sequence.  Called
+// by every thread of the CTA (it holds barriers).
+__device__ int64_t c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta, int64_t ba,
+                           int tile, int tile_end, int64_t pos_lo, int64_t pos_hi, int phase,
+                           uint32_t *cnt, uint32_t *list, unsigned int *nb,
+                           unsigned long long &wk) {
     const int tid = threadIdx.x;
     const int L = p.L, L2 = L * L, TM = p.tile;
     const int x = tile + tid;
@@ -134,7 +158,7 @@ __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta,
     uint32_t wu = 0;
     int64_t bu = 0;
     int du = 0;
-    if (tid < TM && x < da) {
+    if (tid < TM && x < tile_end) {
         wu = __ldg(p.adj + ba + x);
         const uint32_t u = wu & TG_IDMASK;
         if (u > a) {
@@ -158,9 +182,10 @@ __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta,
     if (phase == 1)
         for (int q = tid; q < nmem * L2; q += blockDim.x) sm.acc[q] = 0ull;
     __syncthreads();
-    for (int64_t base = 0; base < total; base += blockDim.x) {
+    const int64_t lim = total < pos_hi ? total : pos_hi;
+    for (int64_t base = pos_lo > 0 ? pos_lo : 0; base < lim; base += blockDim.x) {
         const int64_t pos = base + tid;
-        if (pos >= total) continue;
+        if (pos >= lim) continue;
         int lo = 0, hi = nmem - 1;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -183,7 +208,7 @@ __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta,
             if (list) {
                 // the first wedge to reach b lists it
                 if (!(atomicOr(bw, bit) & bit)) list[atomicAdd(nb, 1u)] = b;
-            } else {
+            } else if (p.mark) {
                 atomicOr(bw, bit);  // marks b for the scan of k_c4_pairs
             }
             ++wk;
@@ -223,36 +248,67 @@ __device__ void c4_tile(const C4Params &p, const C4Smem &sm, uint32_t a, int ta,
         }
         __syncthreads();
     }
+    return total;
 }
 
 // Far end b of anchor a (counters cb, per type): global mode adds the cycles
 // per type pair of middles (C(c_t, 2) for t = t', c_t c_t' for t < t') under
 // the multiset {a, b, t, t'}; both modes then clear b's counters.
-__device__ __forceinline__ void c4_one(const C4Params &p, const C4Smem &sm, int ta, uint32_t *cb,
-                                       uint32_t b) {
-    const int L = p.L;
-    if (p.g4) {
-        const int tb = p.ntype[b];
-        uint32_t c[TG_MAX_TYPES];
-#pragma unroll
-        for (int t = 0; t < TG_MAX_TYPES; ++t) c[t] = t < L ? __ldcg(cb + t) : 0u;
-        int s0 = ta, s1 = tb;
-        sort2(s0, s1);
-        for (int t = 0; t < L; ++t) {
-            if (!c[t]) continue;
-            for (int u = t; u < L; ++u) {
-                const unsigned long long v =
-                    u == t ? (unsigned long long)c[t] * (c[t] - 1) / 2 : (unsigned long long)c[t] * c[u];
-                if (!v) continue;
-                int q0s = s0, q1s = s1, q2s = t, q3s = u;
-                sort2(q0s, q2s);
-                sort2(q1s, q3s);
-                sort2(q1s, q2s);
-                atomicAdd(sm.h4 + colex4(q0s, q1s, q2s, q3s), v);
-            }
+// The cycles of one far end b (type tb) of an anchor of type ta, from its
+// middle counts c[t] (t < L): C(c_t, 2) for t = t' and c_t c_t' for t < t',
+// each under the multiset {ta, tb, t, t'}, into the shared histogram h4.  Only
+// the types with a non-zero count are visited.
+__device__ __forceinline__ void c4_add(unsigned long long *h4, int L, int ta, int tb,
+                                       const uint32_t *c) {
+    uint32_t mask = 0;
+    for (int t = 0; t < L; ++t)
+        if (c[t]) mask |= 1u << t;
+    int s0 = ta, s1 = tb;
+    sort2(s0, s1);
+    for (uint32_t mt = mask; mt; mt &= mt - 1u) {
+        const int t = __ffs(mt) - 1;
+        const unsigned long long ct = c[t];
+        if (ct > 1) {
+            int q0 = s0, q1 = s1, q2 = t, q3 = t;
+            sort2(q0, q2);
+            sort2(q1, q3);
+            sort2(q1, q2);
+            atomicAdd(h4 + colex4(q0, q1, q2, q3), ct * (ct - 1) / 2);
+        }
+        for (uint32_t mu = mt & (mt - 1u); mu; mu &= mu - 1u) {
+            const int u = __ffs(mu) - 1;
+            int q0 = s0, q1 = s1, q2 = t, q3 = u;
+            sort2(q0, q2);
+            sort2(q1, q3);
+            sort2(q1, q2);
+            atomicAdd(h4 + colex4(q0, q1, q2, q3), ct * c[u]);
         }
     }
-    for (int t = 0; t < L; ++t) cb[t] = 0u;
+}
+
+__device__ __forceinline__ void c4_one(const C4Params &p, unsigned long long *h4, int ta,
+                                       uint32_t *cb, uint32_t b) {
+    const int L = p.L;
+    uint32_t c[TG_MAX_TYPES];
+    for (int t = 0; t < L; ++t) c[t] = __ldcg(cb + t);
+    if (p.g4) c4_add(h4, L, ta, p.ntype[b], c);
+    for (int t = 0; t < L; ++t)
+        if (c[t]) cb[t] = 0u;
+}
+
+// Position of the j-th (from 0) set bit of m; m has more than j set bits.
+__device__ __forceinline__ int select_bit(uint32_t m, int j) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (j >= c) {
+            j -= c;
+            m >>= w;
+            pos += w;
+        }
+    }
+    return pos;
 }
 
 // The listed far ends of anchor a (entries q0, q0 + step, ... < nb).
@@ -261,7 +317,7 @@ __device__ __forceinline__ void c4_pairs(const C4Params &p, const C4Smem &sm, in
                                          unsigned int q0, unsigned int step) {
     for (unsigned int q = q0; q < nb; q += step) {
         const uint32_t b = __ldcg(list + q);  // written by other threads this anchor
-        c4_one(p, sm, ta, cnt + (int64_t)b * p.L, b);
+        c4_one(p, sm.h4, ta, cnt + (int64_t)b * p.L, b);
         cnt[p.n * (p.L + 1) + (b >> 5)] = 0u;  // every set bit of the word is listed
     }
 }
@@ -276,9 +332,9 @@ __device__ __forceinline__ void c4_finish(const C4Params &p, const C4Smem &sm,
     if (p.work && wk) atomicAdd(p.work + 4, wk);
 }
 
-// Anchors not marked in p.split: one CTA per anchor, the three passes in
-// turn over its own counter slot.
-__global__ void __launch_bounds__(kC4Threads) k_c4(C4Params p) {
+// The anchors of alist: one CTA per anchor, the passes in turn over the CTA's
+// own counter slot.
+__global__ void __launch_bounds__(kC4Threads) k_c4(C4Params p, const uint32_t *alist, int64_t na) {
     extern __shared__ __align__(16) unsigned char smem[];
     const C4Smem sm = c4_smem(smem, p.tile, p.acc_l2);
     const int tid = threadIdx.x;
@@ -292,9 +348,8 @@ __global__ void __launch_bounds__(kC4Threads) k_c4(C4Params p) {
         if (tid == 0) *sm.s_item = atomicAdd(p.queue, 1ull);
         __syncthreads();
         const unsigned long long item = *sm.s_item;
-        if (item >= (unsigned long long)p.n) break;
-        const uint32_t a = (uint32_t)item;
-        if (p.split[a]) continue;
+        if (item >= (unsigned long long)na) break;
+        const uint32_t a = alist[item];
         const int64_t ba = p.rowptr[a];
         const int da = (int)(p.rowptr[a + 1] - ba);
         if (da < 2) continue;  // a cycle through a needs two of its neighbours
@@ -302,10 +357,12 @@ __global__ void __launch_bounds__(kC4Threads) k_c4(C4Params p) {
         if (tid == 0) *sm.s_nb = 0u;
         __syncthreads();
         for (int tile = 0; tile < da; tile += p.tile)
-            c4_tile(p, sm, a, ta, ba, da, tile, 0, cnt, list, sm.s_nb, wk);
+            c4_tile(p, sm, a, ta, ba, tile, min(da, tile + p.tile), 0, INT64_MAX, 0, cnt, list,
+                    sm.s_nb, wk);
         if (!p.g4)
             for (int tile = 0; tile < da; tile += p.tile)
-                c4_tile(p, sm, a, ta, ba, da, tile, 1, cnt, list, sm.s_nb, wk);
+                c4_tile(p, sm, a, ta, ba, tile, min(da, tile + p.tile), 0, INT64_MAX, 1, cnt, list,
+                        sm.s_nb, wk);
         __syncthreads();
         c4_pairs(p, sm, ta, cnt, list, *sm.s_nb, tid, blockDim.x);
     }
@@ -331,44 +388,392 @@ __global__ void __launch_bounds__(kC4Threads) k_c4_split(C4Params p) {
         const int4 un = p.units[item];
         const uint32_t a = (uint32_t)un.y;
         const int64_t ba = p.rowptr[a];
-        const int da = (int)(p.rowptr[a + 1] - ba);
         uint32_t *cnt = p.scratch + (int64_t)un.x * p.slot_words;
-        c4_tile(p, sm, a, p.ntype[a], ba, da, un.z, p.phase, cnt, nullptr, nullptr, wk);
+        c4_tile(p, sm, a, p.ntype[a], ba, un.z, un.w, 0, INT64_MAX, p.phase, cnt, nullptr, nullptr,
+                wk);
     }
     c4_finish(p, sm, wk);
 }
 
 // The far ends of the wave's split anchors (na slots, anchors[slot] the
-// anchor of a slot): one grid-stride over the slots' bitmaps of far ends, so a
-// long list of far ends is shared by every CTA and pass 0 needs no returning
-// atomic to list them.  Clears the bitmap words it reads.
+// anchor of a slot), from the slots' bitmaps: each warp takes 32 bitmap words
+// at a time, lists their set bits across the lanes (a scan of the words'
+// popcounts) and treats 32 far ends per step, one per lane.  Clears the bitmap
+// words it reads.  Shared memory: the type-multiset histogram, one copy per
+// warp when `priv` (else one per CTA).
 __global__ void __launch_bounds__(kC4Threads) k_c4_pairs(C4Params p, const uint32_t *anchors,
-                                                         int na) {
+                                                         int na, int priv) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const C4Smem sm = c4_smem(smem, p.tile, p.acc_l2);
+    unsigned long long *h4all = reinterpret_cast<unsigned long long *>(smem);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int copies = priv ? (int)(blockDim.x >> 5) : 1;
     if (p.g4) {
-        for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x) sm.h4[q] = 0ull;
+        for (int64_t q = threadIdx.x; q < p.n4 * copies; q += blockDim.x) h4all[q] = 0ull;
         __syncthreads();
     }
+    unsigned long long *h4 = h4all + (priv ? (int64_t)warp * p.n4 : 0);
     const int L = p.L;
     const int64_t words = (p.n + 31) >> 5;
-    const int64_t total = (int64_t)na * words;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t slot = g / words, wi = g - slot * words;
+    const int64_t cps = (words + 31) >> 5;  // chunks of 32 words per slot
+    const int64_t total = (int64_t)na * cps;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
+        const int64_t slot = c / cps, wc = c - slot * cps;
         uint32_t *cnt = p.scratch + slot * p.slot_words;
-        uint32_t *bw = cnt + p.n * (L + 1) + wi;
-        uint32_t m = __ldcg(bw);
-        if (!m) continue;
-        *bw = 0u;
+        uint32_t *bw = cnt + p.n * (L + 1);
+        const int64_t wi = wc * 32 + lane;
+        uint32_t m = 0;
+        if (wi < words) {
+            m = __ldcg(bw + wi);
+            if (m) bw[wi] = 0u;
+        }
+        const int k = __popc(m);
+        int incl = k;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int tot = __shfl_sync(kFull, incl, 31);
+        if (tot == 0) continue;
         const int ta = p.ntype[anchors[slot]];
-        while (m) {
-            const uint32_t b = (uint32_t)(wi * 32 + __ffs(m) - 1);
-            m &= m - 1;
-            c4_one(p, sm, ta, cnt + (int64_t)b * L, b);
+        for (int base = 0; base < tot; base += 32) {
+            const int kk = base + lane;
+            int r = 0;  // the lane whose word holds far end kk
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int v = __shfl_sync(kFull, incl, r + st - 1);
+                if (v <= kk) r += st;
+            }
+            const uint32_t mr = __shfl_sync(kFull, m, r);
+            const int er = __shfl_sync(kFull, incl - k, r);
+            if (kk < tot) {
+                const uint32_t b = (uint32_t)((wc * 32 + r) * 32 + select_bit(mr, kk - er));
+                c4_one(p, h4, ta, cnt + (int64_t)b * L, b);
+            }
         }
     }
-    c4_finish(p, sm, 0ull);
+    if (p.g4) {
+        __syncthreads();
+        for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x) {
+            unsigned long long v = 0;
+            for (int cpy = 0; cpy < copies; ++cpy) v += h4all[cpy * p.n4 + q];
+            if (v) atomicAdd(p.g4 + q, v);
+        }
+    }
+}
+
+// ------------------------------------------------- dense waves (global) ----
+// Costly anchors when a few counter slots of n L words fit in L2: a wave of
+// anchors counts into its slots with fire-and-forget adds only (no far-end
+// bitmap), and k_c4_dense_pairs then scans the slots densely.  Work units cut
+// each anchor's walk (its members' lists in order) into position ranges of
+// about equal length, so one hub member's long list spreads over many CTAs.
+
+// Walk positions of the costly anchors: member x of heavy[q] costs d_u when it
+// is a member (u ranked below the anchor, d_u > 1), else 0; mprefix holds the
+// exclusive prefix from pbase[q], totals[q] the sum.  One CTA per anchor.
+__global__ void k_c4_prefix(const uint32_t *heavy, const int64_t *pbase, const int64_t *rowptr,
+                            const uint32_t *adj, int64_t *mprefix, unsigned long long *totals) {
+    __shared__ uint64_t wsum[34];
+    const int64_t q = blockIdx.x;
+    const uint32_t a = heavy[q];
+    const int64_t ba = rowptr[a];
+    const int da = (int)(rowptr[a + 1] - ba);
+    int64_t *out = mprefix + pbase[q];
+    uint64_t run = 0;
+    for (int c = 0; c < da; c += blockDim.x) {
+        const int x = c + threadIdx.x;
+        uint64_t v = 0;
+        if (x < da) {
+            const uint32_t u = __ldg(adj + ba + x) & TG_IDMASK;
+            if (u > a) {
+                const int64_t du = rowptr[u + 1] - rowptr[u];
+                v = du > 1 ? (uint64_t)du : 0ull;
+            }
+        }
+        const uint64_t incl = block_scan_packed(v, wsum);
+        if (x < da) out[x] = (int64_t)(run + incl - v);
+        run += wsum[32];
+        __syncthreads();  // wsum is rewritten by the next chunk's scan
+    }
+    if (threadIdx.x == 0) totals[q] = run;
+}
+
+// Units of the walk waves: unit u belongs to anchor q with ustart[q] <= u <
+// ustart[q + 1], covers positions [k tgt[q], min((k + 1) tgt[q], totals[q]))
+// for k = u - ustart[q], and starts at the member holding its first position.
+__global__ void k_c4_units(const int64_t *ustart, int64_t nq, const int64_t *tgt,
+                           const unsigned long long *totals, const int64_t *mprefix,
+                           const int64_t *pbase, const uint32_t *heavy, const int64_t *rowptr,
+                           C4Unit *units) {
+    const int64_t nu = ustart[nq];
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nu;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nq - 1;  // last q with ustart[q] <= u
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (ustart[mid] <= u)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int64_t q = lo;
+        const int64_t f_lo = (u - ustart[q]) * tgt[q];
+        const int64_t f_hi = min(f_lo + tgt[q], (int64_t)totals[q]);
+        const uint32_t a = heavy[q];
+        const int da = (int)(rowptr[a + 1] - rowptr[a]);
+        const int64_t *pre = mprefix + pbase[q];
+        int m0 = 0, m1 = da - 1;  // last member m with pre[m] <= f_lo
+        while (m0 < m1) {
+            const int mid = (m0 + m1 + 1) >> 1;
+            if (pre[mid] <= f_lo)
+                m0 = mid;
+            else
+                m1 = mid - 1;
+        }
+        C4Unit un;
+        un.lo = f_lo;
+        un.hi = f_hi;
+        un.q = (int32_t)q;
+        un.m = m0;
+        units[u] = un;
+    }
+}
+
+// Positions [f_lo, f_hi) of anchor a's walk, from member m on (its first
+// position `at`), by one warp: members are taken 32 at a time, their list
+// lengths scanned across the lanes, and each position mapped to its member by
+// a 5-step search over the lanes' running sums.  op(b, t_u) runs for every
+// entry b ranked below a of a member u.  With stride > 32 the warp takes every
+// (stride / 32)-th chunk of 32 members (no window: f_lo = 0, f_hi unbounded).
+template <class Op>
+__device__ __forceinline__ void c4_warp_walk(const C4Params &p, uint32_t a, int64_t ba, int da,
+                                             int m, int64_t at, int64_t f_lo, int64_t f_hi,
+                                             int stride, Op op) {
+    const int lane = threadIdx.x & 31;
+    for (; m < da && at < f_hi; m += stride) {
+        const int x = m + lane;
+        int64_t len = 0, bu = 0;
+        int tu = 0;
+        if (x < da) {
+            const uint32_t wu = __ldg(p.adj + ba + x);
+            const uint32_t u = wu & TG_IDMASK;
+            if (u > a) {
+                bu = p.rowptr[u];
+                const int64_t du = p.rowptr[u + 1] - bu;
+                if (du > 1) {
+                    len = du;
+                    tu = (int)(wu >> TG_TSHIFT);
+                }
+            }
+        }
+        int64_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int64_t total = __shfl_sync(kFull, incl, 31);
+        const int64_t lo = f_lo > at ? f_lo - at : 0;
+        const int64_t hi = f_hi - at < total ? f_hi - at : total;
+        for (int64_t b0 = lo; b0 < hi; b0 += 32) {
+            const int64_t pos = b0 + lane;
+            int r = 0;  // the first member whose running sum exceeds pos
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int64_t v = __shfl_sync(kFull, incl, r + st - 1);
+                if (v <= pos) r += st;
+            }
+            const int64_t bur = __shfl_sync(kFull, bu, r);
+            const int64_t str = __shfl_sync(kFull, incl - len, r);
+            const int tur = __shfl_sync(kFull, tu, r);
+            if (pos < hi) {
+                const uint32_t b = __ldg(p.adj + bur + (pos - str)) & TG_IDMASK;
+                if (b > a) op(b, tur);
+            }
+        }
+        at += total;
+    }
+}
+
+// Pass 0 of a wave of costly anchors (global mode): one warp per unit, adding
+// to the counters of its anchor's slot and marking the far ends in the slot's
+// bitmap with fire-and-forget atomics; k_c4_pairs then takes the marked ends.
+constexpr int kC4WalkWarps = 8;
+
+__global__ void __launch_bounds__(kC4WalkWarps * 32) k_c4_walk(C4Params p) {
+    const int lane = threadIdx.x & 31;
+    const int L = p.L;
+    unsigned long long wk = 0;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(p.queue, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= (unsigned long long)p.n_units) break;
+        const C4Unit un = p.wunits[item];
+        const uint32_t a = p.heavy[un.q];
+        const int64_t ba = p.rowptr[a];
+        const int da = (int)(p.rowptr[a + 1] - ba);
+        uint32_t *cnt = p.scratch + (un.q - p.q0) * p.slot_words;
+        uint32_t *bits = cnt + p.n * (L + 1);
+        const int64_t at = p.mprefix[p.pbase[un.q] + un.m];
+        c4_warp_walk(p, a, ba, da, un.m, at, un.lo, un.hi, 32, [&](uint32_t b, int tu) {
+            atomicAdd(cnt + (int64_t)b * L + tu, 1u);
+            atomicOr(bits + (b >> 5), 1u << (b & 31u));
+            ++wk;
+        });
+    }
+    if (p.work) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wk += __shfl_xor_sync(kFull, wk, o);
+        if (lane == 0 && wk) atomicAdd(p.work + 4, wk);
+    }
+}
+
+// ------------------------------------------------- light anchors (global) --
+// Anchors whose walk cost (sum of d_u over their members) is at most half a
+// warp's table: one warp per anchor, the far ends in a per-warp shared-memory
+// hash set with L 16-bit middle counters per slot (a count never exceeds the
+// cost).  No global counters, no CTA barrier between anchors.
+constexpr int kC4WarpWarps = 8;
+constexpr int kC4WarpLgMax = 9;  // 512 slots per warp
+
+__device__ __forceinline__ uint32_t c4w_count(const uint32_t *cw, int k) {
+    const volatile uint32_t *v = cw;
+    return (v[k >> 1] >> ((k & 1) * 16)) & 0xffffu;
+}
+
+__global__ void __launch_bounds__(kC4WarpWarps * 32, 4) k_c4_warp(C4Params p, const uint32_t *alist,
+                                                              int64_t na,
+                                                              const unsigned long long *cost,
+                                                              int lg_max) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int L = p.L;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int emax = 1 << lg_max;
+    const int cwords = (emax * L + 1) >> 1;
+    unsigned long long *h4 = reinterpret_cast<unsigned long long *>(smem);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(h4 + p.n4) + (size_t)warp * (emax + cwords);
+    uint32_t *cw = keys + emax;
+    for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x) h4[q] = 0ull;
+    for (int q = lane; q < emax + cwords; q += 32) keys[q] = 0u;
+    __syncthreads();
+    unsigned long long wk = 0;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(p.queue, 32ull);
+        base = __shfl_sync(kFull, base, 0);
+        if (base >= (unsigned long long)na) break;
+        const int64_t stop = min((int64_t)base + 32, na);
+        for (int64_t i = (int64_t)base; i < stop; ++i) {
+            const uint32_t a = alist[i];
+            const int64_t ba = p.rowptr[a];
+            const int da = (int)(p.rowptr[a + 1] - ba);
+            const int ta = p.ntype[a];
+            const unsigned long long ca = cost[a];
+            int lg = 5;
+            while ((1ull << lg) < 2 * ca && lg < lg_max) ++lg;
+            c4_warp_walk(p, a, ba, da, 0, 0, 0, INT64_MAX, 32, [&](uint32_t b, int tu) {
+                const int h = hset_claim(keys, lg, b);
+                if (h >= 0) {
+                    const int k = h * L + tu;
+                    atomicAdd(cw + (k >> 1), 1u << ((k & 1) * 16));
+                    ++wk;
+                }
+            });
+            __syncwarp();
+            const int e = 1 << lg;
+            const volatile uint32_t *vk = keys;
+            for (int h = lane; h < e; h += 32) {
+                const uint32_t k = vk[h];
+                if (!k) continue;
+                uint32_t c[TG_MAX_TYPES];
+                for (int t = 0; t < L; ++t) c[t] = c4w_count(cw, h * L + t);
+                c4_add(h4, L, ta, p.ntype[k - 1u], c);
+            }
+            __syncwarp();
+            for (int q = lane; q < e; q += 32) keys[q] = 0u;
+            for (int q = lane; q < ((e * L + 1) >> 1); q += 32) cw[q] = 0u;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int64_t q = threadIdx.x; q < p.n4; q += blockDim.x)
+        if (h4[q]) atomicAdd(p.g4 + q, h4[q]);
+    if (p.work) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wk += __shfl_xor_sync(kFull, wk, o);
+        if (lane == 0 && wk) atomicAdd(p.work + 4, wk);
+    }
+}
+
+// Anchors of cost up to half a CTA table: one CTA per anchor, its warps taking
+// every eighth chunk of 32 members, the far ends in one shared-memory hash set
+// with 16-bit middle counters (the cost stays far below 2^16).
+constexpr int kC4CtaThreads = 256;
+constexpr int kC4CtaLgMax = 13;  // 8192 slots
+
+__global__ void __launch_bounds__(kC4CtaThreads) k_c4_cta(C4Params p, const uint32_t *alist,
+                                                          int64_t na,
+                                                          const unsigned long long *cost,
+                                                          int lg_max) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int L = p.L;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int stride = blockDim.x;  // 32 members per warp
+    const int emax = 1 << lg_max;
+    const int cwords = (emax * L + 1) >> 1;
+    unsigned long long *h4 = reinterpret_cast<unsigned long long *>(smem);
+    unsigned long long *s_item = h4 + p.n4;
+    uint32_t *keys = reinterpret_cast<uint32_t *>(s_item + 1);
+    uint32_t *cw = keys + emax;
+    for (int64_t q = tid; q < p.n4; q += blockDim.x) h4[q] = 0ull;
+    for (int q = tid; q < emax + cwords; q += blockDim.x) keys[q] = 0u;
+    unsigned long long wk = 0;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) *s_item = atomicAdd(p.queue, 1ull);
+        __syncthreads();
+        const unsigned long long item = *s_item;
+        if (item >= (unsigned long long)na) break;
+        const uint32_t a = alist[item];
+        const int64_t ba = p.rowptr[a];
+        const int da = (int)(p.rowptr[a + 1] - ba);
+        const int ta = p.ntype[a];
+        const unsigned long long ca = cost[a];
+        int lg = 5;
+        while ((1ull << lg) < 2 * ca && lg < lg_max) ++lg;
+        c4_warp_walk(p, a, ba, da, 32 * warp, 0, 0, INT64_MAX, stride, [&](uint32_t b, int tu) {
+            const int h = hset_claim(keys, lg, b);
+            if (h >= 0) {
+                const int k = h * L + tu;
+                atomicAdd(cw + (k >> 1), 1u << ((k & 1) * 16));
+                ++wk;
+            }
+        });
+        __syncthreads();
+        const int e = 1 << lg;
+        const volatile uint32_t *vk = keys;
+        for (int h = tid; h < e; h += blockDim.x) {
+            const uint32_t k = vk[h];
+            if (!k) continue;
+            uint32_t c[TG_MAX_TYPES];
+            for (int t = 0; t < L; ++t) c[t] = c4w_count(cw, h * L + t);
+            c4_add(h4, L, ta, p.ntype[k - 1u], c);
+        }
+        __syncthreads();
+        for (int q = tid; q < e; q += blockDim.x) keys[q] = 0u;
+        for (int q = tid; q < ((e * L + 1) >> 1); q += blockDim.x) cw[q] = 0u;
+    }
+    __syncthreads();
+    for (int64_t q = tid; q < p.n4; q += blockDim.x)
+        if (h4[q]) atomicAdd(p.g4 + q, h4[q]);
+    if (p.work) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wk += __shfl_xor_sync(kFull, wk, o);
+        if (lane == 0 && wk) atomicAdd(p.work + 4, wk);
+    }
 }
 
 // Walk cost of each anchor (sum of d_u over its neighbours u ranked below it)
@@ -395,14 +800,23 @@ __global__ void k_c4_cost(const int64_t *rowptr, const uint32_t *adj, int64_t n,
     if (lane == 0 && mine) atomicAdd(total, mine);
 }
 
-// split[a] = cost[a] > thr; flag (as uint32) for the compaction
+// Anchor classes by walk cost c (flags[k n + a] = 1 for the class of a):
+// kClsSplit c > thr, else kClsWarp 0 < c <= lite, kClsCta lite < c <= mid,
+// kClsSlot mid < c (anchors of cost 0 close no cycle and take none).
+enum { kClsSplit = 0, kClsWarp, kClsCta, kClsSlot, kClsN };
+
 __global__ void k_c4_mark(const unsigned long long *cost, int64_t n, unsigned long long thr,
-                          uint8_t *split, uint32_t *flag) {
+                          unsigned long long lite, unsigned long long mid, uint32_t *flags) {
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
          a += (int64_t)gridDim.x * blockDim.x) {
-        const bool h = cost[a] > thr;
-        split[a] = h ? 1 : 0;
-        flag[a] = h ? 1u : 0u;
+        const unsigned long long c = cost[a];
+        int cls = -1;
+        if (c > thr)
+            cls = kClsSplit;
+        else if (c > 0)
+            cls = c <= lite ? kClsWarp : c <= mid ? kClsCta : kClsSlot;
+#pragma unroll
+        for (int k = 0; k < kClsN; ++k) flags[k * n + a] = cls == k ? 1u : 0u;
     }
 }
 
@@ -1672,6 +2086,115 @@ int smem_optin_c() {
     return v > 0 ? v : 48 * 1024;
 }
 
+// Launch shape of k_c4_pairs: per-warp histogram copies when they fit in 64 KB.
+struct PairsConf {
+    size_t smem;
+    int priv;
+    int64_t grid;
+};
+int c4_pairs_conf(int64_t n4, PairsConf &c) {
+    const size_t one = (size_t)n4 * 8;
+    c.priv = one * (kC4Threads / 32) <= (size_t)64 * 1024 ? 1 : 0;
+    c.smem = c.priv ? one * (kC4Threads / 32) : one;
+    TG_TRY(tg_allow_max_smem((const void *)k_c4_pairs));
+    int per = 0;
+    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_c4_pairs, kC4Threads, c.smem));
+    c.grid = (int64_t)num_sms_c() * (per > 0 ? per : 1);
+    return TG_OK;
+}
+
+// shared memory of k_c4_warp / k_c4_cta with tables of 2^lg slots
+size_t c4_warp_smem(int64_t n4, int L, int lg) {
+    const size_t e = (size_t)1 << lg;
+    return (size_t)n4 * 8 + (size_t)kC4WarpWarps * (e + ((e * L + 1) >> 1)) * 4;
+}
+size_t c4_cta_smem(int64_t n4, int L, int lg) {
+    const size_t e = (size_t)1 << lg;
+    return (size_t)n4 * 8 + 8 + (e + ((e * L + 1) >> 1)) * 4;
+}
+
+// Global-mode waves of the split anchors list[0 .. nheavy) (degrees hdeg):
+// walk positions per anchor (k_c4_prefix), warp units of about a quarter of a
+// warp's share of each wave (k_c4_units), then per wave of K anchors (K =
+// slots of p.scratch) k_c4_walk and k_c4_pairs.
+int c4_walk_waves(const C4Params &p, const tg_graph *g, const uint32_t *list, int64_t nheavy,
+                  const std::vector<int64_t> &hdeg, int64_t K, cudaStream_t s) {
+    PairsConf pc;
+    TG_TRY(c4_pairs_conf(p.n4, pc));
+    const int64_t pgrid = pc.grid;
+    const size_t psmem = pc.smem;
+    const int ppriv = pc.priv;
+    std::vector<int64_t> pb((size_t)nheavy + 1, 0);
+    for (int64_t q = 0; q < nheavy; ++q) pb[q + 1] = pb[q] + hdeg[q];
+    DevBuf<int64_t> dpb, dmp;
+    DevBuf<unsigned long long> dtot;
+    if (!dpb.alloc(nheavy + 1, s) || !dmp.alloc(pb[nheavy], s) || !dtot.alloc(nheavy, s))
+        return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemcpyAsync(dpb.p, pb.data(), (nheavy + 1) * 8, cudaMemcpyHostToDevice, s));
+    k_c4_prefix<<<(unsigned)nheavy, 256, 0, s>>>(list, dpb.p, g->rowptr, g->adj, dmp.p, dtot.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    std::vector<unsigned long long> tot_h((size_t)nheavy);
+    TG_TRY_CUDA(cudaMemcpyAsync(tot_h.data(), dtot.p, nheavy * 8, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    int wper = 0;
+    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_c4_walk, kC4WalkWarps * 32, 0));
+    if (wper < 1) wper = 1;
+    const int64_t walk_grid = (int64_t)num_sms_c() * wper;
+    const int64_t warps = walk_grid * kC4WalkWarps;
+    const int64_t nwaves = (nheavy + K - 1) / K;
+    std::vector<int64_t> us((size_t)nheavy + 1, 0), tg((size_t)nheavy, 1);
+    for (int64_t w = 0; w < nwaves; ++w) {
+        const int64_t q0 = w * K, q1 = std::min(nheavy, q0 + K);
+        unsigned long long wt = 0;
+        for (int64_t q = q0; q < q1; ++q) wt += tot_h[q];
+        const int64_t tgt =
+            std::max<int64_t>(kWalkUnitMin, (int64_t)((wt + 4 * warps - 1) / (4 * warps)));
+        for (int64_t q = q0; q < q1; ++q) {
+            tg[q] = tgt;
+            us[q + 1] = us[q] + (int64_t)((tot_h[q] + tgt - 1) / tgt);
+        }
+    }
+    const int64_t nunits = us[nheavy];
+    DevBuf<int64_t> dus, dtg;
+    DevBuf<C4Unit> dun;
+    DevBuf<unsigned long long> dq;
+    if (!dus.alloc(nheavy + 1, s) || !dtg.alloc(nheavy, s) || !dun.alloc(nunits ? nunits : 1, s) ||
+        !dq.alloc(nwaves, s))
+        return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemcpyAsync(dus.p, us.data(), (nheavy + 1) * 8, cudaMemcpyHostToDevice, s));
+    TG_TRY_CUDA(cudaMemcpyAsync(dtg.p, tg.data(), nheavy * 8, cudaMemcpyHostToDevice, s));
+    TG_TRY_CUDA(cudaMemsetAsync(dq.p, 0, nwaves * 8, s));
+    if (nunits > 0) {
+        const unsigned ug = (unsigned)std::min<int64_t>((nunits + 255) / 256, 65535LL * 16);
+        k_c4_units<<<ug, 256, 0, s>>>(dus.p, nheavy, dtg.p, dtot.p, dmp.p, dpb.p, list, g->rowptr,
+                                      dun.p); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
+    C4Params pd = p;
+    pd.phase = 0;
+    pd.heavy = list;
+    pd.mprefix = dmp.p;
+    pd.pbase = dpb.p;
+    for (int64_t w = 0; w < nwaves; ++w) {
+        const int64_t q0 = w * K, q1 = std::min(nheavy, q0 + K);
+        pd.q0 = q0;
+        pd.wunits = dun.p + us[q0];
+        pd.n_units = us[q1] - us[q0];
+        pd.queue = dq.p + w;
+        if (pd.n_units > 0) {
+            const int64_t need = (pd.n_units + kC4WalkWarps - 1) / kC4WalkWarps;
+            const int64_t grid = std::min<int64_t>(walk_grid, need);
+            k_c4_walk<<<(unsigned)grid, kC4WalkWarps * 32, 0, s>>>(pd); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+        }
+        k_c4_pairs<<<(unsigned)pgrid, kC4Threads, psmem, s>>>(pd, list + q0, (int)(q1 - q0), ppriv); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
+    // the host vectors are read by the copies above before they go out of scope
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    return TG_OK;
+}
+
 }  // namespace
 
 int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long *g4,
@@ -1698,12 +2221,11 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     if (per_sm < 1) per_sm = 1;
     const int64_t full_grid = (int64_t)num_sms_c() * per_sm;
 
-    // anchor costs; those above thr are split into units over the whole grid
+    // anchor costs and classes
     DevBuf<unsigned long long> cost, total;
-    DevBuf<uint8_t> split;
-    DevBuf<uint32_t> flag, pos, list;
-    if (!cost.alloc(n, s) || !total.alloc(1, s) || !split.alloc(n, s) || !flag.alloc(n, s) ||
-        !pos.alloc(n, s))
+    DevBuf<uint32_t> flags, pos;
+    if (!cost.alloc(n, s) || !total.alloc(1, s) || !flags.alloc((size_t)kClsN * n, s) ||
+        !pos.alloc((size_t)kClsN * n, s))
         return TG_ENOMEM;
     TG_TRY_CUDA(cudaMemsetAsync(total.p, 0, 8, s));
     const unsigned wgrid = (unsigned)std::min<int64_t>((n * 32 + 255) / 256, 65535LL * 16);
@@ -1712,27 +2234,54 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     unsigned long long tot = 0;
     TG_TRY_CUDA(cudaMemcpyAsync(&tot, total.p, 8, cudaMemcpyDeviceToHost, s));
     TG_TRY_CUDA(cudaStreamSynchronize(s));
-    // unroll selects the split rule: 1 none, 4 every anchor, else by cost
-    unsigned long long thr = std::max<unsigned long long>(tot / (unsigned long long)(16 * full_grid),
-                                                          (unsigned long long)1 << 12);
+    // Global mode: anchors whose far ends fit half a warp table (2^lg_w
+    // slots) or half a CTA table (2^lg_c) count in shared memory; costlier
+    // ones are split over the grid.  Per-edge mode: anchors above a share of
+    // the total are split, the others take one CTA and a counter slot each.
+    // hash_slots caps the warp table; unroll 1 splits none, 4 every anchor.
+    int lg_w = 0, lg_c = 0;
+    if (global) {
+        lg_w = kC4WarpLgMax;
+        while (lg_w > 5 && ((1 << lg_w) > t.hash_slots ||
+                            c4_warp_smem(n4, L, lg_w) > (size_t)smem_optin_c() - 1024))
+            --lg_w;
+        lg_c = kC4CtaLgMax;
+        while (lg_c > lg_w && c4_cta_smem(n4, L, lg_c) > (size_t)smem_optin_c() - 1024) --lg_c;
+    }
+    const unsigned long long lite = global ? (1ull << lg_w) / 2 : 0ull;
+    const unsigned long long mid = global ? (1ull << lg_c) / 2 : 0ull;
+    unsigned long long thr =
+        global ? mid
+               : std::max<unsigned long long>(tot / (unsigned long long)(16 * full_grid),
+                                              (unsigned long long)1 << 12);
     if (t.unroll == 1) thr = ~0ull;
     if (t.unroll == 4) thr = 0ull;
     const unsigned egrid = (unsigned)std::min<int64_t>((n + 255) / 256, 65535LL * 16);
-    k_c4_mark<<<egrid, 256, 0, s>>>(cost.p, n, thr, split.p, flag.p); tg_note_launch();
+    k_c4_mark<<<egrid, 256, 0, s>>>(cost.p, n, thr, lite, mid, flags.p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
-    TG_TRY(tg_scan_u32(flag.p, pos.p, n, s));
-    uint32_t lastp = 0, lastf = 0;
-    TG_TRY_CUDA(cudaMemcpyAsync(&lastp, pos.p + n - 1, 4, cudaMemcpyDeviceToHost, s));
-    TG_TRY_CUDA(cudaMemcpyAsync(&lastf, flag.p + n - 1, 4, cudaMemcpyDeviceToHost, s));
+    for (int k = 0; k < kClsN; ++k) TG_TRY(tg_scan_u32(flags.p + (size_t)k * n, pos.p + (size_t)k * n, n, s));
+    uint32_t lastp[kClsN], lastf[kClsN];
+    for (int k = 0; k < kClsN; ++k) {
+        TG_TRY_CUDA(cudaMemcpyAsync(&lastp[k], pos.p + (size_t)k * n + n - 1, 4, cudaMemcpyDeviceToHost, s));
+        TG_TRY_CUDA(cudaMemcpyAsync(&lastf[k], flags.p + (size_t)k * n + n - 1, 4, cudaMemcpyDeviceToHost, s));
+    }
     TG_TRY_CUDA(cudaStreamSynchronize(s));
-    const int64_t nheavy = (int64_t)lastp + lastf;
+    int64_t ncls[kClsN];
+    DevBuf<uint32_t> lists[kClsN];
+    for (int k = 0; k < kClsN; ++k) {
+        ncls[k] = (int64_t)lastp[k] + lastf[k];
+        if (ncls[k] == 0) continue;
+        if (!lists[k].alloc(ncls[k], s)) return TG_ENOMEM;
+        k_c4_compact<<<egrid, 256, 0, s>>>(flags.p + (size_t)k * n, pos.p + (size_t)k * n, n,
+                                           lists[k].p); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
+    const int64_t nheavy = ncls[kClsSplit];
+    const uint32_t *list = lists[kClsSplit].p;
     std::vector<uint32_t> heavy((size_t)nheavy);
     std::vector<int64_t> hdeg((size_t)nheavy);
     if (nheavy > 0) {
-        if (!list.alloc(nheavy, s)) return TG_ENOMEM;
-        k_c4_compact<<<egrid, 256, 0, s>>>(flag.p, pos.p, n, list.p); tg_note_launch();
-        TG_TRY_CUDA(cudaGetLastError());
-        TG_TRY_CUDA(cudaMemcpyAsync(heavy.data(), list.p, nheavy * 4, cudaMemcpyDeviceToHost, s));
+        TG_TRY_CUDA(cudaMemcpyAsync(heavy.data(), list, nheavy * 4, cudaMemcpyDeviceToHost, s));
         TG_TRY_CUDA(cudaStreamSynchronize(s));
         // degrees of the split anchors: the list is ascending, so one copy of
         // rowptr up to the largest of them
@@ -1743,24 +2292,30 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
         for (int64_t q = 0; q < nheavy; ++q) hdeg[q] = rp[heavy[q] + 1] - rp[heavy[q]];
     }
 
-    // counter slots: one per CTA of the one-CTA kernel, one per split anchor of
-    // a wave; all within a quarter of free memory
+    // counter slots: one per CTA of k_c4, one per split anchor of a wave; all
+    // within a quarter of free memory
+    const bool walk_waves = global && t.hash_slots >= 64;
     const int64_t slot_words = n * (L + 1) + (n + 31) / 32;
     const size_t slot_bytes = (size_t)slot_words * 4;
+    int64_t want = 0;
+    if (ncls[kClsSlot] > 0) want = std::min<int64_t>(full_grid, ncls[kClsSlot]);
+    if (nheavy > 0)
+        want = std::max<int64_t>(want, std::min<int64_t>(walk_waves ? kWaveMax : full_grid, nheavy));
     size_t free_b = 0, total_b = 0;
     TG_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    int64_t slots = (int64_t)(free_b / 4 / (slot_bytes ? slot_bytes : 1));
-    if (slots > full_grid) slots = full_grid;
-    if (slots > n) slots = n;
-    if (slots < 1) {
+    int64_t slots = std::min<int64_t>(want, (int64_t)(free_b / 4 / (slot_bytes ? slot_bytes : 1)));
+    if (want > 0 && slots < 1) {
         if (slot_bytes > free_b / 2) return TG_ENOMEM;
         slots = 1;
     }
-    DevBuf<uint32_t> scratch, wave_anchor;
+    DevBuf<uint32_t> scratch;
     DevBuf<unsigned long long> queue;
-    if (!scratch.alloc((size_t)slots * slot_words, s) || !queue.alloc(1, s))
-        return TG_ENOMEM;
-    TG_TRY_CUDA(cudaMemsetAsync(scratch.p, 0, (size_t)slots * slot_bytes, s));
+    if (!queue.alloc(kClsN, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, kClsN * 8, s));
+    if (slots > 0) {
+        if (!scratch.alloc((size_t)slots * slot_words, s)) return TG_ENOMEM;
+        TG_TRY_CUDA(cudaMemsetAsync(scratch.p, 0, (size_t)slots * slot_bytes, s));
+    }
     C4Params p{};
     p.rowptr = g->rowptr;
     p.adj = g->adj;
@@ -1776,11 +2331,21 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     p.c4e = c4e;
     p.g4 = g4;
     p.n4 = n4;
-    p.split = split.p;
     p.work = work;
+    p.mark = 1;
 
-    // split anchors, in waves of at most `slots` anchors
-    if (nheavy > 0) {
+    if (nheavy > 0 && walk_waves) {
+        // global mode: each split anchor's walk is cut into position ranges of
+        // about equal length (warp units of k_c4_walk), in waves of `slots`
+        // anchors; each wave's far ends are taken by k_c4_pairs
+        TG_TRY(c4_walk_waves(p, g, list, nheavy, hdeg, slots, s));
+    } else if (nheavy > 0) {
+        // member tiles of 'TM' members as units (both passes in per-edge mode)
+        PairsConf pc;
+        TG_TRY(c4_pairs_conf(n4, pc));
+        const int64_t pgrid = pc.grid;
+        const size_t psmem = pc.smem;
+        const int ppriv = pc.priv;
         const int64_t wave = slots;
         std::vector<int4> units;
         std::vector<int64_t> wave_start;
@@ -1788,41 +2353,75 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
             wave_start.push_back((int64_t)units.size());
             for (int64_t q = q0; q < std::min(nheavy, q0 + wave); ++q)
                 for (int64_t tl = 0; tl < hdeg[q]; tl += TM)
-                    units.push_back(make_int4((int)(q - q0), (int)heavy[q], (int)tl, 0));
+                    units.push_back(make_int4((int)(q - q0), (int)heavy[q], (int)tl,
+                                              (int)std::min<int64_t>(tl + TM, hdeg[q])));
         }
         wave_start.push_back((int64_t)units.size());
         DevBuf<int4> du;
-        if (!du.alloc(units.size(), s) || !wave_anchor.alloc(nheavy, s)) return TG_ENOMEM;
+        if (!du.alloc(units.size(), s)) return TG_ENOMEM;
         TG_TRY_CUDA(cudaMemcpyAsync(du.p, units.data(), units.size() * sizeof(int4),
                                     cudaMemcpyHostToDevice, s));
-        TG_TRY_CUDA(cudaMemcpyAsync(wave_anchor.p, heavy.data(), nheavy * 4,
-                                    cudaMemcpyHostToDevice, s));
+        DevBuf<unsigned long long> wq;
+        if (!wq.alloc(2 * (wave_start.size() - 1), s)) return TG_ENOMEM;
+        TG_TRY_CUDA(cudaMemsetAsync(wq.p, 0, 2 * (wave_start.size() - 1) * 8, s));
+        C4Params ps = p;
         for (size_t w = 0; w + 1 < wave_start.size(); ++w) {
             const int64_t u0 = wave_start[w], nu = wave_start[w + 1] - u0;
             const int64_t a0 = (int64_t)w * wave, na = std::min<int64_t>(wave, nheavy - a0);
-            p.units = du.p + u0;
-            p.n_units = nu;
+            ps.units = du.p + u0;
+            ps.n_units = nu;
             const int64_t grid = std::min<int64_t>(full_grid, nu);
             for (int ph = 0; ph < (global ? 1 : 2); ++ph) {
-                p.phase = ph;
-                TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
-                k_c4_split<<<(unsigned)grid, kC4Threads, smem, s>>>(p); tg_note_launch();
+                ps.phase = ph;
+                ps.queue = wq.p + 2 * w + ph;
+                k_c4_split<<<(unsigned)grid, kC4Threads, smem, s>>>(ps); tg_note_launch();
                 TG_TRY_CUDA(cudaGetLastError());
             }
-            k_c4_pairs<<<(unsigned)full_grid, kC4Threads, smem, s>>>(p, wave_anchor.p + a0, (int)na); tg_note_launch();
+            k_c4_pairs<<<(unsigned)pgrid, kC4Threads, psmem, s>>>(ps, list + a0, (int)na, ppriv); tg_note_launch();
             TG_TRY_CUDA(cudaGetLastError());
         }
         // the host vectors are read by the copy above before they go out of scope
         TG_TRY_CUDA(cudaStreamSynchronize(s));
     }
-    // the other anchors, one CTA each
-    p.units = nullptr;
-    p.n_units = 0;
-    p.phase = 0;
-    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
-    int64_t grid = slots;
-    k_c4<<<(unsigned)grid, kC4Threads, smem, s>>>(p); tg_note_launch();
-    TG_TRY_CUDA(cudaGetLastError());
+    // light anchors: one warp each, a CTA each, in shared memory
+    if (ncls[kClsWarp] > 0) {
+        const size_t wsmem = c4_warp_smem(n4, L, lg_w);
+        TG_TRY(tg_allow_max_smem((const void *)k_c4_warp));
+        int wper = 0;
+        TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_c4_warp,
+                                                                  kC4WarpWarps * 32, wsmem));
+        if (wper < 1) wper = 1;
+        int64_t wg = (int64_t)num_sms_c() * wper;
+        wg = std::min<int64_t>(wg, (ncls[kClsWarp] + 32 * kC4WarpWarps - 1) / (32 * kC4WarpWarps));
+        C4Params pw = p;
+        pw.queue = queue.p + kClsWarp;
+        k_c4_warp<<<(unsigned)wg, kC4WarpWarps * 32, wsmem, s>>>(pw, lists[kClsWarp].p,
+                                                                  ncls[kClsWarp], cost.p, lg_w); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
+    if (ncls[kClsCta] > 0) {
+        const size_t csmem = c4_cta_smem(n4, L, lg_c);
+        TG_TRY(tg_allow_max_smem((const void *)k_c4_cta));
+        int cper = 0;
+        TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cper, k_c4_cta, kC4CtaThreads,
+                                                                  csmem));
+        if (cper < 1) cper = 1;
+        const int64_t cg = std::min<int64_t>((int64_t)num_sms_c() * cper, ncls[kClsCta]);
+        C4Params pc = p;
+        pc.queue = queue.p + kClsCta;
+        k_c4_cta<<<(unsigned)cg, kC4CtaThreads, csmem, s>>>(pc, lists[kClsCta].p, ncls[kClsCta],
+                                                             cost.p, lg_c); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
+    // the other anchors, one CTA and counter slot each
+    if (ncls[kClsSlot] > 0) {
+        C4Params pl = p;
+        pl.queue = queue.p + kClsSlot;
+        pl.phase = 0;
+        const int64_t grid = std::min<int64_t>(slots, ncls[kClsSlot]);
+        k_c4<<<(unsigned)grid, kC4Threads, smem, s>>>(pl, lists[kClsSlot].p, ncls[kClsSlot]); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
     return TG_OK;
 }
 

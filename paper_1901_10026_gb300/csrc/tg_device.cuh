@@ -111,6 +111,24 @@ __device__ __forceinline__ bool hset_has(const uint32_t *tab, int lg, uint32_t i
     return false;
 }
 
+// Slot of id in a hash set as above, claiming an empty slot for it; -1 when
+// the table is full.  Concurrent claims of one id meet in one slot.
+__device__ __forceinline__ int hset_claim(uint32_t *tab, int lg, uint32_t id) {
+    const uint32_t mask = (1u << lg) - 1u;
+    const volatile uint32_t *t = tab;
+    uint32_t h = hset_slot(id, lg);
+    for (int probe = 0; probe < (1 << lg); ++probe) {
+        const uint32_t k = t[h];
+        if (k == id + 1u) return (int)h;
+        if (k == 0u) {
+            const uint32_t old = atomicCAS(tab + h, 0u, id + 1u);
+            if (old == 0u || old == id + 1u) return (int)h;
+        }
+        h = (h + 1u) & mask;
+    }
+    return -1;
+}
+
 // Per-warp hash map of node ids to 32-bit values in shared memory (keys as
 // in hset, values beside them; a value is written after its key is claimed and
 // read after a __syncwarp).

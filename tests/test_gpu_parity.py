@@ -19,6 +19,7 @@ VARIANTS = {
     "cycles-small": dict(kernel=tg.TG_KERNEL_CYCLES, cta_threads=64, hash_slots=32, bitmap_bits=96,
                          grid_limit=3, unroll=1),
     "cycles-split": dict(kernel=tg.TG_KERNEL_CYCLES, unroll=4),
+    "cycles-split-bitmap": dict(kernel=tg.TG_KERNEL_CYCLES, unroll=4, hash_slots=32),
     "reuse": dict(kernel=tg.TG_KERNEL_REUSE),
     "warp-search": dict(kernel=tg.TG_KERNEL_WARP_SEARCH),
     "cta-small": dict(kernel=tg.TG_KERNEL_CTA_BITMAP, cta_threads=128, unroll=1, hash_slots=32,
