@@ -598,8 +598,8 @@ __device__ __forceinline__ void c4_warp_walk(const C4Params &p, uint32_t a, int6
 }
 
 // Pass 0 of a wave of costly anchors (global mode): one warp per unit, adding
-// to the counters of its anchor's slot and marking the far ends in the slot's
-// bitmap with fire-and-forget atomics; k_c4_pairs then takes the marked ends.
+// to the counters of its anchor's slot and marking a far end in the slot's
+// bitmap when a count of it leaves zero; k_c4_pairs then takes the marked ends.
 constexpr int kC4WalkWarps = 8;
 
 __global__ void __launch_bounds__(kC4WalkWarps * 32) k_c4_walk(C4Params p) {
@@ -619,8 +619,8 @@ __global__ void __launch_bounds__(kC4WalkWarps * 32) k_c4_walk(C4Params p) {
         uint32_t *bits = cnt + p.n * (L + 1);
         const int64_t at = p.mprefix[p.pbase[un.q] + un.m];
         c4_warp_walk(p, a, ba, da, un.m, at, un.lo, un.hi, 32, [&](uint32_t b, int tu) {
-            atomicAdd(cnt + (int64_t)b * L + tu, 1u);
-            atomicOr(bits + (b >> 5), 1u << (b & 31u));
+            // the first middle of a type at b marks b
+            if (!atomicAdd(cnt + (int64_t)b * L + tu, 1u)) atomicOr(bits + (b >> 5), 1u << (b & 31u));
             ++wk;
         });
     }

@@ -250,48 +250,119 @@ __global__ void __launch_bounds__(kLightWarps * 32) k_tau_light(
 
 // --------------------------------------------------- per-node aggregates ----
 // Theta_v[a][b] = sum over w in Gamma_v^a of tau_vw[b]; D_v[a][b] = sum of
-// d_w^b.  One warp per node, one pass per typed range.
+// d_w^b.  Nodes of degree up to dsmall: one thread per node, its 2 L^2 sums in
+// a private column of shared memory (k_node_aggr_small).  Larger nodes: their
+// typed ranges are cut into chunks of at most kAggrChunk entries, one warp per
+// chunk, whose sums are added to the (zeroed) rows (k_node_aggr).
+constexpr int kAggrSmall = 64;        // degree bound of the one-thread nodes
+constexpr int kAggrSmallMaxL = 8;     // types up to which they are used
+constexpr int kAggrSmallThreads = 128;
+constexpr int kAggrChunk = 2048;
+
+// chunks of node v's typed ranges (0 for a node left to the one-thread kernel)
+__global__ void k_aggr_chunks(const int64_t *rowptr, const int32_t *toff, int64_t n, int32_t L,
+                              int dsmall, uint32_t *nch) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c = 0;
+        if (rowptr[v + 1] - rowptr[v] > dsmall) {
+            const int32_t *tv = toff + v * (L + 1);
+            for (int a = 0; a < L; ++a) c += (uint32_t)((tv[a + 1] - tv[a] + kAggrChunk - 1) / kAggrChunk);
+        }
+        nch[v] = c;
+    }
+}
+
+__global__ void __launch_bounds__(kAggrSmallThreads)
+    k_node_aggr_small(const int64_t *rowptr, const uint32_t *adj, const uint32_t *eid,
+                      const int32_t *toff, const uint32_t *tau, int64_t n, int32_t L,
+                      int dsmall, uint32_t *theta, uint32_t *dsum) {
+    extern __shared__ uint32_t col[];  // [2 L^2][blockDim.x]
+    const int tid = threadIdx.x, bd = blockDim.x;
+    const int L2 = L * L;
+    for (int64_t v = blockIdx.x * (int64_t)bd + tid; v < n; v += (int64_t)gridDim.x * bd) {
+        const int64_t rb = rowptr[v], re = rowptr[v + 1];
+        if (re - rb > dsmall) continue;  // a warp of k_node_aggr takes it
+        for (int q = 0; q < 2 * L2; ++q) col[q * bd + tid] = 0u;
+        for (int64_t x = rb; x < re; ++x) {
+            const uint32_t wu = __ldg(adj + x);
+            const int a = (int)(wu >> TG_TSHIFT);
+            const uint32_t *tw = tau + (int64_t)__ldg(eid + x) * L;
+            const int32_t *ow = toff + (int64_t)(wu & TG_IDMASK) * (L + 1);
+            int prev = __ldg(ow);
+            for (int b = 0; b < L; ++b) {
+                const int nx = __ldg(ow + b + 1);
+                col[(a * L + b) * bd + tid] += __ldg(tw + b);
+                col[(L2 + a * L + b) * bd + tid] += (uint32_t)(nx - prev);
+                prev = nx;
+            }
+        }
+        for (int q = 0; q < L2; ++q) {
+            theta[v * L2 + q] = col[q * bd + tid];
+            dsum[v * L2 + q] = col[(L2 + q) * bd + tid];
+        }
+    }
+}
+
 __global__ void k_node_aggr(const int64_t *rowptr, const uint32_t *adj, const uint32_t *eid,
                             const int32_t *toff, const uint32_t *tau, int64_t n, int32_t L,
-                            uint32_t *theta, uint32_t *dsum) {
+                            const uint32_t *nch, const uint32_t *cpos, uint32_t *theta,
+                            uint32_t *dsum) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = wid; v < n; v += nw) {
+    const int64_t items = (int64_t)cpos[n - 1] + nch[n - 1];
+    for (int64_t it = wid; it < items; it += nw) {
+        int64_t lo = 0, hi = n - 1;  // the last node whose first chunk is <= it
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if ((int64_t)cpos[mid] <= it)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int64_t v = lo;
+        int64_t r = it - cpos[v];
         const int64_t rb = rowptr[v];
         const int32_t *tv = toff + v * (L + 1);
-        for (int a = 0; a < L; ++a) {
-            const int s0 = __ldg(tv + a), s1 = __ldg(tv + a + 1);
-            uint32_t at[TG_MAX_TYPES], ad[TG_MAX_TYPES];
+        int a = 0, s0 = 0, s1 = 0;
+        for (; a < L; ++a) {
+            s0 = __ldg(tv + a);
+            s1 = __ldg(tv + a + 1);
+            const int64_t ch = (s1 - s0 + kAggrChunk - 1) / kAggrChunk;
+            if (r < ch) break;
+            r -= ch;
+        }
+        const int c0 = s0 + (int)r * kAggrChunk, c1 = min(s1, c0 + kAggrChunk);
+        uint32_t at[TG_MAX_TYPES], ad[TG_MAX_TYPES];
 #pragma unroll
-            for (int b = 0; b < TG_MAX_TYPES; ++b) {
-                at[b] = 0;
-                ad[b] = 0;
-            }
-            for (int x = s0 + lane; x < s1; x += 32) {
-                const uint32_t w = __ldg(adj + rb + x) & TG_IDMASK;
-                const uint32_t *tw = tau + (int64_t)__ldg(eid + rb + x) * L;
-                const int32_t *ow = toff + (int64_t)w * (L + 1);
-                int prev = __ldg(ow);
-#pragma unroll
-                for (int b = 0; b < TG_MAX_TYPES; ++b) {
-                    if (b < L) {
-                        at[b] += __ldg(tw + b);
-                        const int nx = __ldg(ow + b + 1);
-                        ad[b] += (uint32_t)(nx - prev);
-                        prev = nx;
-                    }
-                }
-            }
+        for (int b = 0; b < TG_MAX_TYPES; ++b) {
+            at[b] = 0;
+            ad[b] = 0;
+        }
+        for (int x = c0 + lane; x < c1; x += 32) {
+            const uint32_t w = __ldg(adj + rb + x) & TG_IDMASK;
+            const uint32_t *tw = tau + (int64_t)__ldg(eid + rb + x) * L;
+            const int32_t *ow = toff + (int64_t)w * (L + 1);
+            int prev = __ldg(ow);
 #pragma unroll
             for (int b = 0; b < TG_MAX_TYPES; ++b) {
                 if (b < L) {
-                    const uint32_t st = __reduce_add_sync(kFull, at[b]);
-                    const uint32_t sd = __reduce_add_sync(kFull, ad[b]);
-                    if (lane == 0) {
-                        theta[(v * L + a) * L + b] = st;
-                        dsum[(v * L + a) * L + b] = sd;
-                    }
+                    at[b] += __ldg(tw + b);
+                    const int nx = __ldg(ow + b + 1);
+                    ad[b] += (uint32_t)(nx - prev);
+                    prev = nx;
+                }
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < TG_MAX_TYPES; ++b) {
+            if (b < L) {
+                const uint32_t st = __reduce_add_sync(kFull, at[b]);
+                const uint32_t sd = __reduce_add_sync(kFull, ad[b]);
+                if (lane == 0) {
+                    if (st) atomicAdd(theta + (v * L + a) * L + b, st);
+                    if (sd) atomicAdd(dsum + (v * L + a) * L + b, sd);
                 }
             }
         }
@@ -947,9 +1018,34 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
     TG_TRY_CUDA(cudaEventRecord(g_last.ev[1], s));
     if (k == 4) {
         if (!theta.alloc((size_t)n * L2, s) || !dsum.alloc((size_t)n * L2, s)) return TG_ENOMEM;
-        k_node_aggr<<<grid_r(n * 32), 256, 0, s>>>(g->rowptr, g->adj, g->eid, g->toff, tau.p, n, L,
-                                                   theta.p, dsum.p); tg_note_launch();
-        TG_TRY_CUDA(cudaGetLastError());
+        const int dsmall = L <= kAggrSmallMaxL ? kAggrSmall : -1;
+        // rows of the chunked nodes start at zero
+        TG_TRY_CUDA(cudaMemsetAsync(theta.p, 0, (size_t)n * L2 * 4, s));
+        TG_TRY_CUDA(cudaMemsetAsync(dsum.p, 0, (size_t)n * L2 * 4, s));
+        if (dsmall >= 0) {
+            const size_t asmem = (size_t)2 * L2 * kAggrSmallThreads * 4;
+            TG_TRY(tg_allow_max_smem((const void *)k_node_aggr_small));
+            int per = 0;
+            TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_node_aggr_small,
+                                                                      kAggrSmallThreads, asmem));
+            const int64_t ag = std::min<int64_t>((int64_t)num_sms_r() * (per > 0 ? per : 1),
+                                                 (n + kAggrSmallThreads - 1) / kAggrSmallThreads);
+            k_node_aggr_small<<<(unsigned)std::max<int64_t>(ag, 1), kAggrSmallThreads, asmem, s>>>(
+                g->rowptr, g->adj, g->eid, g->toff, tau.p, n, L, dsmall, theta.p, dsum.p); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+        }
+        DevBuf<uint32_t> nch, cpos;
+        if (n > 0) {
+            if (!nch.alloc(n, s) || !cpos.alloc(n, s)) return TG_ENOMEM;
+            k_aggr_chunks<<<grid_r(n), 256, 0, s>>>(g->rowptr, g->toff, n, L, dsmall, nch.p); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+            TG_TRY(tg_scan_u32(nch.p, cpos.p, n, s));
+            int per = 0;
+            TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_node_aggr, 256, 0));
+            k_node_aggr<<<(unsigned)((int64_t)num_sms_r() * (per > 0 ? per : 1)), 256, 0, s>>>(
+                g->rowptr, g->adj, g->eid, g->toff, tau.p, n, L, nch.p, cpos.p, theta.p, dsum.p); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+        }
     }
     TG_TRY_CUDA(cudaEventRecord(g_last.ev[2], s));
     if (t.kernel == TG_KERNEL_CYCLES || t.kernel == TG_KERNEL_AUTO) {
