@@ -398,6 +398,21 @@ typedef void *(*tg_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*tg_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 int tg_set_allocator(tg_alloc_fn alloc, tg_free_fn free_fn, void *ctx);
 
+/*
+ * Scratch kept between calls (default allocation path only).  With bytes = 0
+ * (the default) scratch comes from the device's default stream-ordered pool,
+ * which hands freed memory back to the device at each synchronisation, so
+ * every call maps its scratch anew (milliseconds for the gigabytes a large
+ * count needs).  With bytes > 0 the library allocates from a pool of its own
+ * per device that keeps up to `bytes` of freed scratch mapped for later calls;
+ * other allocators in the process cannot use that memory meanwhile.
+ * tg_set_memory_retention(0) also releases what the pools hold;
+ * tg_trim_memory releases it and keeps the setting.  TG_ECUDA on a failed
+ * CUDA call (tg_last_cuda_error has its code).
+ */
+int tg_set_memory_retention(uint64_t bytes);
+int tg_trim_memory(void);
+
 /* ------------------------------------------------------- measurement ---- */
 /* Kernels launched by this library since it was loaded. */
 uint64_t tg_launch_count(void);

@@ -26,7 +26,7 @@ __all__ = [
     "tg_work_model", "tg_slots", "tg_global_len", "tg_config_count", "tg_config_rank",
     "tg_config_unrank", "tg_paper_hash", "tg_slot_config", "tg_strerror", "tg_version",
     "tg_debug_fail_alloc", "tg_set_tune", "tg_get_tune", "tg_launch_count", "tg_last_timing",
-    "tg_last_cuda_error", "TG_GRAPHLET", "TG_ORBIT",
+    "tg_last_cuda_error", "tg_set_memory_retention", "tg_trim_memory", "TG_GRAPHLET", "TG_ORBIT",
 ]
 
 TG_OK = 0
@@ -139,6 +139,8 @@ def lib():
             "tg_global_finalize": (ctypes.c_int, [i32, i32, vp, vp]),
             "tg_work_model": (ctypes.c_int, [vp, vp, vp]),
             "tg_set_allocator": (ctypes.c_int, [vp, vp, vp]),
+            "tg_set_memory_retention": (ctypes.c_int, [u64]),
+            "tg_trim_memory": (ctypes.c_int, []),
             "tg_debug_fail_alloc": (ctypes.c_int, [i64]),
             "tg_set_tune": (ctypes.c_int, [vp]),
             "tg_launch_count": (u64, []),
@@ -487,6 +489,17 @@ def tg_get_tune() -> dict:
 def tg_launch_count() -> int:
     """Kernels launched by libtg.so so far in this process."""
     return int(lib().tg_launch_count())
+
+
+def tg_set_memory_retention(nbytes: int) -> None:
+    """Keep up to ``nbytes`` of freed device scratch mapped between calls (0 restores
+    the default pool, which returns scratch to the device at each synchronisation)."""
+    _check(lib().tg_set_memory_retention(int(nbytes)), "tg_set_memory_retention")
+
+
+def tg_trim_memory() -> None:
+    """Release the scratch the library's pools keep, keeping the retention setting."""
+    _check(lib().tg_trim_memory(), "tg_trim_memory")
 
 
 def tg_last_cuda_error() -> int:

@@ -2,6 +2,7 @@
 // injection, exclusive scans and a stable LSD radix sort on uint64 keys.
 // All kernels here are this library's own; no vendor sort or scan is used.
 #include <atomic>
+#include <mutex>
 
 #include "tg_internal.cuh"
 
@@ -48,6 +49,61 @@ extern "C" int tg_debug_fail_alloc(int64_t n) {
     return TG_OK;
 }
 
+// Retained scratch: with a positive retention the library allocates from a
+// pool of its own per device whose release threshold is that many bytes, so
+// freed scratch stays mapped for the next call instead of going back to the
+// device at each synchronisation.
+constexpr int kMaxDevices = 64;
+static std::mutex g_pool_mu;
+static std::atomic<uint64_t> g_retain{0};
+static cudaMemPool_t g_pools[kMaxDevices] = {};
+
+static cudaMemPool_t lib_pool(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t thr = g_retain.load();
+        (void)cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        g_pools[dev] = pool;
+    }
+    return g_pools[dev];
+}
+
+extern "C" int tg_set_memory_retention(uint64_t bytes) {
+    g_retain.store(bytes);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (int d = 0; d < kMaxDevices; ++d) {
+        if (!g_pools[d]) continue;
+        uint64_t thr = bytes;
+        if (cudaMemPoolSetAttribute(g_pools[d], cudaMemPoolAttrReleaseThreshold, &thr) != cudaSuccess ||
+            (bytes == 0 && cudaMemPoolTrimTo(g_pools[d], 0) != cudaSuccess)) {
+            tg_note_cuda_error(cudaGetLastError());
+            return TG_ECUDA;
+        }
+    }
+    return TG_OK;
+}
+
+extern "C" int tg_trim_memory(void) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (int d = 0; d < kMaxDevices; ++d) {
+        if (g_pools[d] && cudaMemPoolTrimTo(g_pools[d], 0) != cudaSuccess) {
+            tg_note_cuda_error(cudaGetLastError());
+            return TG_ECUDA;
+        }
+    }
+    return TG_OK;
+}
+
 void *tg_dalloc(size_t bytes, cudaStream_t s) {
     int64_t c = g_fail_countdown.load();
     while (c > 0) {
@@ -58,7 +114,13 @@ void *tg_dalloc(size_t bytes, cudaStream_t s) {
     }
     if (g_alloc) return g_alloc(bytes, s, g_alloc_ctx);
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaMemPool_t pool = nullptr;
+    if (g_retain.load() > 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) pool = lib_pool(dev);
+    }
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s) : cudaMallocAsync(&p, bytes, s);
+    if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return nullptr;
     }

@@ -134,6 +134,26 @@ def test_chung_lu_medium(variant):
     _check_all(G, levels=(tg.TG_GRAPHLET,), ks=(4,))
 
 
+def test_memory_retention_keeps_counts():
+    """Scratch from the library's retaining pool (and after a trim) gives the
+    same global and per-edge counts as the default pool."""
+    g0 = synth.rng(705)
+    u, v = synth.chung_lu_exact(20000, 120000, 2.1, g0)
+    G = synth.TypedEdgeList(20000, u, v, synth.zipf_types(20000, 5, 1.2, g0), 5, "cl-20k-b")
+    g, og = _both(G)
+    want_g, want_e = og.global_counts(k=4), og.per_edge(k=4, level="graphlet")
+    try:
+        tg.tg_set_memory_retention(1 << 30)
+        for _ in range(2):
+            assert np.array_equal(tg.tg_count_global(g, 4), want_g)
+            assert np.array_equal(tg.tg_count_per_edge(g, 4, tg.TG_GRAPHLET), want_e)
+        tg.tg_trim_memory()
+        assert np.array_equal(tg.tg_count_global(g, 4), want_g)
+    finally:
+        tg.tg_set_memory_retention(0)
+    assert np.array_equal(tg.tg_count_global(g, 4), want_g)
+
+
 def test_device_inputs_and_outputs():
     import torch
     G = synth.er_1000(seed=2)
