@@ -159,7 +159,7 @@ def committed_traffic():
     committed ncu summary, used only while the kernel source still matches the
     one profiled."""
     path = os.path.join(ROOT, "profiles", "k_cyc_edge_traffic.json")
-    src = os.path.join(ROOT, "paper_1901_10026_gb300", "csrc", "tg_cycles.cu")
+    src = os.path.join(ROOT, "paper_1901_10026_gb300", "csrc", "tg_edges.cu")
     try:
         rec = json.load(open(path))
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()

@@ -30,7 +30,7 @@
 //     off the edge.
 // The enumeration work is the number of degree-ordered wedges plus the
 // 4-clique search, instead of sum over w in S_i u S_j u T_ij of d_w per edge.
-// The per-edge pass (k_cyc_edge) then needs only Gamma_i n Gamma_j (the T
+// The per-edge pass (tg_edges.cu) then needs only Gamma_i n Gamma_j (the T
 // sums) and O(L^2) identity and closed-form arithmetic.
 #include <algorithm>
 #include <new>
@@ -290,8 +290,12 @@ __device__ __forceinline__ void c4_one(const C4Params &p, unsigned long long *h4
                                        uint32_t *cb, uint32_t b) {
     const int L = p.L;
     uint32_t c[TG_MAX_TYPES];
-    for (int t = 0; t < L; ++t) c[t] = __ldcg(cb + t);
-    if (p.g4) c4_add(h4, L, ta, p.ntype[b], c);
+    uint32_t sum = 0;
+    for (int t = 0; t < L; ++t) {
+        c[t] = __ldcg(cb + t);
+        sum += c[t];
+    }
+    if (p.g4 && sum > 1) c4_add(h4, L, ta, p.ntype[b], c);  // one middle closes no cycle
     for (int t = 0; t < L; ++t)
         if (c[t]) cb[t] = 0u;
 }
@@ -547,6 +551,49 @@ __global__ void k_c4_units(const int64_t *ustart, int64_t nq, const int64_t *tgt
 // a 5-step search over the lanes' running sums.  op(b, t_u) runs for every
 // entry b ranked below a of a member u.  With stride > 32 the warp takes every
 // (stride / 32)-th chunk of 32 members (no window: f_lo = 0, f_hi unbounded).
+// One chunk of 32 members (lane values len, bu, tu) of c4_warp_walk, with
+// running sums in IT (int when every list is short enough); returns the
+// chunk's length.
+template <class IT, class Op>
+__device__ __forceinline__ int64_t c4_chunk(const C4Params &p, uint32_t a, int64_t len64,
+                                            int64_t bu, int tu, int64_t at, int64_t f_lo,
+                                            int64_t f_hi, Op &op) {
+    const int lane = threadIdx.x & 31;
+    const IT len = (IT)len64;
+    IT incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const IT y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const IT total = __shfl_sync(kFull, incl, 31);
+    const IT lo = (IT)(f_lo > at ? (f_lo - at < (int64_t)total ? f_lo - at : (int64_t)total) : 0);
+    const IT hi = (IT)(f_hi - at < (int64_t)total ? f_hi - at : (int64_t)total);
+    for (IT b0 = lo; b0 < hi; b0 += 32) {
+        const IT pos = b0 + lane;
+        int r = 0;  // the first member whose running sum exceeds pos
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const IT v = __shfl_sync(kFull, incl, r + st - 1);
+            if (v <= pos) r += st;
+        }
+        const int64_t bur = __shfl_sync(kFull, bu, r);
+        const IT str = __shfl_sync(kFull, incl - len, r);
+        const int tur = __shfl_sync(kFull, tu, r);
+        if (pos < hi) {
+            const uint32_t b = __ldg(p.adj + bur + (int64_t)(pos - str)) & TG_IDMASK;
+            if (b > a) op(b, tur);
+        }
+    }
+    return (int64_t)total;
+}
+
+// Positions [f_lo, f_hi) of anchor a's walk, from member m on (its first
+// position `at`), by one warp: members are taken 32 at a time, their list
+// lengths scanned across the lanes, and each position mapped to its member by
+// a 5-step search over the lanes' running sums.  op(b, t_u) runs for every
+// entry b ranked below a of a member u.  With stride > 32 the warp takes every
+// (stride / 32)-th chunk of 32 members (no window: f_lo = 0, f_hi unbounded).
 template <class Op>
 __device__ __forceinline__ void c4_warp_walk(const C4Params &p, uint32_t a, int64_t ba, int da,
                                              int m, int64_t at, int64_t f_lo, int64_t f_hi,
@@ -568,32 +615,10 @@ __device__ __forceinline__ void c4_warp_walk(const C4Params &p, uint32_t a, int6
                 }
             }
         }
-        int64_t incl = len;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const int64_t total = __shfl_sync(kFull, incl, 31);
-        const int64_t lo = f_lo > at ? f_lo - at : 0;
-        const int64_t hi = f_hi - at < total ? f_hi - at : total;
-        for (int64_t b0 = lo; b0 < hi; b0 += 32) {
-            const int64_t pos = b0 + lane;
-            int r = 0;  // the first member whose running sum exceeds pos
-#pragma unroll
-            for (int st = 16; st > 0; st >>= 1) {
-                const int64_t v = __shfl_sync(kFull, incl, r + st - 1);
-                if (v <= pos) r += st;
-            }
-            const int64_t bur = __shfl_sync(kFull, bu, r);
-            const int64_t str = __shfl_sync(kFull, incl - len, r);
-            const int tur = __shfl_sync(kFull, tu, r);
-            if (pos < hi) {
-                const uint32_t b = __ldg(p.adj + bur + (pos - str)) & TG_IDMASK;
-                if (b > a) op(b, tur);
-            }
-        }
-        at += total;
+        if (__all_sync(kFull, len < ((int64_t)1 << 26)))  // 32 lists sum below 2^31
+            at += c4_chunk<int>(p, a, len, bu, tu, at, f_lo, f_hi, op);
+        else
+            at += c4_chunk<int64_t>(p, a, len, bu, tu, at, f_lo, f_hi, op);
     }
 }
 
@@ -1529,549 +1554,6 @@ __global__ void k_cyc_correct(unsigned long long *hist, int64_t off4, int64_t n4
     }
 }
 
-// ------------------------------------------------------ per-edge counts ----
-struct EdgeParams {
-    const int64_t *rowptr;
-    const uint32_t *adj;
-    const uint32_t *eid;
-    const int32_t *toff;
-    const uint8_t *ntype;
-    const int2 *edges;
-    const uint32_t *order;
-    const uint32_t *ustart;
-    const uint32_t *ulist;     // units this launch takes (NULL: units 0 .. nunits - 1)
-    uint32_t nunits;
-    const uint32_t *tau;
-    const uint32_t *theta;
-    const uint32_t *dsum;
-    const unsigned long long *c4e;
-    const unsigned long long *k4e;
-    int32_t L, P, k, level;
-    int64_t nbits;
-    uint32_t *emap;            // per CTA, nbits entries: edge id of (j, y) for y in Gamma_j
-    unsigned long long *tsum;  // split mode: per edge id, B, C and DT (3 L^2 uint64)
-    unsigned long long *queue;
-    uint64_t *rows;
-    int64_t width;
-    unsigned long long *hist;
-    int64_t hist_len;
-    int32_t hist_smem;
-    int64_t off1, off2, off4, n4;
-    unsigned long long *work;  // [0]: Gamma_i entries, [3]: T members
-};
-
-// The inputs of the identities for one edge (see tg_reuse.cu).
-struct EdgeIn {
-    int L, ti, tj;
-    const unsigned long long *B, *C, *DT;  // ordered [a][b], this warp's shared memory
-    const unsigned long long *c4;          // ordered [a][b]
-    const unsigned long long *k4;          // unordered pairs
-    const uint32_t *thi, *thj, *dvi, *dvj; // ordered [a][b]
-    const uint32_t *tn;                    // tau of the edge: |T^t|
-    const int32_t *toi, *toj;
-};
-
-struct EdgeEval {
-    const EdgeIn &in;
-    __device__ long long deg_i(int b) const { return __ldg(in.toi + b + 1) - __ldg(in.toi + b); }
-    __device__ long long deg_j(int b) const { return __ldg(in.toj + b + 1) - __ldg(in.toj + b); }
-    __device__ long long Tn(int a) const { return (long long)__ldg(in.tn + a); }
-    __device__ long long Si(int a) const { return deg_i(a) - Tn(a) - (a == in.tj); }
-    __device__ long long Sj(int a) const { return deg_j(a) - Tn(a) - (a == in.ti); }
-    __device__ long long B(int a, int b) const { return (long long)in.B[a * in.L + b]; }
-    __device__ long long C(int a, int b) const { return (long long)in.C[a * in.L + b]; }
-    __device__ long long DT(int a, int b) const { return (long long)in.DT[a * in.L + b]; }
-    __device__ long long Q(int a, int b) const {
-        if (!in.k4) return 0;  // global mode: added from the 4-clique totals
-        const long long k = (long long)__ldg(in.k4 + pair_index(in.L, a, b));
-        return a == b ? 2 * k : k;
-    }
-    __device__ long long TSj(int a, int b) const {
-        return B(a, b) - Q(a, b) - (b == in.ti ? Tn(a) : 0);
-    }
-    __device__ long long TSi(int a, int b) const {
-        return C(a, b) - Q(a, b) - (b == in.tj ? Tn(a) : 0);
-    }
-    __device__ long long SSj(int a, int b) const {
-        return (long long)__ldg(in.thj + a * in.L + b) - B(a, b) - (a == in.ti ? Tn(b) : 0);
-    }
-    __device__ long long SSi(int a, int b) const {
-        return (long long)__ldg(in.thi + a * in.L + b) - C(a, b) - (a == in.tj ? Tn(b) : 0);
-    }
-    __device__ long long DSj(int a, int b) const {
-        return (long long)__ldg(in.dvj + a * in.L + b) - DT(a, b) - (a == in.ti ? deg_i(b) : 0);
-    }
-    __device__ long long DSi(int a, int b) const {
-        return (long long)__ldg(in.dvi + a * in.L + b) - DT(a, b) - (a == in.tj ? deg_j(b) : 0);
-    }
-    __device__ long long S6(int a, int b) const {
-        const long long c4 = in.c4 ? (long long)__ldg(in.c4 + a * in.L + b) : 0;
-        return c4 - B(a, b) + (b == in.ti ? Tn(a) : 0);
-    }
-    __device__ long long Ypart(int a, int b) const {  // Y without its G6 terms
-        return DSi(a, b) - (b == in.ti ? Si(a) : 0) - SSi(a, b) + DSj(a, b) -
-               (b == in.tj ? Sj(a) : 0) - SSj(a, b);
-    }
-    __device__ long long Z(int a, int b) const {
-        return DT(a, b) - Tn(a) * ((b == in.ti) + (b == in.tj)) - Q(a, b) - TSi(a, b) -
-               TSj(a, b);
-    }
-};
-
-// Per-edge table of the identities' ordered L x L terms (one warp fills it,
-// one lane per entry), so a type pair reads its terms instead of re-deriving
-// them: TSi, TSj, SSi, SSj, G6 = S6 - TSi^T, Y without its G6 terms, Z, Q.
-enum { XT_TSI = 0, XT_TSJ, XT_SSI, XT_SSJ, XT_G6, XT_YP, XT_Z, XT_Q, XT_N };
-
-__device__ __forceinline__ void fill_terms(const EdgeEval &E, int L, long long *xt) {
-    const int lane = threadIdx.x & 31, L2 = L * L;
-    for (int m = lane; m < L2; m += 32) {
-        const int a = m / L, b = m % L;
-        xt[XT_TSI * L2 + m] = E.TSi(a, b);
-        xt[XT_TSJ * L2 + m] = E.TSj(a, b);
-        xt[XT_SSI * L2 + m] = E.SSi(a, b);
-        xt[XT_SSJ * L2 + m] = E.SSj(a, b);
-        xt[XT_YP * L2 + m] = E.Ypart(a, b);
-        xt[XT_Z * L2 + m] = E.Z(a, b);
-        xt[XT_Q * L2 + m] = E.Q(a, b);
-        xt[XT_G6 * L2 + m] = E.S6(a, b);
-    }
-    __syncwarp();
-    for (int m = lane; m < L2; m += 32) {
-        const int a = m / L, b = m % L;
-        xt[XT_G6 * L2 + m] -= xt[XT_TSI * L2 + b * L + a];
-    }
-    __syncwarp();
-}
-
-// Orbits g3..g12 of the type pair (t, u), t <= u, from the table.
-__device__ __forceinline__ void pair_orbits_tab(const long long *xt, int L, int t, int u,
-                                                uint64_t sit, uint64_t siu, uint64_t sjt,
-                                                uint64_t sju, uint64_t tt, uint64_t tu,
-                                                uint64_t g[10]) {
-    const int L2 = L * L, m = t * L + u, mt = u * L + t;
-    auto X = [&](int k, int mm) -> long long { return xt[k * L2 + mm]; };
-    auto sym = [&](int k) -> long long { return t == u ? X(k, m) : X(k, m) + X(k, mt); };
-    const uint64_t g12 = (uint64_t)(sym(XT_Q) / 2);
-    const uint64_t g10 = (uint64_t)(sym(XT_TSI) + sym(XT_TSJ));
-    const long long sisi_tu = X(XT_SSI, m) - X(XT_TSI, mt), sisi_ut = X(XT_SSI, mt) - X(XT_TSI, m);
-    const long long sjsj_tu = X(XT_SSJ, m) - X(XT_TSJ, mt), sjsj_ut = X(XT_SSJ, mt) - X(XT_TSJ, m);
-    const uint64_t g7 =
-        (uint64_t)((t == u ? sisi_tu + sjsj_tu : sisi_tu + sjsj_tu + sisi_ut + sjsj_ut) / 2);
-    const uint64_t g6 = (uint64_t)sym(XT_G6);
-    const long long y_tu = X(XT_YP, m) - X(XT_G6, m) - X(XT_G6, mt);
-    const long long y_ut = X(XT_YP, mt) - X(XT_G6, mt) - X(XT_G6, m);
-    const uint64_t g3 = (uint64_t)(t == u ? y_tu : y_tu + y_ut);
-    const uint64_t g8 = (uint64_t)sym(XT_Z);
-    uint64_t g4, g5, g9, g11;
-    if (t == u) {
-        g4 = sit * sjt - g6;
-        g5 = c2(sit) + c2(sjt) - g7;
-        g9 = tt * (sit + sjt) - g10;
-        g11 = c2(tt) - g12;
-    } else {
-        g4 = sit * sju + siu * sjt - g6;
-        g5 = sit * siu + sjt * sju - g7;
-        g9 = tt * (siu + sju) + tu * (sit + sjt) - g10;
-        g11 = tt * tu - g12;
-    }
-    g[0] = g3;
-    g[1] = g4;
-    g[2] = g5;
-    g[3] = g6;
-    g[4] = g7;
-    g[5] = g8;
-    g[6] = g9;
-    g[7] = g10;
-    g[8] = g11;
-    g[9] = g12;
-}
-
-__device__ __forceinline__ void hadd_e(const EdgeParams &p, unsigned long long *shist, int64_t x,
-                                       unsigned long long v) {
-    if (!v) return;
-    if (p.hist_smem)
-        atomicAdd(shist + x, v);
-    else
-        atomicAdd(p.hist + x, v);
-}
-
-// The 2- and 3-node entries of edge e, then the identities and closed forms
-// per type pair (t, u) from B, C, DT (this warp's, in shared memory) and the
-// per-edge or per-node rows; written to the row of e or added to the
-// histogram.  Called by the 32 lanes of the edge's warp.
-__device__ void edge_finish(const EdgeParams &p, unsigned long long *shist, int64_t e, int i, int j,
-                            int ti, int tj, const int32_t *toi, const int32_t *toj,
-                            const uint32_t *tn, const unsigned long long *Bm,
-                            const unsigned long long *Cm, const unsigned long long *Dm,
-                            long long *xt) {
-    const int lane = threadIdx.x & 31;
-    const int L = p.L, P = p.P, L2 = L * L;
-    // 2- and 3-node entries
-    if (p.rows) {
-        uint64_t *row = p.rows + e * p.width;
-        for (int t = lane; t < L; t += 32) {
-            const uint32_t tt = __ldg(tn + t);
-            const int64_t si = (int64_t)(__ldg(toi + t + 1) - __ldg(toi + t)) - tt - (t == tj);
-            const int64_t sj = (int64_t)(__ldg(toj + t + 1) - __ldg(toj + t)) - tt - (t == ti);
-            row[t] = (uint64_t)(si + sj);
-            row[L + t] = tt;
-        }
-    } else {
-        if (lane == 0) {
-            int a = ti, b = tj;
-            sort2(a, b);
-            hadd_e(p, shist, (int64_t)a + (int64_t)(b + 1) * b / 2, 1ull);
-        }
-        for (int t = lane; t < L; t += 32) {
-            const uint32_t tt = __ldg(tn + t);
-            const int64_t si = (int64_t)(__ldg(toi + t + 1) - __ldg(toi + t)) - tt - (t == tj);
-            const int64_t sj = (int64_t)(__ldg(toj + t + 1) - __ldg(toj + t)) - tt - (t == ti);
-            int a = ti, b = tj, cc = t;
-            sort2(a, b);
-            sort2(b, cc);
-            sort2(a, b);
-            const int64_t r = colex3(a, b, cc);
-            hadd_e(p, shist, p.off1 + r, (unsigned long long)(si + sj));
-            hadd_e(p, shist, p.off2 + r, (unsigned long long)tt);
-        }
-    }
-    if (p.k == 4) {
-        EdgeIn in;
-        in.L = L;
-        in.ti = ti;
-        in.tj = tj;
-        in.B = Bm;
-        in.C = Cm;
-        in.DT = Dm;
-        in.c4 = p.c4e ? p.c4e + e * L2 : nullptr;
-        in.k4 = p.k4e ? p.k4e + e * P : nullptr;
-        in.thi = p.theta + (int64_t)i * L2;
-        in.thj = p.theta + (int64_t)j * L2;
-        in.dvi = p.dsum + (int64_t)i * L2;
-        in.dvj = p.dsum + (int64_t)j * L2;
-        in.tn = tn;
-        in.toi = toi;
-        in.toj = toj;
-        const EdgeEval E{in};
-        fill_terms(E, L, xt);
-        for (int pr = lane; pr < P; pr += 32) {
-            int t, u;
-            unpair(L, pr, t, u);
-            uint64_t g[10];
-            pair_orbits_tab(xt, L, t, u, (uint64_t)E.Si(t), (uint64_t)E.Si(u), (uint64_t)E.Sj(t),
-                            (uint64_t)E.Sj(u), (uint64_t)E.Tn(t), (uint64_t)E.Tn(u), g);
-            if (p.rows) {
-                uint64_t *row = p.rows + e * p.width + 2 * L;
-                if (p.level == TG_ORBIT) {
-#pragma unroll
-                    for (int o = 0; o < 10; ++o) row[o * P + pr] = g[o];
-                } else {
-                    row[0 * P + pr] = g[0] + g[1];
-                    row[1 * P + pr] = g[2];
-                    row[2 * P + pr] = g[3];
-                    row[3 * P + pr] = g[4] + g[5] + g[6];
-                    row[4 * P + pr] = g[7] + g[8];
-                    row[5 * P + pr] = g[9];
-                }
-            } else {
-                const uint64_t h[6] = {g[0] + g[1], g[2], g[3], g[4] + g[5] + g[6],
-                                       g[7] + g[8], g[9]};
-                if (h[0] | h[1] | h[2] | h[3] | h[4] | h[5]) {
-                    int a = ti, b = tj, cc = t, d = u;
-                    sort2(a, b);
-                    sort2(cc, d);
-                    sort2(a, cc);
-                    sort2(b, d);
-                    sort2(b, cc);
-                    const int64_t r = colex4(a, b, cc, d);
-#pragma unroll
-                    for (int qq = 0; qq < 6; ++qq) hadd_e(p, shist, p.off4 + qq * p.n4 + r, h[qq]);
-                }
-            }
-        }
-    }
-}
-
-// One chunk of Gamma_i (one entry per lane): the lanes holding a T member y
-// (packed entry w, edge ids eiy of (i, y) and ejy of (j, y)) add tau_jy,
-// tau_iy and y's typed degrees, by the type of y, to this warp's B, C, DT.
-// All 32 lanes call it.
-__device__ __forceinline__ void tsum_chunk(const EdgeParams &p, bool isT, uint32_t w, uint32_t eiy,
-                                           uint32_t ejy, unsigned long long *Bm,
-                                           unsigned long long *Cm, unsigned long long *Dm) {
-    const int L = p.L;
-    const int lane = threadIdx.x & 31;
-    const int a = (int)(w >> TG_TSHIFT);
-    const unsigned tm = __match_any_sync(kFull, isT ? a : -1);
-    const bool lead = isT && lane == __ffs(tm) - 1;
-    const uint32_t *tiy = p.tau, *tjy = p.tau;
-    const int32_t *ty = p.toff;
-    if (isT) {
-        tiy = p.tau + (int64_t)eiy * L;
-        tjy = p.tau + (int64_t)ejy * L;
-        ty = p.toff + (int64_t)(w & TG_IDMASK) * (L + 1);
-    }
-    int prev = isT ? __ldg(ty) : 0;
-    for (int b = 0; b < L; ++b) {
-        uint32_t vb = 0, vc = 0, vd = 0;
-        if (isT) {
-            vb = __ldg(tjy + b);
-            vc = __ldg(tiy + b);
-            const int nx = __ldg(ty + b + 1);
-            vd = (uint32_t)(nx - prev);
-            prev = nx;
-        }
-        const uint32_t sb = __reduce_add_sync(tm, vb);
-        const uint32_t sc = __reduce_add_sync(tm, vc);
-        const uint32_t sd = __reduce_add_sync(tm, vd);
-        if (lead) {
-            Bm[a * L + b] += sb;
-            Cm[a * L + b] += sc;
-            Dm[a * L + b] += sd;
-        }
-    }
-}
-
-constexpr int kEdgeMaxThreads = 512;
-constexpr int kTsumThreads = 1024;
-
-// One CTA per unit of edges sharing j (Gamma_j bitmap and edge-id map shared
-// by the CTA), one warp per edge: T = Gamma_i n Gamma_j gives B, C, DT.
-// kWrite: store them for k_cyc_finish (fewer registers, more warps in
-// flight for the gathers); else finish the edge here.
-template <bool kWrite>
-__global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc_edge(EdgeParams p) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
-    const int L = p.L, P = p.P, L2 = L * L;
-    size_t off = 0;
-    unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);
-    if (p.hist_smem) off += ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
-    // per warp: B, C, DT, then (finishing here) the table of identity terms
-    const size_t tbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
-    const size_t wbytes = tbytes + (kWrite ? 0 : (size_t)XT_N * L2 * 8);
-    unsigned long long *Bm = reinterpret_cast<unsigned long long *>(smem + off + warp * wbytes);
-    unsigned long long *Cm = Bm + L2;
-    unsigned long long *Dm = Cm + L2;
-    long long *xt = reinterpret_cast<long long *>(smem + off + warp * wbytes + tbytes);
-    off += (size_t)W * wbytes;
-    unsigned long long *s_unit = reinterpret_cast<unsigned long long *>(smem + off);
-    off += 16;
-    uint32_t *bm = reinterpret_cast<uint32_t *>(smem + off);
-    const int64_t bwords = (p.nbits + 31) >> 5;
-    uint32_t *emap = p.emap + (int64_t)blockIdx.x * p.nbits;
-    for (int64_t x = tid; x < bwords; x += blockDim.x) bm[x] = 0u;
-    if (p.hist_smem)
-        for (int64_t x = tid; x < p.hist_len; x += blockDim.x) shist[x] = 0;
-    const int64_t *__restrict__ rowptr = p.rowptr;
-    const uint32_t *__restrict__ adj = p.adj;
-    int cur_j = -1;
-    int64_t cur_bj = 0;
-    int cur_dj = 0;
-    unsigned long long wk_gamma = 0, wk_t = 0;
-
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) *s_unit = atomicAdd(p.queue, 1ull);
-        __syncthreads();
-        const unsigned long long item = *s_unit;
-        if (item >= p.nunits) break;
-        const uint32_t un = p.ulist ? p.ulist[item] : (uint32_t)item;
-        const uint32_t p0 = p.ustart[un], p1 = p.ustart[un + 1];
-        const int2 ab0 = p.edges[p.order[p0]];
-        const int j = min(ab0.x, ab0.y);
-        const int64_t bj = rowptr[j];
-        const int dj = (int)(rowptr[j + 1] - bj);
-        if (p.k == 4 && j != cur_j) {
-            for (int x = tid; x < cur_dj; x += blockDim.x) {
-                const uint32_t id = __ldg(adj + cur_bj + x) & TG_IDMASK;
-                if ((int64_t)id < p.nbits) atomicAnd(&bm[id >> 5], ~(1u << (id & 31u)));
-            }
-            __syncthreads();
-            for (int x = tid; x < dj; x += blockDim.x) {
-                const uint32_t id = __ldg(adj + bj + x) & TG_IDMASK;
-                if ((int64_t)id < p.nbits) {
-                    atomicOr(&bm[id >> 5], 1u << (id & 31u));
-                    emap[id] = __ldg(p.eid + bj + x);
-                }
-            }
-            cur_j = j;
-            cur_bj = bj;
-            cur_dj = dj;
-            __syncthreads();
-        }
-        for (uint32_t q = p0 + warp; q < p1; q += W) {
-            const int64_t e = p.order[q];
-            const int2 ab = p.edges[e];
-            const int i = max(ab.x, ab.y);
-            const int ti = p.ntype[i], tj = p.ntype[j];
-            const int64_t bi = rowptr[i];
-            const int di = (int)(rowptr[i + 1] - bi);
-            const int32_t *toi = p.toff + (int64_t)i * (L + 1);
-            const int32_t *toj = p.toff + (int64_t)j * (L + 1);
-            const uint32_t *tn = p.tau + e * L;
-            if (p.k == 4) {
-                for (int x = lane; x < 3 * L2; x += 32) Bm[x] = 0ull;
-                __syncwarp();
-                // T = Gamma_i n Gamma_j: sums of tau_jy, tau_iy and d_y by types
-                for (int c0 = 0; c0 < di; c0 += 32) {
-                    const int x = c0 + lane;
-                    bool isT = false;
-                    uint32_t w = 0;
-                    if (x < di) {
-                        w = __ldg(adj + bi + x);
-                        const uint32_t id = w & TG_IDMASK;
-                        if ((int)id != j)
-                            isT = (int64_t)id < p.nbits ? bm_test(bm, id)
-                                                        : contains(adj, bj, toj, w);
-                    }
-                    uint32_t eiy = 0, ejy = 0;
-                    if (isT) {
-                        const uint32_t yid = w & TG_IDMASK;
-                        eiy = __ldg(p.eid + bi + x);
-                        if ((int64_t)yid < p.nbits) {
-                            ejy = __ldcg(emap + yid);  // written for this j before the barrier
-                        } else {
-                            const int pj = find_pos(adj, bj, toj, w);
-                            ejy = __ldg(p.eid + bj + (pj < 0 ? 0 : pj));
-                        }
-                    }
-                    tsum_chunk(p, isT, w, eiy, ejy, Bm, Cm, Dm);
-                    const unsigned tb = __ballot_sync(kFull, isT);
-                    if (lane == 0) wk_t += (unsigned long long)__popc(tb);
-                }
-                __syncwarp();
-            }
-            if (lane == 0) wk_gamma += (unsigned long long)di;
-            if (kWrite) {
-                // B, C, DT of this edge for the finishing kernel
-                unsigned long long *dst = p.tsum + (int64_t)q * 3 * L2;
-                for (int x = lane; x < 3 * L2; x += 32) dst[x] = Bm[x];
-            } else {
-                edge_finish(p, shist, e, i, j, ti, tj, toi, toj, tn, Bm, Cm, Dm, xt);
-            }
-            __syncwarp();  // this warp's matrices are cleared for the next edge
-        }
-    }
-    if (p.hist_smem) {
-        __syncthreads();
-        for (int64_t x = tid; x < p.hist_len; x += blockDim.x)
-            if (shist[x]) atomicAdd(p.hist + x, shist[x]);
-    }
-    if (p.work && lane == 0) {
-        atomicAdd(p.work + 0, wk_gamma);
-        atomicAdd(p.work + 3, wk_t);
-    }
-}
-
-// T sums of light units (Gamma_j of at most TG_LIGHT_DEGREE entries): one warp
-// per unit, Gamma_j in a per-warp hash map from node id to the edge id of
-// (j, y); the unit's edges one after the other, no CTA barrier.
-constexpr int kTsumLightWarps = 8;
-
-__global__ void __launch_bounds__(kTsumLightWarps * 32) k_cyc_tsum_light(EdgeParams p) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int L = p.L, L2 = L * L;
-    const size_t wbytes = (((size_t)3 * L2 * 8 + 15) & ~(size_t)15) + (size_t)2 * 4 * (1 << TG_LIGHT_LG);
-    unsigned long long *Bm = reinterpret_cast<unsigned long long *>(smem + warp * wbytes);
-    unsigned long long *Cm = Bm + L2;
-    unsigned long long *Dm = Cm + L2;
-    uint32_t *hk = reinterpret_cast<uint32_t *>(smem + warp * wbytes + (((size_t)3 * L2 * 8 + 15) & ~(size_t)15));
-    uint32_t *hv = hk + (1 << TG_LIGHT_LG);
-    const int64_t *__restrict__ rowptr = p.rowptr;
-    const uint32_t *__restrict__ adj = p.adj;
-    unsigned long long wk_gamma = 0, wk_t = 0;
-    for (;;) {
-        unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(p.queue, 1ull);
-        item = __shfl_sync(kFull, item, 0);
-        if (item >= p.nunits) break;
-        const uint32_t un = p.ulist[item];
-        const uint32_t p0 = p.ustart[un], p1 = p.ustart[un + 1];
-        const int2 ab0 = p.edges[p.order[p0]];
-        const int j = min(ab0.x, ab0.y);
-        const int64_t bj = rowptr[j];
-        const int dj = (int)(rowptr[j + 1] - bj);
-        for (int q = lane; q < (1 << TG_LIGHT_LG); q += 32) hk[q] = 0u;
-        __syncwarp();
-        for (int x = lane; x < dj; x += 32)
-            hmap_put(hk, hv, TG_LIGHT_LG, __ldg(adj + bj + x) & TG_IDMASK, __ldg(p.eid + bj + x));
-        __syncwarp();
-        for (uint32_t q = p0; q < p1; ++q) {
-            const int64_t e = p.order[q];
-            const int2 ab = p.edges[e];
-            const int i = max(ab.x, ab.y);
-            const int64_t bi = rowptr[i];
-            const int di = (int)(rowptr[i + 1] - bi);
-            for (int x = lane; x < 3 * L2; x += 32) Bm[x] = 0ull;
-            __syncwarp();
-            for (int c0 = 0; c0 < di; c0 += 32) {
-                const int x = c0 + lane;
-                bool isT = false;
-                uint32_t w = 0, eiy = 0, ejy = 0;
-                if (x < di) {
-                    w = __ldg(adj + bi + x);
-                    const uint32_t id = w & TG_IDMASK;
-                    if ((int)id != j) {
-                        ejy = hmap_get(hk, hv, TG_LIGHT_LG, id);
-                        isT = ejy != 0xffffffffu;
-                        if (isT) eiy = __ldg(p.eid + bi + x);
-                    }
-                }
-                tsum_chunk(p, isT, w, eiy, ejy, Bm, Cm, Dm);
-                const unsigned tb = __ballot_sync(kFull, isT);
-                if (lane == 0) wk_t += (unsigned long long)__popc(tb);
-            }
-            __syncwarp();
-            if (lane == 0) wk_gamma += (unsigned long long)di;
-            unsigned long long *dst = p.tsum + (int64_t)q * 3 * L2;
-            for (int x = lane; x < 3 * L2; x += 32) dst[x] = Bm[x];
-            __syncwarp();
-        }
-    }
-    if (p.work && lane == 0) {
-        atomicAdd(p.work + 0, wk_gamma);
-        atomicAdd(p.work + 3, wk_t);
-    }
-}
-
-// Warp per edge: B, C, DT from k_cyc_edge<true>, then edge_finish.
-__global__ void __launch_bounds__(256) k_cyc_finish(EdgeParams p, int64_t count) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int L = p.L, L2 = L * L;
-    size_t off = 0;
-    unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);
-    if (p.hist_smem) off += ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
-    const size_t tbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
-    const size_t wbytes = tbytes + (size_t)XT_N * L2 * 8;
-    unsigned long long *Bm = reinterpret_cast<unsigned long long *>(smem + off + warp * wbytes);
-    long long *xt = reinterpret_cast<long long *>(smem + off + warp * wbytes + tbytes);
-    if (p.hist_smem) {
-        for (int64_t x = tid; x < p.hist_len; x += blockDim.x) shist[x] = 0;
-        __syncthreads();
-    }
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5; q < count; q += nw) {
-        const int64_t e = p.order[q];
-        const int2 ab = p.edges[e];
-        const int j = min(ab.x, ab.y), i = max(ab.x, ab.y);
-        const unsigned long long *src = p.tsum + q * 3 * L2;
-        for (int x = lane; x < 3 * L2; x += 32) Bm[x] = __ldg(src + x);
-        __syncwarp();
-        edge_finish(p, shist, e, i, j, p.ntype[i], p.ntype[j], p.toff + (int64_t)i * (L + 1),
-                    p.toff + (int64_t)j * (L + 1), p.tau + e * L, Bm, Bm + L2, Bm + 2 * L2, xt);
-        __syncwarp();
-    }
-    if (p.hist_smem) {
-        __syncthreads();
-        for (int64_t x = tid; x < p.hist_len; x += blockDim.x)
-            if (shist[x]) atomicAdd(p.hist + x, shist[x]);
-    }
-}
-
 int num_sms_c() {
     int dev = 0, sms = 0;
     (void)cudaGetDevice(&dev);
@@ -2587,140 +2069,7 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
     return TG_OK;
 }
 
-int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int64_t count,
-                 const tg_units &un, uint64_t *rows, int64_t width,
-                 unsigned long long *hist, const uint32_t *tau, const uint32_t *theta,
-                 const uint32_t *dsum, const unsigned long long *c4e,
-                 const unsigned long long *k4e, unsigned long long *work, const tg_tune &t,
-                 cudaStream_t s) {
-    if (un.nunits == 0 || count <= 0) return TG_OK;
-    const int L = g->L, L2 = L * L;
-    if (g->max_degree >= ((int64_t)1 << 27)) return TG_EOVERFLOW;  // 32-lane uint32 sums
-    EdgeParams p{};
-    p.rowptr = g->rowptr;
-    p.adj = g->adj;
-    p.eid = g->eid;
-    p.toff = g->toff;
-    p.ntype = g->ntype;
-    p.edges = g->edges;
-    p.order = order;
-    p.ustart = un.ustart.p;
-    p.tau = tau;
-    p.theta = theta;
-    p.dsum = dsum;
-    p.c4e = c4e;
-    p.k4e = k4e;
-    p.L = L;
-    p.P = L * (L + 1) / 2;
-    p.k = k;
-    p.level = level;
-    p.rows = rows;
-    p.width = width;
-    p.hist = hist;
-    p.hist_len = tg_global_len(L, k);
-    p.off1 = tg_binom(L + 1, 2);
-    p.off2 = p.off1 + tg_binom(L + 2, 3);
-    p.off4 = p.off1 + 2 * tg_binom(L + 2, 3);
-    p.n4 = tg_binom(L + 3, 4);
-    p.work = work;
-    const size_t avail = (size_t)smem_optin_c() - 1024;
-    const size_t hist_bytes = ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
-    const int hist_smem = (!rows && hist_bytes <= 48 * 1024) ? 1 : 0;
-    // per warp: B, C, DT; the kernels that finish edges add the term table
-    const size_t tbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
-    const size_t xbytes = tbytes + (size_t)XT_N * L2 * 8;
-    // B, C, DT through memory when they fit in a quarter of free memory
-    const size_t tsum_bytes = (size_t)count * 3 * L2 * 8;
-    size_t free_b = 0, total_b = 0;
-    TG_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const bool split = k == 4 && tsum_bytes <= free_b / 4;
-    int threads = t.cta_threads;
-    if (threads > (split ? kTsumThreads : kEdgeMaxThreads)) threads = split ? kTsumThreads : kEdgeMaxThreads;
-    if (threads < 32) threads = 32;
-    p.hist_smem = split ? 0 : hist_smem;
-    const size_t wbytes = split ? tbytes : xbytes;
-    size_t fixed = (p.hist_smem ? hist_bytes : 0) + (size_t)(threads / 32) * wbytes + 16;
-    while (fixed + 4096 > avail && threads > 32) {
-        threads -= 32;
-        fixed = (p.hist_smem ? hist_bytes : 0) + (size_t)(threads / 32) * wbytes + 16;
-    }
-    if (fixed + 16 > avail) return TG_EINVAL;
-    int64_t nbits = k == 4 ? g->n_nonisolated : 0;
-    if (t.bitmap_bits > 0 && nbits > t.bitmap_bits) nbits = t.bitmap_bits;
-    const int64_t maxb = (int64_t)((avail - fixed) / 16) * 128;
-    if (nbits > maxb) nbits = maxb;
-    if (nbits < 0) nbits = 0;
-    p.nbits = nbits;
-    const size_t smem = fixed + ((((size_t)((nbits + 31) >> 5)) * 4 + 15) & ~(size_t)15);
-    DevBuf<unsigned long long> queue, tsum;
-    if (!queue.alloc(1, s)) return TG_ENOMEM;
-    if (split && !tsum.alloc((size_t)count * 3 * L2, s)) return TG_ENOMEM;
-    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
-    p.queue = queue.p;
-    p.tsum = tsum.p;
-    // heavy units (all units when fused): one CTA each, Gamma_j bitmap
-    p.ulist = split ? un.heavy.p : nullptr;
-    p.nunits = split ? un.nheavy : un.nunits;
-    if (p.nunits > 0) {
-        const void *kfn = split ? (const void *)k_cyc_edge<true> : (const void *)k_cyc_edge<false>;
-        TG_TRY(tg_allow_max_smem(kfn));
-        int per_sm = 0;
-        TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem));
-        if (per_sm < 1) per_sm = 1;
-        int64_t grid = (int64_t)num_sms_c() * per_sm;
-        if (grid > p.nunits) grid = p.nunits;
-        if (t.grid_limit > 0 && grid > t.grid_limit) grid = t.grid_limit;
-        if (grid < 1) grid = 1;
-        DevBuf<uint32_t> emap;
-        if (!emap.alloc((size_t)std::max<int64_t>(1, grid * nbits), s)) return TG_ENOMEM;
-        p.emap = emap.p;
-        if (split)
-            k_cyc_edge<true><<<(unsigned)grid, threads, smem, s>>>(p);
-        else
-            k_cyc_edge<false><<<(unsigned)grid, threads, smem, s>>>(p);
-        tg_note_launch();
-        TG_TRY_CUDA(cudaGetLastError());
-    }
-    if (!split) return TG_OK;
-    // light units: one warp each, Gamma_j in a per-warp hash map
-    if (un.nlight > 0) {
-        DevBuf<unsigned long long> lq;
-        if (!lq.alloc(1, s)) return TG_ENOMEM;
-        TG_TRY_CUDA(cudaMemsetAsync(lq.p, 0, 8, s));
-        EdgeParams lp = p;
-        lp.queue = lq.p;
-        lp.ulist = un.light.p;
-        lp.nunits = un.nlight;
-        const size_t lw = (((size_t)3 * L2 * 8 + 15) & ~(size_t)15) + (size_t)2 * 4 * (1 << TG_LIGHT_LG);
-        const size_t lsmem = (size_t)kTsumLightWarps * lw;
-        TG_TRY(tg_allow_max_smem((const void *)k_cyc_tsum_light));
-        int lper = 0;
-        TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lper, k_cyc_tsum_light,
-                                                                  kTsumLightWarps * 32, lsmem));
-        if (lper < 1) lper = 1;
-        int64_t lgrid = (int64_t)num_sms_c() * lper;
-        const int64_t need = ((int64_t)un.nlight + kTsumLightWarps - 1) / kTsumLightWarps;
-        if (lgrid > need) lgrid = need;
-        if (t.grid_limit > 0 && lgrid > t.grid_limit) lgrid = t.grid_limit;
-        k_cyc_tsum_light<<<(unsigned)lgrid, kTsumLightWarps * 32, lsmem, s>>>(lp); tg_note_launch();
-        TG_TRY_CUDA(cudaGetLastError());
-    }
-    // finishing pass: warp per edge
-    p.hist_smem = hist_smem;
-    const size_t fsmem = (hist_smem ? hist_bytes : 0) + (256 / 32) * xbytes;
-    TG_TRY(tg_allow_max_smem((const void *)k_cyc_finish));
-    int fper = 0;
-    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, k_cyc_finish, 256, fsmem));
-    if (fper < 1) fper = 1;
-    int64_t fgrid = (int64_t)num_sms_c() * fper;
-    if (fgrid > (count + 7) / 8) fgrid = (count + 7) / 8;
-    if (t.grid_limit > 0 && fgrid > t.grid_limit) fgrid = t.grid_limit;
-    if (fgrid < 1) fgrid = 1;
-    k_cyc_finish<<<(unsigned)fgrid, 256, fsmem, s>>>(p, count); tg_note_launch();
-    TG_TRY_CUDA(cudaGetLastError());
-    return TG_OK;
-}
-
+// ---------------------------------------------- global shortcut ----
 int tg_cyc_correct(unsigned long long *hist, int L, const unsigned long long *c4w,
                    const unsigned long long *k4, cudaStream_t s) {
     const int64_t n4 = tg_binom(L + 3, 4);
