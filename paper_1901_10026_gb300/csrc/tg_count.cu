@@ -940,10 +940,6 @@ static int get_sched(const tg_graph *g, cudaStream_t s, tg_sched **out) {
         return TG_OK;
     }
     DevBuf<uint32_t> order;
-    DevBuf<unsigned long long> sv;
-    if (!sv.alloc(g->n, s)) return TG_ENOMEM;
-    k_neighbor_degree_sum<<<grid_for(g->n * 32), 256, 0, s>>>(g->rowptr, g->adj, g->n, sv.p); tg_note_launch();
-    TG_TRY_CUDA(cudaGetLastError());
     TG_TRY(grouped_order(g, 0, g->M, s, order));
     TG_TRY_CUDA(cudaStreamSynchronize(s));
     tg_sched *sc = new (std::nothrow) tg_sched();
@@ -951,9 +947,22 @@ static int get_sched(const tg_graph *g, cudaStream_t s, tg_sched **out) {
     sc->M = g->M;
     sc->n = g->n;
     sc->order = order.release();
-    sc->s = sv.release();
     g->sched = sc;
     *out = sc;
+    return TG_OK;
+}
+
+// The neighbour-degree sums of the schedule, made on first use (only the
+// work model reads them).
+static int sched_sums(const tg_graph *g, tg_sched *sc, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g->mu);
+    if (sc->s) return TG_OK;
+    DevBuf<unsigned long long> sv;
+    if (!sv.alloc(g->n, s)) return TG_ENOMEM;
+    k_neighbor_degree_sum<<<grid_for(g->n * 32), 256, 0, s>>>(g->rowptr, g->adj, g->n, sv.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    sc->s = sv.release();
     return TG_OK;
 }
 
@@ -1199,6 +1208,7 @@ extern "C" int tg_work_model(const tg_graph *g, uint64_t *entries, void *stream)
     if (g->M == 0) return TG_OK;
     tg_sched *sc = nullptr;
     TG_TRY(get_sched(g, s, &sc));
+    TG_TRY(sched_sums(g, sc, s));
     DevBuf<unsigned long long> tot;
     if (!tot.alloc(1, s)) return TG_ENOMEM;
     TG_TRY_CUDA(cudaMemsetAsync(tot.p, 0, 8, s));

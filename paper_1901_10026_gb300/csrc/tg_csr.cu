@@ -62,13 +62,19 @@ __global__ void k_compact_edges(const uint64_t *key, const uint32_t *flag, const
                                 int64_t m, int64_t n, int32_t *lo, int32_t *hi, int32_t *deg) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
-        if (!flag[e]) continue;
-        uint64_t k = key[e];
+        const bool keep = flag[e] != 0;
+        uint64_t k = keep ? key[e] : 0ull;
         int32_t a = (int32_t)(k / (uint64_t)n), b = (int32_t)(k % (uint64_t)n);
-        lo[pos[e]] = a;
-        hi[pos[e]] = b;
-        atomicAdd(&deg[a], 1);
-        atomicAdd(&deg[b], 1);
+        if (keep) {
+            lo[pos[e]] = a;
+            hi[pos[e]] = b;
+            atomicAdd(&deg[b], 1);
+        }
+        // the keys are sorted, so the lanes holding one lower end a are
+        // adjacent: one add of their number per a (a hub's edges no longer
+        // queue on one counter)
+        const unsigned peers = __match_any_sync(__activemask(), keep ? a : -1);
+        if (keep && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&deg[a], __popc(peers));
     }
 }
 

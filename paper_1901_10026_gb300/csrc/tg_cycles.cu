@@ -622,6 +622,71 @@ __device__ __forceinline__ void c4_warp_walk(const C4Params &p, uint32_t a, int6
     }
 }
 
+// One chunk of 32 members for k_c4_walk: as c4_chunk, with kWalkUnroll
+// batches of 32 positions in flight per step (their list loads, then their
+// counter adds, then the bitmap marks), so each lane keeps several returning
+// adds outstanding.
+constexpr int kWalkUnroll = 4;
+
+template <class IT>
+__device__ __forceinline__ int64_t c4_chunk_count(const C4Params &p, uint32_t a, int64_t len64,
+                                                  int64_t bu, int tu, int64_t at, int64_t f_lo,
+                                                  int64_t f_hi, uint32_t *cnt, uint32_t *bits,
+                                                  unsigned long long &wk) {
+    const int lane = threadIdx.x & 31;
+    const int L = p.L;
+    const IT len = (IT)len64;
+    IT incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const IT y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const IT total = __shfl_sync(kFull, incl, 31);
+    const IT lo = (IT)(f_lo > at ? (f_lo - at < (int64_t)total ? f_lo - at : (int64_t)total) : 0);
+    const IT hi = (IT)(f_hi - at < (int64_t)total ? f_hi - at : (int64_t)total);
+    for (IT b0 = lo; b0 < hi; b0 += 32 * kWalkUnroll) {
+        uint32_t bv[kWalkUnroll];
+        uint32_t *ca[kWalkUnroll];
+        bool ok[kWalkUnroll];
+#pragma unroll
+        for (int q = 0; q < kWalkUnroll; ++q) {
+            const IT pos = b0 + 32 * q + lane;
+            int r = 0;  // the first member whose running sum exceeds pos
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const IT v = __shfl_sync(kFull, incl, r + st - 1);
+                if (v <= pos) r += st;
+            }
+            const int64_t bur = __shfl_sync(kFull, bu, r);
+            const IT str = __shfl_sync(kFull, incl - len, r);
+            const int tur = __shfl_sync(kFull, tu, r);
+            ok[q] = false;
+            bv[q] = 0;
+            ca[q] = cnt;
+            if (pos < hi) {
+                const uint32_t b = __ldg(p.adj + bur + (int64_t)(pos - str)) & TG_IDMASK;
+                if (b > a) {
+                    ok[q] = true;
+                    bv[q] = b;
+                    ca[q] = cnt + (int64_t)b * L + tur;
+                }
+            }
+        }
+        uint32_t old[kWalkUnroll];
+#pragma unroll
+        for (int q = 0; q < kWalkUnroll; ++q) old[q] = ok[q] ? atomicAdd(ca[q], 1u) : 1u;
+#pragma unroll
+        for (int q = 0; q < kWalkUnroll; ++q) {
+            if (!ok[q]) continue;
+            ++wk;
+            // the first middle of a type at b marks b
+            if (!old[q]) atomicOr(bits + (bv[q] >> 5), 1u << (bv[q] & 31u));
+        }
+    }
+    return (int64_t)total;
+}
+
 // Pass 0 of a wave of costly anchors (global mode): one warp per unit, adding
 // to the counters of its anchor's slot and marking a far end in the slot's
 // bitmap when a count of it leaves zero; k_c4_pairs then takes the marked ends.
@@ -642,12 +707,28 @@ __global__ void __launch_bounds__(kC4WalkWarps * 32) k_c4_walk(C4Params p) {
         const int da = (int)(p.rowptr[a + 1] - ba);
         uint32_t *cnt = p.scratch + (un.q - p.q0) * p.slot_words;
         uint32_t *bits = cnt + p.n * (L + 1);
-        const int64_t at = p.mprefix[p.pbase[un.q] + un.m];
-        c4_warp_walk(p, a, ba, da, un.m, at, un.lo, un.hi, 32, [&](uint32_t b, int tu) {
-            // the first middle of a type at b marks b
-            if (!atomicAdd(cnt + (int64_t)b * L + tu, 1u)) atomicOr(bits + (b >> 5), 1u << (b & 31u));
-            ++wk;
-        });
+        int64_t at = p.mprefix[p.pbase[un.q] + un.m];
+        for (int m = un.m; m < da && at < un.hi; m += 32) {
+            const int x = m + lane;
+            int64_t len = 0, bu = 0;
+            int tu = 0;
+            if (x < da) {
+                const uint32_t wu = __ldg(p.adj + ba + x);
+                const uint32_t u = wu & TG_IDMASK;
+                if (u > a) {
+                    bu = p.rowptr[u];
+                    const int64_t du = p.rowptr[u + 1] - bu;
+                    if (du > 1) {
+                        len = du;
+                        tu = (int)(wu >> TG_TSHIFT);
+                    }
+                }
+            }
+            if (__all_sync(kFull, len < ((int64_t)1 << 26)))
+                at += c4_chunk_count<int>(p, a, len, bu, tu, at, un.lo, un.hi, cnt, bits, wk);
+            else
+                at += c4_chunk_count<int64_t>(p, a, len, bu, tu, at, un.lo, un.hi, cnt, bits, wk);
+        }
     }
     if (p.work) {
 #pragma unroll
