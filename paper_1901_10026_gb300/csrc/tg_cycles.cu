@@ -1581,8 +1581,11 @@ __global__ void __launch_bounds__(256) k_k4_bits_cta(K4GParams p, const uint32_t
                 const volatile uint32_t *bq = bm + q * words;
                 const int tw = (int)ty[q];
                 for (int t = 0; t < L; ++t) {
+                    // only the words of type t's position range
+                    const int s0 = __ldg(to0 + t), s1 = __ldg(to0 + t + 1);
                     int c = 0;
-                    for (int k = 0; k < words; ++k) c += __popc(bv[k] & bq[k] & tm[t * 32 + k]);
+                    for (int k = s0 >> 5; k < ((s1 + 31) >> 5); ++k)
+                        c += __popc(bv[k] & bq[k] & tm[t * 32 + k]);
                     if (c) k4_hist_add(h4, t0, tv, tw, t, (unsigned long long)c);
                     wk += (unsigned long long)c;
                 }
