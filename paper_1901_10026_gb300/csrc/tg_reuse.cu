@@ -122,6 +122,15 @@ __global__ void k_unit_lists(const uint32_t *flag, const uint32_t *pos, uint32_t
 // One CTA per unit (edges sharing j); Gamma_j is a shared-memory bitmap that
 // stays set while the CTA's units keep the same j; one warp per edge counts
 // Gamma_i \ {j} against it by type.
+// Bits [lo, hi) of a 32-bit word, the range clamped to the word.
+__device__ __forceinline__ uint32_t word_bits(int lo, int hi) {
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > 32 ? 32 : hi;
+    if (lo >= hi) return 0u;
+    const uint32_t up = hi == 32 ? 0xffffffffu : ((1u << hi) - 1u);
+    return up & ~((1u << lo) - 1u);
+}
+
 __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32_t *adj,
                                              const int32_t *toff, const int2 *edges,
                                              const uint32_t *order, const uint32_t *ustart,
@@ -172,22 +181,22 @@ __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32
             const int i = max(ab.x, ab.y);
             const int64_t bi = rowptr[i];
             const int di = (int)(rowptr[i + 1] - bi);
-            unsigned mine = 0;  // lane t keeps the count of type t
+            // lane t < L keeps the count of type t: Gamma_i is sorted by type, so
+            // the hits of type t are the ballot's bits in t's position range
+            const int32_t *toi = toff + (int64_t)i * (L + 1);
+            const int ts0 = lane < L ? __ldg(toi + lane) : 0, ts1 = lane < L ? __ldg(toi + lane + 1) : 0;
+            unsigned mine = 0;
             for (int c0 = 0; c0 < di; c0 += 32) {
                 const int x = c0 + lane;
                 bool hit = false;
-                int t = 0;
                 if (x < di) {
                     const uint32_t w = __ldg(adj + bi + x);
                     const uint32_t id = w & TG_IDMASK;
-                    t = (int)(w >> TG_TSHIFT);
                     if ((int)id != j)
                         hit = (int64_t)id < nbits ? bm_test(bm, id) : contains(adj, bj, toj, w);
                 }
-                for (int q = 0; q < L; ++q) {
-                    const unsigned c = __popc(__ballot_sync(kFull, hit && t == q));
-                    if (lane == q) mine += c;
-                }
+                const unsigned hm = __ballot_sync(kFull, hit);
+                if (lane < L) mine += __popc(hm & word_bits(ts0 - c0, ts1 - c0));
             }
             if (lane < L) tau[(int64_t)e * L + lane] = mine;
         }
@@ -199,7 +208,8 @@ __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32
 constexpr int kLightWarps = 8;
 
 __global__ void __launch_bounds__(kLightWarps * 32) k_tau_light(
-    const int64_t *rowptr, const uint32_t *adj, const int2 *edges, const uint32_t *order,
+    const int64_t *rowptr, const uint32_t *adj, const int32_t *toff, const int2 *edges,
+    const uint32_t *order,
     const uint32_t *ustart, const uint32_t *ulist, uint32_t nlist, int32_t L,
     unsigned long long *queue, uint32_t *tau) {
     __shared__ uint32_t keys[kLightWarps][1 << TG_LIGHT_LG];
@@ -226,21 +236,19 @@ __global__ void __launch_bounds__(kLightWarps * 32) k_tau_light(
             const int i = max(ab.x, ab.y);
             const int64_t bi = rowptr[i];
             const int di = (int)(rowptr[i + 1] - bi);
-            unsigned mine = 0;  // lane t keeps the count of type t
+            // lane t < L keeps the count of type t (hits in t's position range)
+            const int32_t *toi = toff + (int64_t)i * (L + 1);
+            const int ts0 = lane < L ? __ldg(toi + lane) : 0, ts1 = lane < L ? __ldg(toi + lane + 1) : 0;
+            unsigned mine = 0;
             for (int c0 = 0; c0 < di; c0 += 32) {
                 const int x = c0 + lane;
                 bool hit = false;
-                int t = 0;
                 if (x < di) {
-                    const uint32_t w = __ldg(adj + bi + x);
-                    const uint32_t id = w & TG_IDMASK;
-                    t = (int)(w >> TG_TSHIFT);
+                    const uint32_t id = __ldg(adj + bi + x) & TG_IDMASK;
                     hit = (int)id != j && hset_has(hk, TG_LIGHT_LG, id);
                 }
-                for (int q = 0; q < L; ++q) {
-                    const unsigned c = __popc(__ballot_sync(kFull, hit && t == q));
-                    if (lane == q) mine += c;
-                }
+                const unsigned hm = __ballot_sync(kFull, hit);
+                if (lane < L) mine += __popc(hm & word_bits(ts0 - c0, ts1 - c0));
             }
             if (lane < L) tau[(int64_t)e * L + lane] = mine;
         }
@@ -1010,8 +1018,8 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
             const int64_t need = ((int64_t)un.nlight + kLightWarps - 1) / kLightWarps;
             if (grid > need) grid = need;
             k_tau_light<<<(unsigned)grid, kLightWarps * 32, 0, s>>>(
-                g->rowptr, g->adj, g->edges, ord, un.ustart.p, un.light.p, un.nlight, L, q.p + 1,
-                tau.p); tg_note_launch();
+                g->rowptr, g->adj, g->toff, g->edges, ord, un.ustart.p, un.light.p, un.nlight, L,
+                q.p + 1, tau.p); tg_note_launch();
             TG_TRY_CUDA(cudaGetLastError());
         }
     }
