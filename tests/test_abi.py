@@ -112,3 +112,12 @@ def test_strerror(lib):
     assert tg.tg_strerror(0) == "ok"
     assert tg.tg_strerror(tg.TG_EINVAL) == "invalid argument"
     assert tg.tg_version() >= 100
+
+
+def test_memory_retention_setting_without_device_work(lib):
+    """The retention setting is host state until a pool is made on first
+    allocation; setting, trimming and resetting it needs no GPU."""
+    tg.tg_set_memory_retention(1 << 30)
+    tg.tg_trim_memory()
+    tg.tg_set_memory_retention(0)
+    tg.tg_trim_memory()
