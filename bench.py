@@ -60,6 +60,8 @@ def parse():
                     help="graph: one graph per step (default); batch: the 10,000-graph batched "
                          "workload; serve: the Poisson request stream")
     ap.add_argument("--batch-graphs", type=int, default=10000)
+    ap.add_argument("--kernel", choices=["cycles", "reuse", "cta", "warp"], default="cycles",
+                    help="counting kernel of the graph mode (tg_set_tune): cycles is the default path")
     ap.add_argument("--retain-gib", type=int, default=64,
                     help="tg_set_memory_retention for the graph mode, GiB (0: the default pool)")
     ap.add_argument("--serve-requests", type=int, default=200)
@@ -393,6 +395,9 @@ def main():
     glen = tg.tg_global_len(L, k)
     # a counting loop keeps its scratch mapped between steps (library setting)
     tg.tg_set_memory_retention(args.retain_gib << 30)
+    if args.kernel != "cycles":
+        tg.tg_set_tune(kernel={"reuse": tg.TG_KERNEL_REUSE, "cta": tg.TG_KERNEL_CTA_BITMAP,
+                               "warp": tg.TG_KERNEL_WARP_SEARCH}[args.kernel])
 
     # shard ranges from the canonical edge list of the built graph (untimed)
     g0 = tg.tg_build_csr(G.n, src_d, dst_d, typ_d, L)
@@ -526,6 +531,7 @@ def main():
             "config": {"workload": WORKLOADS[args.workload], "n": G.n, "M": M, "m_input": G.m, "L": L, "k": k,
                        "step": "tg_build_csr + tg_count_global from device-resident inputs",
                        "memory_retention_bytes": args.retain_gib << 30,
+                       "kernel": args.kernel,
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"edge ranges x{world}" if world > 1 else "single GPU"},
             "clocks": clocks,
