@@ -306,6 +306,8 @@ def run_serve(args):
     import paper_1901_10026_gb300 as tg
     from paper_1901_10026_gb300 import synth
 
+    # a serving process keeps its scratch mapped between requests (library setting)
+    tg.tg_set_memory_retention(args.retain_gib << 30)
     reqs = synth.serve_stream(args.serve_requests, rate=1.0)
     t0 = time.perf_counter()
     Gs = [synth.serve_graph(e, key) for _, e, key in reqs]
@@ -355,7 +357,8 @@ def run_serve(args):
                                "edges log-uniform [1e3, 2e6], L=6 uniform, global k=4",
                    "requests": len(Gs), "edges": int(sum(G.m for G in Gs)),
                    "arrival_rate_per_s": rate, "load": args.serve_load,
-                   "solo_capacity_graphs_per_s": capacity},
+                   "solo_capacity_graphs_per_s": capacity,
+                   "memory_retention_bytes": args.retain_gib << 30},
         "served": {k: serv_st[k] for k in ("p50_ms", "p99_ms", "graphs_per_s", "peak_in_flight",
                                             "batched_launches", "grouped_requests")},
         "one_at_a_time": {k: base_st[k] for k in ("p50_ms", "p99_ms", "graphs_per_s", "peak_in_flight")},
