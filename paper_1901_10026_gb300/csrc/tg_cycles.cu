@@ -102,6 +102,11 @@ struct C4Params {
     const int64_t *mprefix;
     const int64_t *pbase;
     int64_t q0;
+    // slot layout: 32-bit counts at b L + t (half = 0) or 16-bit counts at
+    // b Lp + t, Lp = L rounded up to even, two to a word (half = 1); the
+    // far-end bitmap starts at word bits_off of the slot
+    int32_t half;
+    int64_t bits_off;
 };
 
 // A warp unit of k_c4_walk: positions [lo, hi) of the walk of split anchor
@@ -300,6 +305,23 @@ __device__ __forceinline__ void c4_one(const C4Params &p, unsigned long long *h4
         if (c[t]) cb[t] = 0u;
 }
 
+// c4_one for a 16-bit slot: b's counts are the halves of its (L + 1) / 2
+// words at cw (low half the even type), words no other far end shares.
+__device__ __forceinline__ void c4_one16(const C4Params &p, unsigned long long *h4, int ta,
+                                         uint32_t *cw, uint32_t b) {
+    const int L = p.L, nw = (L + 1) >> 1;
+    uint32_t c[TG_MAX_TYPES];
+    uint32_t sum = 0;
+    for (int q = 0; q < nw; ++q) {
+        const uint32_t w = __ldcg(cw + q);
+        c[2 * q] = w & 0xffffu;
+        if (2 * q + 1 < L) c[2 * q + 1] = w >> 16;
+        sum += (w & 0xffffu) + (w >> 16);
+        if (w) cw[q] = 0u;
+    }
+    if (p.g4 && sum > 1) c4_add(h4, L, ta, p.ntype[b], c);  // one middle closes no cycle
+}
+
 // Position of the j-th (from 0) set bit of m; m has more than j set bits.
 __device__ __forceinline__ int select_bit(uint32_t m, int j) {
     int pos = 0;
@@ -424,7 +446,7 @@ __global__ void __launch_bounds__(kC4Threads) k_c4_pairs(C4Params p, const uint3
     for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
         const int64_t slot = c / cps, wc = c - slot * cps;
         uint32_t *cnt = p.scratch + slot * p.slot_words;
-        uint32_t *bw = cnt + p.n * (L + 1);
+        uint32_t *bw = cnt + p.bits_off;
         const int64_t wi = wc * 32 + lane;
         uint32_t m = 0;
         if (wi < words) {
@@ -453,7 +475,10 @@ __global__ void __launch_bounds__(kC4Threads) k_c4_pairs(C4Params p, const uint3
             const int er = __shfl_sync(kFull, incl - k, r);
             if (kk < tot) {
                 const uint32_t b = (uint32_t)((wc * 32 + r) * 32 + select_bit(mr, kk - er));
-                c4_one(p, h4, ta, cnt + (int64_t)b * L, b);
+                if (p.half)
+                    c4_one16(p, h4, ta, cnt + (int64_t)b * ((L + 1) >> 1), b);
+                else
+                    c4_one(p, h4, ta, cnt + (int64_t)b * L, b);
             }
         }
     }
@@ -645,9 +670,11 @@ __device__ __forceinline__ int64_t c4_chunk_count(const C4Params &p, uint32_t a,
     const IT total = __shfl_sync(kFull, incl, 31);
     const IT lo = (IT)(f_lo > at ? (f_lo - at < (int64_t)total ? f_lo - at : (int64_t)total) : 0);
     const IT hi = (IT)(f_hi - at < (int64_t)total ? f_hi - at : (int64_t)total);
+    const int Lp = L + (L & 1);
     for (IT b0 = lo; b0 < hi; b0 += 32 * kWalkUnroll) {
         uint32_t bv[kWalkUnroll];
         uint32_t *ca[kWalkUnroll];
+        int sh[kWalkUnroll];
         bool ok[kWalkUnroll];
 #pragma unroll
         for (int q = 0; q < kWalkUnroll; ++q) {
@@ -664,24 +691,32 @@ __device__ __forceinline__ int64_t c4_chunk_count(const C4Params &p, uint32_t a,
             ok[q] = false;
             bv[q] = 0;
             ca[q] = cnt;
+            sh[q] = 0;
             if (pos < hi) {
                 const uint32_t b = __ldg(p.adj + bur + (int64_t)(pos - str)) & TG_IDMASK;
                 if (b > a) {
                     ok[q] = true;
                     bv[q] = b;
-                    ca[q] = cnt + (int64_t)b * L + tur;
+                    if (p.half) {
+                        const int64_t k = (int64_t)b * Lp + tur;
+                        ca[q] = cnt + (k >> 1);
+                        sh[q] = (int)(k & 1) * 16;
+                    } else {
+                        ca[q] = cnt + (int64_t)b * L + tur;
+                    }
                 }
             }
         }
         uint32_t old[kWalkUnroll];
 #pragma unroll
-        for (int q = 0; q < kWalkUnroll; ++q) old[q] = ok[q] ? atomicAdd(ca[q], 1u) : 1u;
+        for (int q = 0; q < kWalkUnroll; ++q) old[q] = ok[q] ? atomicAdd(ca[q], 1u << sh[q]) : 0xffffffffu;
 #pragma unroll
         for (int q = 0; q < kWalkUnroll; ++q) {
             if (!ok[q]) continue;
             ++wk;
             // the first middle of a type at b marks b
-            if (!old[q]) atomicOr(bits + (bv[q] >> 5), 1u << (bv[q] & 31u));
+            if (!((old[q] >> sh[q]) & (p.half ? 0xffffu : 0xffffffffu)))
+                atomicOr(bits + (bv[q] >> 5), 1u << (bv[q] & 31u));
         }
     }
     return (int64_t)total;
@@ -706,7 +741,7 @@ __global__ void __launch_bounds__(kC4WalkWarps * 32) k_c4_walk(C4Params p) {
         const int64_t ba = p.rowptr[a];
         const int da = (int)(p.rowptr[a + 1] - ba);
         uint32_t *cnt = p.scratch + (un.q - p.q0) * p.slot_words;
-        uint32_t *bits = cnt + p.n * (L + 1);
+        uint32_t *bits = cnt + p.bits_off;
         int64_t at = p.mprefix[p.pbase[un.q] + un.m];
         for (int m = un.m; m < da && at < un.hi; m += 32) {
             const int x = m + lane;
@@ -1707,10 +1742,24 @@ int c4_walk_waves(const C4Params &p, const tg_graph *g, const uint32_t *list, in
     if (wper < 1) wper = 1;
     const int64_t walk_grid = (int64_t)num_sms_c() * wper;
     const int64_t warps = walk_grid * kC4WalkWarps;
-    const int64_t nwaves = (nheavy + K - 1) / K;
+    // waves: runs of at most K consecutive anchors of one counter width; an
+    // anchor with fewer than 2^16 neighbours counts in 16-bit halves (no
+    // count can reach 2^16), the others in 32-bit words
+    std::vector<int64_t> wq0, wq1;
+    std::vector<int> whalf;
+    for (int64_t q = 0; q < nheavy;) {
+        const int half = hdeg[q] < 65536 ? 1 : 0;
+        int64_t e = q + 1;
+        while (e < nheavy && e - q < K && (hdeg[e] < 65536 ? 1 : 0) == half) ++e;
+        wq0.push_back(q);
+        wq1.push_back(e);
+        whalf.push_back(half);
+        q = e;
+    }
+    const int64_t nwaves = (int64_t)wq0.size();
     std::vector<int64_t> us((size_t)nheavy + 1, 0), tg((size_t)nheavy, 1);
     for (int64_t w = 0; w < nwaves; ++w) {
-        const int64_t q0 = w * K, q1 = std::min(nheavy, q0 + K);
+        const int64_t q0 = wq0[w], q1 = wq1[w];
         unsigned long long wt = 0;
         for (int64_t q = q0; q < q1; ++q) wt += tot_h[q];
         const int64_t tgt =
@@ -1741,9 +1790,12 @@ int c4_walk_waves(const C4Params &p, const tg_graph *g, const uint32_t *list, in
     pd.heavy = list;
     pd.mprefix = dmp.p;
     pd.pbase = dpb.p;
+    const int L = p.L;
     for (int64_t w = 0; w < nwaves; ++w) {
-        const int64_t q0 = w * K, q1 = std::min(nheavy, q0 + K);
+        const int64_t q0 = wq0[w], q1 = wq1[w];
         pd.q0 = q0;
+        pd.half = whalf[w];
+        pd.bits_off = whalf[w] ? p.n * ((L + 1) >> 1) : p.n * (L + 1);
         pd.wunits = dun.p + us[q0];
         pd.n_units = us[q1] - us[q0];
         pd.queue = dq.p + w;
@@ -1899,6 +1951,8 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     p.n4 = n4;
     p.work = work;
     p.mark = 1;
+    p.half = 0;
+    p.bits_off = n * (L + 1);
 
     if (nheavy > 0 && walk_waves) {
         // global mode: each split anchor's walk is cut into position ranges of
