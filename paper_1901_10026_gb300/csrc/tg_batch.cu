@@ -337,12 +337,6 @@ __global__ void k_batch_keys(const BatchGraph *gs, const int64_t *eoff, int32_t 
     }
 }
 
-int num_sms_b() {
-    int dev = 0, sms = 0;
-    (void)cudaGetDevice(&dev);
-    (void)cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms > 0 ? sms : 1;
-}
 
 }  // namespace
 
@@ -389,7 +383,7 @@ static int batch_config(tg_batch *b, int64_t *grid, size_t *smem) {
     int per_sm = 0;
     TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_warp, threads, *smem));
     if (per_sm < 1) per_sm = 1;
-    int64_t gr = (int64_t)num_sms_b() * per_sm;
+    int64_t gr = (int64_t)tg_num_sms() * per_sm;
     const int64_t need = (b->count + b->warps - 1) / b->warps;
     if (gr > need) gr = need;
     *grid = gr < 1 ? 1 : gr;

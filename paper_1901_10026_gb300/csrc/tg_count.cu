@@ -967,12 +967,6 @@ static int sched_sums(const tg_graph *g, tg_sched *sc, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ launches ----
-static int num_sms() {
-    int dev = 0, sms = 0;
-    (void)cudaGetDevice(&dev);
-    (void)cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms > 0 ? sms : 1;
-}
 
 static int max_smem_optin() {
     int dev = 0, v = 0;
@@ -1022,7 +1016,7 @@ static int launch_warp(const CountParams &p, cudaStream_t s) {
     int per_sm = 0;
     TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_warp, kBlock, smem));
     if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)num_sms() * per_sm;
+    int64_t grid = (int64_t)tg_num_sms() * per_sm;
     const int64_t need = (p.count + kWarps - 1) / kWarps;
     if (grid > need) grid = need;
     const int gl = tune_now().grid_limit;
@@ -1067,7 +1061,7 @@ static int launch_cta_u(const CountParams &p, const CtaParams &cp, int threads, 
     TG_TRY_CUDA(
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_cta<U>, threads, smem));
     if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)num_sms() * per_sm;
+    int64_t grid = (int64_t)tg_num_sms() * per_sm;
     if (grid > p.count) grid = p.count;
     const int gl = tune_now().grid_limit;
     if (gl > 0 && grid > gl) grid = gl;

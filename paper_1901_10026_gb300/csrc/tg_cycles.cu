@@ -1673,19 +1673,7 @@ __global__ void k_cyc_correct(unsigned long long *hist, int64_t off4, int64_t n4
     }
 }
 
-int num_sms_c() {
-    int dev = 0, sms = 0;
-    (void)cudaGetDevice(&dev);
-    (void)cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms > 0 ? sms : 1;
-}
 
-int smem_optin_c() {
-    int dev = 0, v = 0;
-    (void)cudaGetDevice(&dev);
-    (void)cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return v > 0 ? v : 48 * 1024;
-}
 
 // Launch shape of k_c4_pairs: per-warp histogram copies when they fit in 64 KB.
 struct PairsConf {
@@ -1700,7 +1688,7 @@ int c4_pairs_conf(int64_t n4, PairsConf &c) {
     TG_TRY(tg_allow_max_smem((const void *)k_c4_pairs));
     int per = 0;
     TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_c4_pairs, kC4Threads, c.smem));
-    c.grid = (int64_t)num_sms_c() * (per > 0 ? per : 1);
+    c.grid = (int64_t)tg_num_sms() * (per > 0 ? per : 1);
     return TG_OK;
 }
 
@@ -1740,7 +1728,7 @@ int c4_walk_waves(const C4Params &p, const tg_graph *g, const uint32_t *list, in
     int wper = 0;
     TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_c4_walk, kC4WalkWarps * 32, 0));
     if (wper < 1) wper = 1;
-    const int64_t walk_grid = (int64_t)num_sms_c() * wper;
+    const int64_t walk_grid = (int64_t)tg_num_sms() * wper;
     const int64_t warps = walk_grid * kC4WalkWarps;
     // waves: runs of at most K consecutive anchors of one counter width; an
     // anchor with fewer than 2^16 neighbours counts in 16-bit halves (no
@@ -1822,7 +1810,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     const int64_t n = g->n;
     const bool global = g4 != nullptr;
     const int64_t n4 = tg_binom(L + 3, 4);
-    const size_t avail = (size_t)smem_optin_c() - 1024;
+    const size_t avail = (size_t)tg_smem_optin() - 1024;
     // staged members per tile: their lists, ids and (a, u) accumulators
     const size_t per_member = 8 + 8 + 4 + 4 + (global ? 0 : (size_t)L2 * 8);
     const size_t fixed = 34 * 8 + 16 + 8 + (global ? (size_t)n4 * 8 : 0);
@@ -1837,7 +1825,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     int per_sm = 0;
     TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_c4, kC4Threads, smem));
     if (per_sm < 1) per_sm = 1;
-    const int64_t full_grid = (int64_t)num_sms_c() * per_sm;
+    const int64_t full_grid = (int64_t)tg_num_sms() * per_sm;
 
     // anchor costs and classes
     DevBuf<unsigned long long> cost, total;
@@ -1861,10 +1849,10 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     if (global) {
         lg_w = kC4WarpLgMax;
         while (lg_w > 5 && ((1 << lg_w) > t.hash_slots ||
-                            c4_warp_smem(n4, L, lg_w) > (size_t)smem_optin_c() - 1024))
+                            c4_warp_smem(n4, L, lg_w) > (size_t)tg_smem_optin() - 1024))
             --lg_w;
         lg_c = kC4CtaLgMax;
-        while (lg_c > lg_w && c4_cta_smem(n4, L, lg_c) > (size_t)smem_optin_c() - 1024) --lg_c;
+        while (lg_c > lg_w && c4_cta_smem(n4, L, lg_c) > (size_t)tg_smem_optin() - 1024) --lg_c;
     }
     const unsigned long long lite = global ? (1ull << lg_w) / 2 : 0ull;
     const unsigned long long mid = global ? (1ull << lg_c) / 2 : 0ull;
@@ -2011,7 +1999,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
         TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_c4_warp,
                                                                   kC4WarpWarps * 32, wsmem));
         if (wper < 1) wper = 1;
-        int64_t wg = (int64_t)num_sms_c() * wper;
+        int64_t wg = (int64_t)tg_num_sms() * wper;
         wg = std::min<int64_t>(wg, (ncls[kClsWarp] + 32 * kC4WarpWarps - 1) / (32 * kC4WarpWarps));
         C4Params pw = p;
         pw.queue = queue.p + kClsWarp;
@@ -2026,7 +2014,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
         TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cper, k_c4_cta, kC4CtaThreads,
                                                                   csmem));
         if (cper < 1) cper = 1;
-        const int64_t cg = std::min<int64_t>((int64_t)num_sms_c() * cper, ncls[kClsCta]);
+        const int64_t cg = std::min<int64_t>((int64_t)tg_num_sms() * cper, ncls[kClsCta]);
         C4Params pc = p;
         pc.queue = queue.p + kClsCta;
         k_c4_cta<<<(unsigned)cg, kC4CtaThreads, csmem, s>>>(pc, lists[kClsCta].p, ncls[kClsCta],
@@ -2052,7 +2040,7 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
     const bool global = g4 != nullptr;
     const int64_t n4 = tg_binom(L + 3, 4);
     const size_t hbytes = global ? (size_t)n4 * 8 : 0;
-    const size_t avail = (size_t)smem_optin_c() - 1024 - hbytes;
+    const size_t avail = (size_t)tg_smem_optin() - 1024 - hbytes;
     const size_t per_entry = (size_t)(3 + L) * 4;
     // W entries staged per warp; hash_slots caps it (a small cap sends large W
     // sets down the path that tests membership in the global lists instead)
@@ -2064,7 +2052,7 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
     int per_sm = 0;
     TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_k4, kK4Warps * 32, smem));
     if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)num_sms_c() * per_sm;
+    int64_t grid = (int64_t)tg_num_sms() * per_sm;
     const int64_t need = (g->n + kK4Warps - 1) / kK4Warps;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
@@ -2119,7 +2107,7 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
             TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_k4_bits_warp,
                                                                       kBitsWarps * 32, h4b));
             if (wper < 1) wper = 1;
-            int64_t wgrid2 = (int64_t)num_sms_c() * wper;
+            int64_t wgrid2 = (int64_t)tg_num_sms() * wper;
             if (wgrid2 > (n + kBitsWarps - 1) / kBitsWarps) wgrid2 = (n + kBitsWarps - 1) / kBitsWarps;
             if (wgrid2 < 1) wgrid2 = 1;
             k_k4_bits_warp<<<(unsigned)wgrid2, kBitsWarps * 32, h4b, s>>>(q); tg_note_launch();
@@ -2148,7 +2136,7 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
                     TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cper, k_k4_bits_cta, 256,
                                                                               csmem));
                     if (cper < 1) cper = 1;
-                    int64_t cgrid = (int64_t)num_sms_c() * cper;
+                    int64_t cgrid = (int64_t)tg_num_sms() * cper;
                     if (cgrid > nlist) cgrid = nlist;
                     TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
                     k_k4_bits_cta<<<(unsigned)cgrid, 256, csmem, s>>>(q, list.p, nlist); tg_note_launch();
@@ -2175,7 +2163,7 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
         TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&gper, k_k4_global,
                                                                   kK4GWarps * 32, gsmem));
         if (gper < 1) gper = 1;
-        int64_t ggrid = (int64_t)num_sms_c() * gper;
+        int64_t ggrid = (int64_t)tg_num_sms() * gper;
         const int64_t gneed = (g->M / kK4GChunk + kK4GWarps) / kK4GWarps;
         if (ggrid > gneed) ggrid = gneed;
         if (ggrid < 1) ggrid = 1;

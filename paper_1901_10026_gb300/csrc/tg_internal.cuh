@@ -117,6 +117,10 @@ void tg_note_launch();
 // its static shared memory).  Every caller writes the same value, so a call on
 // another host thread can never lower the limit between this thread's sizing
 // and its launch; launches are then checked against their own size only.
+// Multiprocessors of the current device, and the shared memory a block may
+// opt in to (48 KB when the attribute cannot be read).
+int tg_num_sms();
+int tg_smem_optin();
 int tg_allow_max_smem(const void *func);
 
 // Is p a device pointer (or managed)?  Host pointers, registered or not, -> false.

@@ -23,6 +23,20 @@ extern "C" int32_t tg_last_cuda_error(void) { return g_cuda_error; }
 
 extern "C" uint64_t tg_launch_count(void) { return g_launches.load(); }
 
+int tg_num_sms() {
+    int dev = 0, sms = 0;
+    (void)cudaGetDevice(&dev);
+    (void)cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+int tg_smem_optin() {
+    int dev = 0, v = 0;
+    (void)cudaGetDevice(&dev);
+    (void)cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v > 0 ? v : 48 * 1024;
+}
+
 int tg_allow_max_smem(const void *func) {
     int dev = 0, optin = 0;
     TG_TRY_CUDA(cudaGetDevice(&dev));

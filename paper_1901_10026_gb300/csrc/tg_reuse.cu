@@ -933,19 +933,7 @@ int edge_units(const tg_graph *g, const uint32_t *ord, int64_t cnt, cudaStream_t
     return TG_OK;
 }
 
-int num_sms_r() {
-    int dev = 0, sms = 0;
-    (void)cudaGetDevice(&dev);
-    (void)cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms > 0 ? sms : 1;
-}
 
-int smem_optin_r() {
-    int dev = 0, v = 0;
-    (void)cudaGetDevice(&dev);
-    (void)cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return v > 0 ? v : 48 * 1024;
-}
 
 
 template <int U>
@@ -956,7 +944,7 @@ int launch_reuse_u(const ReuseParams &p, int threads, size_t smem, int grid_limi
     TG_TRY_CUDA(
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_reuse<U>, threads, smem));
     if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)num_sms_r() * per_sm;
+    int64_t grid = (int64_t)tg_num_sms() * per_sm;
     if (grid > p.count) grid = p.count;
     if (grid_limit > 0 && grid > grid_limit) grid = grid_limit;
     if (grid < 1) grid = 1;
@@ -991,7 +979,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
         TG_TRY_CUDA(cudaMemsetAsync(q.p, 0, 16, s));
         TG_TRY_CUDA(cudaEventRecord(g_last.ev[0], s));
         if (un.nheavy > 0) {
-            const size_t avail = (size_t)smem_optin_r();
+            const size_t avail = (size_t)tg_smem_optin();
             int64_t nbits = g->n_nonisolated;
             if (t.bitmap_bits > 0 && nbits > t.bitmap_bits) nbits = t.bitmap_bits;
             const int64_t maxb = (int64_t)((avail - 64) / 16) * 128;
@@ -1001,7 +989,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
             int per_sm = 0;
             TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tau, 512, smem));
             if (per_sm < 1) per_sm = 1;
-            int64_t grid = (int64_t)num_sms_r() * per_sm;
+            int64_t grid = (int64_t)tg_num_sms() * per_sm;
             if (grid > (int64_t)un.nheavy) grid = un.nheavy;
             if (grid < 1) grid = 1;
             k_tau<<<(unsigned)grid, 512, smem, s>>>(g->rowptr, g->adj, g->toff, g->edges, ord,
@@ -1014,7 +1002,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
             TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tau_light,
                                                                       kLightWarps * 32, 0));
             if (per_sm < 1) per_sm = 1;
-            int64_t grid = (int64_t)num_sms_r() * per_sm;
+            int64_t grid = (int64_t)tg_num_sms() * per_sm;
             const int64_t need = ((int64_t)un.nlight + kLightWarps - 1) / kLightWarps;
             if (grid > need) grid = need;
             k_tau_light<<<(unsigned)grid, kLightWarps * 32, 0, s>>>(
@@ -1036,7 +1024,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
             int per = 0;
             TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_node_aggr_small,
                                                                       kAggrSmallThreads, asmem));
-            const int64_t ag = std::min<int64_t>((int64_t)num_sms_r() * (per > 0 ? per : 1),
+            const int64_t ag = std::min<int64_t>((int64_t)tg_num_sms() * (per > 0 ? per : 1),
                                                  (n + kAggrSmallThreads - 1) / kAggrSmallThreads);
             k_node_aggr_small<<<(unsigned)std::max<int64_t>(ag, 1), kAggrSmallThreads, asmem, s>>>(
                 g->rowptr, g->adj, g->eid, g->toff, tau.p, n, L, dsmall, theta.p, dsum.p); tg_note_launch();
@@ -1050,7 +1038,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
             TG_TRY(tg_scan_u32(nch.p, cpos.p, n, s));
             int per = 0;
             TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_node_aggr, 256, 0));
-            k_node_aggr<<<(unsigned)((int64_t)num_sms_r() * (per > 0 ? per : 1)), 256, 0, s>>>(
+            k_node_aggr<<<(unsigned)((int64_t)tg_num_sms() * (per > 0 ? per : 1)), 256, 0, s>>>(
                 g->rowptr, g->adj, g->eid, g->toff, tau.p, n, L, nch.p, cpos.p, theta.p, dsum.p); tg_note_launch();
             TG_TRY_CUDA(cudaGetLastError());
         }
@@ -1130,7 +1118,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
     const size_t stage_bytes = (size_t)threads * (3 * 8 + 2 * 4 + 1) + 34 * 8 + 16;
     const size_t fixed = (p.hist_smem ? hist_bytes : 0) + (size_t)(NMAT + NX) * L2 * 8 +
                          (size_t)kTCap * 4 + kMiscBytes + stage_bytes;
-    const size_t avail = (size_t)smem_optin_r();
+    const size_t avail = (size_t)tg_smem_optin();
     int hmax = t.hash_slots;
     while (fixed + (size_t)hmax * 4 + 4096 > avail && hmax > 32) hmax >>= 1;
     if (fixed + (size_t)hmax * 4 + 16 > avail) return TG_EINVAL;
