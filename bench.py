@@ -42,6 +42,8 @@ WORKLOADS = {
     "cl125k": "Chung-Lu n=125,000 m=1,000,000 gamma=2.1, L=5 Zipf(1.2) types, global k=4",
     "er1000": "Erdos-Renyi G(n=1000, p=0.01), L=3 uniform types, global k=4",
     "rmat23": "R-MAT scale 23, edge factor 16, (0.57,0.19,0.19,0.05), L=8 uniform types, global k=4",
+    "rmat20": "R-MAT scale 20, edge factor 16, (0.57,0.19,0.19,0.05), L=8 uniform types, global k=4",
+    "rmat18": "R-MAT scale 18, edge factor 16, (0.57,0.19,0.19,0.05), L=8 uniform types, global k=4",
 }
 L2_FLUSH_BYTES = 256 << 20
 
@@ -62,6 +64,9 @@ def parse():
     ap.add_argument("--batch-graphs", type=int, default=10000)
     ap.add_argument("--kernel", choices=["cycles", "reuse", "cta", "warp"], default="cycles",
                     help="counting kernel of the graph mode (tg_set_tune): cycles is the default path")
+    ap.add_argument("--edge-pass", choices=["auto", "fused"], default="auto",
+                    help="per-edge pass of the cycles kernel: auto (T sums through memory when they "
+                         "fit) or always the fused kernel")
     ap.add_argument("--retain-gib", type=int, default=64,
                     help="tg_set_memory_retention for the graph mode, GiB (0: the default pool)")
     ap.add_argument("--serve-requests", type=int, default=200)
@@ -82,8 +87,8 @@ def workload(name="cl1m"):
         return synth.cl_1m(seed=2, n=125_000, m=1_000_000)
     if name == "er1000":
         return synth.er_1000(seed=1)
-    if name == "rmat23":
-        return synth.rmat_23()
+    if name.startswith("rmat"):
+        return synth.rmat_23(scale=int(name[4:]))
     return synth.cl_1m()
 
 
@@ -401,6 +406,8 @@ def main():
     if args.kernel != "cycles":
         tg.tg_set_tune(kernel={"reuse": tg.TG_KERNEL_REUSE, "cta": tg.TG_KERNEL_CTA_BITMAP,
                                "warp": tg.TG_KERNEL_WARP_SEARCH}[args.kernel])
+    elif args.edge_pass == "fused":
+        tg.tg_set_tune(kernel=tg.TG_KERNEL_CYCLES, edge_pass=tg.TG_EDGE_PASS_FUSED)
 
     # shard ranges from the canonical edge list of the built graph (untimed)
     g0 = tg.tg_build_csr(G.n, src_d, dst_d, typ_d, L)

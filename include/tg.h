@@ -273,8 +273,15 @@ typedef struct {
                             walked in member tiles instead of warp units    */
     int64_t bitmap_bits; /* cap on the node ids covered by the bitmap       */
     int32_t grid_limit;  /* cap on the CTAs of one counting launch          */
-    int32_t reserved;
+    int32_t edge_pass;   /* CYCLES kernel, k = 4: TG_EDGE_PASS_AUTO keeps the
+                            per-edge T sums in memory between two kernels
+                            when they fit in a quarter of free memory, else
+                            runs the fused kernel; TG_EDGE_PASS_FUSED always
+                            runs the fused kernel                           */
 } tg_tune;
+
+#define TG_EDGE_PASS_AUTO 0
+#define TG_EDGE_PASS_FUSED 1
 
 int tg_set_tune(const tg_tune *t); /* NULL restores the defaults */
 int tg_get_tune(tg_tune *t);

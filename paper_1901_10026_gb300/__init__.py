@@ -55,7 +55,7 @@ class TGError(RuntimeError):
 class TGTune(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("cta_threads", ctypes.c_int32), ("unroll", ctypes.c_int32),
                 ("hash_slots", ctypes.c_int32), ("bitmap_bits", ctypes.c_int64),
-                ("grid_limit", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("grid_limit", ctypes.c_int32), ("edge_pass", ctypes.c_int32)]
 
 
 class TGTiming(ctypes.Structure):
@@ -77,6 +77,8 @@ TG_KERNEL_WARP_SEARCH = 1
 TG_KERNEL_CTA_BITMAP = 2
 TG_KERNEL_REUSE = 3
 TG_KERNEL_CYCLES = 4
+TG_EDGE_PASS_AUTO = 0
+TG_EDGE_PASS_FUSED = 1
 
 
 class TGServeCfg(ctypes.Structure):
@@ -471,12 +473,12 @@ def tg_work_model(g: Graph, stream=None) -> int:
 
 
 def tg_set_tune(kernel=0, cta_threads=0, unroll=0, hash_slots=0, bitmap_bits=0, grid_limit=0,
-                reset=False) -> None:
+                edge_pass=0, reset=False) -> None:
     """Set the counting kernels' launch configuration (``reset`` restores defaults)."""
     if reset:
         _check(lib().tg_set_tune(None), "tg_set_tune")
         return
-    t = TGTune(kernel, cta_threads, unroll, hash_slots, bitmap_bits, grid_limit, 0)
+    t = TGTune(kernel, cta_threads, unroll, hash_slots, bitmap_bits, grid_limit, edge_pass)
     _check(lib().tg_set_tune(ctypes.byref(t)), "tg_set_tune")
 
 

@@ -872,12 +872,15 @@ extern "C" int tg_set_tune(const tg_tune *t) {
         if (t->hash_slots && (t->hash_slots < 32 || (t->hash_slots & (t->hash_slots - 1))))
             return TG_EINVAL;
         if (t->bitmap_bits < 0 || t->grid_limit < 0) return TG_EINVAL;
+        if (t->edge_pass != TG_EDGE_PASS_AUTO && t->edge_pass != TG_EDGE_PASS_FUSED)
+            return TG_EINVAL;
         d.kernel = t->kernel;
         if (t->cta_threads) d.cta_threads = t->cta_threads;
         if (t->unroll) d.unroll = t->unroll;
         if (t->hash_slots) d.hash_slots = t->hash_slots;
         d.bitmap_bits = t->bitmap_bits;
         d.grid_limit = t->grid_limit;
+        d.edge_pass = t->edge_pass;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune = d;

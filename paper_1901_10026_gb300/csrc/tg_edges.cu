@@ -633,7 +633,7 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
     const size_t tsum_bytes = (size_t)count * 3 * L2 * 8;
     size_t free_b = 0, total_b = 0;
     TG_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const bool split = k == 4 && tsum_bytes <= free_b / 4;
+    const bool split = k == 4 && t.edge_pass != TG_EDGE_PASS_FUSED && tsum_bytes <= free_b / 4;
     int threads = t.cta_threads;
     if (threads > (split ? kTsumThreads : kEdgeMaxThreads)) threads = split ? kTsumThreads : kEdgeMaxThreads;
     if (threads < 32) threads = 32;

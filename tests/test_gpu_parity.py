@@ -20,6 +20,12 @@ VARIANTS = {
                          grid_limit=3, unroll=1),
     "cycles-split": dict(kernel=tg.TG_KERNEL_CYCLES, unroll=4),
     "cycles-split-bitmap": dict(kernel=tg.TG_KERNEL_CYCLES, unroll=4, hash_slots=32),
+    # the fused per-edge kernel (T sums kept in shared memory, identities in
+    # the same warp), which the library picks on its own only when the T sums
+    # of the whole graph would not fit in a quarter of free memory
+    "cycles-fused": dict(kernel=tg.TG_KERNEL_CYCLES, edge_pass=tg.TG_EDGE_PASS_FUSED),
+    "cycles-fused-small": dict(kernel=tg.TG_KERNEL_CYCLES, edge_pass=tg.TG_EDGE_PASS_FUSED,
+                               cta_threads=64, hash_slots=32, bitmap_bits=96, grid_limit=3),
     "reuse": dict(kernel=tg.TG_KERNEL_REUSE),
     "warp-search": dict(kernel=tg.TG_KERNEL_WARP_SEARCH),
     "cta-small": dict(kernel=tg.TG_KERNEL_CTA_BITMAP, cta_threads=128, unroll=1, hash_slots=32,
