@@ -1,14 +1,18 @@
 """Benchmark: typed 3/4-node graphlet counting on one graph (global counts).
 
-Workload: Chung-Lu graph, n = 1,000,000, exactly 8,000,000 distinct edges
-(average degree 16), exponent 2.1, L = 5 node types drawn Zipf(s = 1.2); the
-global typed 2/3/4-node counts in uint64.  One step = the whole path on one
-input: typed CSR build from the device-resident raw edge list
-(tg_build_csr) and the global count (tg_count_global: Alg. 1 for every edge,
-per-edge enumeration, closed forms, reduction, division by |E(H)|).  As a
-counting loop would, the bench lets the library keep freed scratch mapped
-between steps (tg_set_memory_retention, --retain-gib; 0 restores the default
-pool, which returns it to the device at every synchronisation).
+Workload (default): R-MAT scale 23 (8,388,608 nodes, 16 * 2^23 draws,
+quadrant probabilities (0.57, 0.19, 0.19, 0.05), no noise; self-loops and
+duplicates removed by the graph builder), L = 8 uniform node types; the
+global typed 2/3/4-node counts in uint64.  ``--workload cl1m`` is the
+Chung-Lu graph (n = 10^6, exactly 8 * 10^6 distinct edges, exponent 2.1,
+L = 5 Zipf(1.2) types).  One step = the whole path on one input: typed CSR
+build from the device-resident raw edge list (tg_build_csr) and the global
+count (tg_count_global: Alg. 1 for every edge, whole-graph 4-cycle and
+4-clique enumerations, the per-edge pass of identities and closed forms,
+reduction, division by |E(H)|).  As a counting loop would, the bench lets the
+library keep freed scratch mapped between steps (tg_set_memory_retention,
+--retain-gib; 0 restores the default pool, which returns it to the device at
+every synchronisation).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
@@ -55,9 +59,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--oracle-edges", type=int, default=20000,
-                    help="edges in the CPU oracle sample (cpu_baseline); 0 skips it")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cl1m",
-                    help="cl1m is the benchmark; the others are profiling and scale cases")
+                    help="most edges in the CPU oracle sample (cpu_baseline); 0 skips it")
+    ap.add_argument("--oracle-seconds", type=float, default=15.0,
+                    help="CPU time budget of the oracle sample (cpu_baseline; the reference arm "
+                         "spreads about 8x this over its steps)")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="end-to-end repeats (host arrays in, histogram out)")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat23",
+                    help="rmat23 is the benchmark; the others are profiling and scale cases")
     ap.add_argument("--mode", choices=["graph", "batch", "serve"], default="graph",
                     help="graph: one graph per step (default); batch: the 10,000-graph batched "
                          "workload; serve: the Poisson request stream")
@@ -161,20 +170,38 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def committed_traffic():
-    """DRAM bytes per edge of the per-edge pass (its three kernels) from the
-    committed ncu summary, used only while the kernel source still matches the
-    one profiled."""
+def committed_traffic(workload):
+    """DRAM bytes per edge of the per-edge pass from the committed ncu summary,
+    used only for the workload it was taken on (scaled by edges) and while the
+    kernel source still matches the one profiled."""
     path = os.path.join(ROOT, "profiles", "k_cyc_edge_traffic.json")
     src = os.path.join(ROOT, "paper_1901_10026_gb300", "csrc", "tg_edges.cu")
     try:
         rec = json.load(open(path))
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("source_sha256") != digest:
+        if rec.get("source_sha256") != digest or rec.get("workload") != workload:
             return None
         return float(rec["dram_bytes_per_edge"])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def oracle_sample(og, seconds, max_edges, seed):
+    """Per-edge graphlet rows of the first oracle on random edges, in growing
+    batches until about ``seconds`` of wall time (or ``max_edges``) are spent.
+    Returns (edges, seconds)."""
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(og.M)
+    done, spent, batch = 0, 0.0, 16
+    while done < min(max_edges, og.M) and spent < seconds:
+        take = min(batch, max_edges - done, og.M - done)
+        pick = np.sort(order[done:done + take])
+        t0 = time.perf_counter()
+        og.per_edge(k=4, level="graphlet", edges=pick)
+        spent += time.perf_counter() - t0
+        done += take
+        batch *= 2
+    return done, spent
 
 
 # -------------------------------------------------------------- reference --
@@ -185,7 +212,12 @@ def run_reference(args, rank, world):
     G = workload(args.workload)
     og = oracle.OracleGraph.from_edges(G)
     rng = np.random.default_rng(0)
-    per_step = max(1, min(og.M, args.oracle_edges // 6))
+    # edges per step: what the oracle does in about 8 * oracle_seconds over all
+    # steps (calibrated on a first sample), at most oracle_edges / 6
+    cal_edges, cal_s = oracle_sample(og, min(2.0, args.oracle_seconds), args.oracle_edges, 2)
+    rate = cal_edges / max(cal_s, 1e-6)
+    budget = 8.0 * args.oracle_seconds / max(1, args.warmup + args.steps)
+    per_step = max(1, min(og.M, args.oracle_edges // 6, int(rate * budget)))
     samples = [np.sort(rng.choice(og.M, per_step, replace=False)) for _ in range(args.warmup + args.steps)]
     times = []
     for s, pick in enumerate(samples):
@@ -214,17 +246,36 @@ def run_reference(args, rank, world):
     return 0
 
 
-def cpu_baseline(G, n_edges):
+def cpu_baseline(G, n_edges, seconds, workload_name):
     import oracle
     og = oracle.OracleGraph.from_edges(G)
-    rng = np.random.default_rng(1)
-    pick = np.sort(rng.choice(og.M, min(n_edges, og.M), replace=False))
-    t0 = time.perf_counter()
-    og.per_edge(k=4, level="graphlet", edges=pick)
-    dt = time.perf_counter() - t0
-    return {"value": pick.shape[0] / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"{pick.shape[0]} random edges of the workload graph (per-edge graphlet rows, "
-                      f"{dt:.1f} s of CPU time on the host)"}
+    done, dt = oracle_sample(og, seconds, n_edges, 1)
+    out = {"value": done / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+           "sample": f"{done} random edges of the workload graph (per-edge graphlet rows of the "
+                     f"paper-method oracle, {dt:.1f} s on the host cores)"}
+    rec = recorded_oracle2(workload_name)
+    if rec is not None:
+        out["oracle2_full_graph"] = rec
+    return out
+
+
+def recorded_oracle2(workload_name):
+    """The second oracle's time for the whole graph, as recorded in the header
+    of the committed golden histogram (not re-measured by this run)."""
+    path = os.path.join(ROOT, "tests", "golden", f"{workload_name}_o2_global.txt")
+    try:
+        for line in open(path):
+            if not line.startswith("#"):
+                break
+            if "from oracle.o2 alone" in line:
+                sec = float(line.split("(")[1].split(" s on ")[0])
+                thr = int(line.split(" s on ")[1].split()[0])
+                return {"seconds": sec, "cores": thr, "edges_per_s": None,
+                        "where": "build host (x86_64), recorded when the golden file was written",
+                        "source": f"tests/golden/{workload_name}_o2_global.txt"}
+    except (OSError, ValueError, IndexError):
+        return None
+    return None
 
 
 # -------------------------------------------------------------------- gpu ---
@@ -482,7 +533,7 @@ def main():
     # end to end: host inputs copied in and the histogram read back every step
     torch.cuda.synchronize()
     e2e_times = []
-    for s in range(max(1, args.steps)):
+    for s in range(max(1, args.e2e_steps)):
         if world > 1:
             tdist.barrier()
         t0 = time.perf_counter()
@@ -511,7 +562,7 @@ def main():
     # and types of i and j and their Theta and D rows (L x L uint32 each)
     own_bytes = (4.0 * tm["gamma_entries"] + tm["t_members"] * 4.0 * (3 * L + 3) +
                  units * (4.0 + 8.0 + 4.0 * L + 8.0 * (L + 1) + 16.0 + 2.0 + 16.0 * L * L))
-    traffic_per_edge = committed_traffic()
+    traffic_per_edge = committed_traffic(args.workload)
     phase_ms = {"tau": tm["tau_ms"], "aggregate": tm["aggregate_ms"], "cycles": tm["cycles_ms"],
                 "cliques": tm["cliques_ms"], "count": tm["count_ms"]}
     roofline = {
@@ -533,7 +584,8 @@ def main():
     }
 
     if rank == 0:
-        cpu = cpu_baseline(G, args.oracle_edges) if (world == 1 and args.oracle_edges > 0) else None
+        cpu = (cpu_baseline(G, args.oracle_edges, args.oracle_seconds, args.workload)
+               if (world == 1 and args.oracle_edges > 0) else None)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -546,7 +598,7 @@ def main():
                        "parallelism": f"edge ranges x{world}" if world > 1 else "single GPU"},
             "clocks": clocks,
             "e2e": {"value": M / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+                    "d2h_bytes_per_step": int(d2h), "repeats": int(max(1, args.e2e_steps))},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "gpu_launches": int(launches),

@@ -174,8 +174,13 @@ int tg_slot_config(int32_t L, int32_t k, int32_t level, int32_t phi_i, int32_t p
  * Global typed graphlet counts (Sec. "Global Typed Graphlet Counts").
  *   k    3 or 4 (k = 4 also fills the 2- and 3-node blocks)
  *   out  tg_global_len(L, k) uint64 entries, host or device
- * Runs Alg. 1-3 and the closed forms per edge on the GPU, reduces into a
- * per-configuration histogram and divides by |E(H)|.  Errors: TG_EINVAL,
+ * The default kernel (TG_KERNEL_CYCLES) runs Alg. 1 for every edge, then
+ * obtains the orbits that Alg. 2-3 enumerate per edge from identities over
+ * Alg. 1's typed triangle counts plus two whole-graph enumerations (4-cycles
+ * and 4-cliques, each met once in degree order), adds the closed forms,
+ * reduces into a per-configuration histogram and divides by |E(H)|; the
+ * other TG_KERNEL_* choices run Alg. 2-3 per edge as the paper does.  The
+ * counts are the same.  Errors: TG_EINVAL,
  * TG_EOVERFLOW (the graph is too large for the 32-bit per-edge counters:
  * 2M >= 2^31), TG_EINTERNAL (a sum not divisible by |E(H)|), TG_ENOMEM,
  * TG_ECUDA.
@@ -235,7 +240,14 @@ int tg_work_model(const tg_graph *g, uint64_t *entries, void *stream);
  *   - tg_global_len(L, k) must not exceed TG_NOALLOC_MAX_GLOBAL (k = 4 with
  *     L <= 9, or k = 3 with any L); larger requests return TG_EINVAL.
  *   - The first call on a device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *     that device current and loads the library's device code there; make
+ *     that first call before any stream capture.  With the CUDA runtime's
+ *     lazy module loading (the default), that first use is when the CUDA
+ *     driver itself places the array and the kernels' code on the device, so
+ *     a caller whose arena will own all device memory makes its first call
+ *     (a one-edge graph will do) before the arena takes the device; later
+ *     calls take no device memory at all.  Resetting the device between
+ *     calls (cudaDeviceReset) is not supported: the address is cached.
  *   - All calls share the array.  Calls whose work overlaps on the GPU (other
  *     streams, other host threads) race on it and give wrong counts; order
  *     them on one stream or synchronise between them.

@@ -1282,6 +1282,8 @@ struct K4GParams {
     unsigned long long *g4;
     int64_t n4;
     unsigned long long *work;
+    uint32_t *rows;       // k_k4_rows: per CTA rows_stride words of bitmap rows
+    int64_t rows_stride;
 };
 
 constexpr int kK4GWarps = 8;
@@ -1461,7 +1463,6 @@ __global__ void __launch_bounds__(kK4GWarps * 32) k_k4_global(K4GParams p) {
 // contiguous range and popc(bm_v & bm_w & mask_t) counts the cliques whose
 // fourth node has type t.
 constexpr int kBitsWarpMax = 32;    // up lists of at most 32: one word, one warp
-constexpr int kBitsCtaMax = 1024;   // up to 1024: shared-memory bitmaps, one CTA
 constexpr int kBitsWarps = 8;
 
 __device__ __forceinline__ uint32_t range_mask(int lo, int hi) {  // bits [lo, hi) of a word
@@ -1554,22 +1555,65 @@ __global__ void __launch_bounds__(kBitsWarps * 32) k_k4_bits_warp(K4GParams p) {
     if (p.work && wpairs) atomicAdd(p.work + 5, wpairs);
 }
 
-// Up lists of 33..kBitsCtaMax: one CTA per x0 (from `list`), bitmaps in shared
-// memory.
-__global__ void __launch_bounds__(256) k_k4_bits_cta(K4GParams p, const uint32_t *list,
-                                                    uint32_t nlist) {
+// Up lists longer than one word: one CTA per x0 (from `list`).  Positions in
+// up(x0) are laid out type by type, each type's range padded to whole 32-bit
+// words, so that every word of a bitmap covers one type.  Row q (member q of
+// up(x0), node v) is the bitmap of up(v) n up(x0) over these positions; one
+// warp builds it from v's up list through a shared-memory map from node id to
+// position and stores it in the CTA's slice of global memory (the rows are
+// read back from L2).  Every clique x0 < v < w < x is one bit of
+// row_v & row_w for a w in row_v: a warp takes v, keeps row_v in registers
+// (WPL words per lane), visits the set bits w of row_v in position order and
+// adds popc(row_v & row_w) per word to per-lane counters, flushed into the
+// type-multiset histogram whenever the type of w changes (the type of x is
+// the word's type).  One pair costs one coalesced row load per warp.
+constexpr int kRowsThreads = 512;
+constexpr int kRowsMaxWords = 128;
+
+template <int WPL>
+__device__ __forceinline__ uint32_t rows_pick(const uint32_t (&r)[WPL], int i) {
+    uint32_t x = r[0];
+#pragma unroll
+    for (int k = 1; k < WPL; ++k)
+        if (i == k) x = r[k];
+    return x;
+}
+
+// The per-lane counts of the words a lane holds (w of type tw so far) into
+// the histogram under {t0, tv, tw, type of the word}; clears them.
+template <int WPL>
+__device__ __forceinline__ void rows_flush(unsigned long long *h4, uint32_t (&acc)[WPL],
+                                           const int32_t *wt, int words, int lane, int t0, int tv,
+                                           int tw, unsigned long long &wk) {
+    if (tw < 0) return;
+#pragma unroll
+    for (int i = 0; i < WPL; ++i) {
+        const int kk = lane + 32 * i;
+        if (kk < words && acc[i]) {
+            k4_hist_add(h4, t0, tv, tw, wt[kk], (unsigned long long)acc[i]);
+            wk += acc[i];
+        }
+        acc[i] = 0u;
+    }
+}
+
+template <int WPL>
+__global__ void __launch_bounds__(kRowsThreads) k_k4_rows(K4GParams p, const uint32_t *list,
+                                                          uint32_t nlist) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
     const int L = p.L;
     unsigned long long *h4 = reinterpret_cast<unsigned long long *>(smem);
     const size_t h4b = ((size_t)p.n4 * 8 + 15) & ~(size_t)15;
-    constexpr int kLg = 11;  // 2048 slots for up to 1024 members
-    uint32_t *hk = reinterpret_cast<uint32_t *>(smem + h4b);
-    uint32_t *hv = hk + (1 << kLg);
-    uint32_t *tm = hv + (1 << kLg);          // TG_MAX_TYPES x 32 words
-    uint32_t *ty = tm + TG_MAX_TYPES * 32;   // types of the positions
-    uint32_t *bm = ty + kBitsCtaMax;         // d0 x words
+    uint32_t *hk = reinterpret_cast<uint32_t *>(smem + h4b);  // 2^p.hlg slots
+    uint32_t *hv = hk + (1 << p.hlg);
+    int32_t *wt = reinterpret_cast<int32_t *>(hv + (1 << p.hlg));  // type of each word
+    int32_t *ws = wt + kRowsMaxWords;        // first word of each type, L + 1
+    int32_t *to = ws + TG_MAX_TYPES + 1;     // type offsets of up(x0), L + 1
+    uint32_t *rb = reinterpret_cast<uint32_t *>(to + TG_MAX_TYPES + 1) + warp * kRowsMaxWords;
+    const volatile uint32_t *vrb = rb;
     __shared__ unsigned long long s_item;
+    uint32_t *rows = p.rows + (size_t)blockIdx.x * (size_t)p.rows_stride;
     for (int64_t q = tid; q < p.n4; q += blockDim.x) h4[q] = 0ull;
     unsigned long long wk = 0, wpairs = 0;
     for (;;) {
@@ -1581,58 +1625,93 @@ __global__ void __launch_bounds__(256) k_k4_bits_cta(K4GParams p, const uint32_t
         const uint32_t x0 = list[item];
         const int64_t b0 = __ldg(p.uoff + x0);
         const int d0 = (int)(__ldg(p.uoff + x0 + 1) - b0);
-        const int words = (d0 + 31) >> 5;
         const int t0 = p.ntype[x0];
         const int32_t *to0 = p.utoff + (int64_t)x0 * (L + 1);
-        for (int q = tid; q < (1 << kLg); q += blockDim.x) hk[q] = 0u;
-        for (int q = tid; q < d0 * words; q += blockDim.x) bm[q] = 0u;
-        for (int q = tid; q < L * words; q += blockDim.x) {
-            const int t = q / words, k = q % words;
-            tm[t * 32 + k] = range_mask(__ldg(to0 + t) - 32 * k, __ldg(to0 + t + 1) - 32 * k);
+        int lg = 5;
+        while ((1 << lg) < 2 * d0 && lg < p.hlg) ++lg;
+        if (tid <= L) to[tid] = __ldg(to0 + tid);
+        if (tid == 0) {
+            int w = 0;
+            for (int t = 0; t < L; ++t) {
+                ws[t] = w;
+                w += (__ldg(to0 + t + 1) - __ldg(to0 + t) + 31) >> 5;
+            }
+            ws[L] = w;
         }
+        for (int q = tid; q < (1 << lg); q += blockDim.x) hk[q] = 0u;
         __syncthreads();
+        const int words = ws[L];
+        for (int k = tid; k < words; k += blockDim.x) {
+            int t = 0;
+            while (t + 1 < L && ws[t + 1] <= k) ++t;
+            wt[k] = t;
+        }
         for (int q = tid; q < d0; q += blockDim.x) {
             const uint32_t e = __ldg(p.uadj + b0 + q);
-            hmap_put(hk, hv, kLg, e & TG_IDMASK, (uint32_t)q);
-            ty[q] = e >> TG_TSHIFT;
+            const int t = (int)(e >> TG_TSHIFT);
+            hmap_put(hk, hv, lg, e & TG_IDMASK, (uint32_t)(32 * ws[t] + (q - to[t])));
         }
         __syncthreads();
-        for (int pv = warp; pv < d0; pv += W) {
-            const uint32_t v = __ldg(p.uadj + b0 + pv) & TG_IDMASK;
+        // rows: warp per member v
+        for (int q = warp; q < d0; q += W) {
+            for (int k = lane; k < words; k += 32) rb[k] = 0u;
+            __syncwarp();
+            const uint32_t v = __ldg(p.uadj + b0 + q) & TG_IDMASK;
             const int64_t bv = __ldg(p.uoff + v);
             const int dv = (int)(__ldg(p.uoff + v + 1) - bv);
             for (int c = lane; c < dv; c += 32) {
-                const uint32_t pos = hmap_get(hk, hv, kLg, __ldg(p.uadj + bv + c) & TG_IDMASK);
-                if (pos != 0xffffffffu) atomicOr(bm + pv * words + (pos >> 5), 1u << (pos & 31u));
+                const uint32_t pp = hmap_get(hk, hv, lg, __ldg(p.uadj + bv + c) & TG_IDMASK);
+                if (pp != 0xffffffffu) atomicOr(rb + (pp >> 5), 1u << (pp & 31u));
             }
+            __syncwarp();
+            for (int k = lane; k < words; k += 32) rows[(size_t)q * words + k] = vrb[k];
+            __syncwarp();
         }
         __syncthreads();
-        // pairs: warp per v, lanes over the positions w of its bitmap
-        for (int pv = warp; pv < d0; pv += W) {
-            const volatile uint32_t *bv = bm + pv * words;
-            const int tv = (int)ty[pv];
-            for (int q = lane; q < d0; q += 32) {
-                if (!((bv[q >> 5] >> (q & 31)) & 1u)) continue;
-                const volatile uint32_t *bq = bm + q * words;
-                const int tw = (int)ty[q];
-                for (int t = 0; t < L; ++t) {
-                    // only the words of type t's position range
-                    const int s0 = __ldg(to0 + t), s1 = __ldg(to0 + t + 1);
-                    int c = 0;
-                    for (int k = s0 >> 5; k < ((s1 + 31) >> 5); ++k)
-                        c += __popc(bv[k] & bq[k] & tm[t * 32 + k]);
-                    if (c) k4_hist_add(h4, t0, tv, tw, t, (unsigned long long)c);
-                    wk += (unsigned long long)c;
-                }
-                ++wpairs;
+        // pairs (v, w in row_v): warp per v
+        for (int q = warp; q < d0; q += W) {
+            const int tv = (int)(__ldg(p.uadj + b0 + q) >> TG_TSHIFT);
+            const uint32_t *rowv = rows + (size_t)q * words;
+            uint32_t rv[WPL], acc[WPL];
+#pragma unroll
+            for (int i = 0; i < WPL; ++i) {
+                const int kk = lane + 32 * i;
+                rv[i] = kk < words ? __ldcg(rowv + kk) : 0u;
+                acc[i] = 0u;
             }
+            int cur = -1;
+            for (int k = 0; k < words; ++k) {
+                uint32_t x = __shfl_sync(kFull, rows_pick<WPL>(rv, k >> 5), k & 31);
+                if (!x) continue;
+                const int tw = wt[k];
+                if (tw != cur) {
+                    rows_flush<WPL>(h4, acc, wt, words, lane, t0, tv, cur, wk);
+                    cur = tw;
+                }
+                const int qb = to[tw] + 32 * (k - ws[tw]);  // member index of the word's bit 0
+                while (x) {
+                    const int b = __ffs(x) - 1;
+                    x &= x - 1u;
+                    const uint32_t *roww = rows + (size_t)(qb + b) * words;
+#pragma unroll
+                    for (int i = 0; i < WPL; ++i) {
+                        const int kk = lane + 32 * i;
+                        if (kk < words) acc[i] += (uint32_t)__popc(rv[i] & __ldcg(roww + kk));
+                    }
+                    ++wpairs;
+                }
+            }
+            rows_flush<WPL>(h4, acc, wt, words, lane, t0, tv, cur, wk);
         }
     }
     __syncthreads();
     for (int64_t q = tid; q < p.n4; q += blockDim.x)
         if (h4[q]) atomicAdd(p.g4 + q, h4[q]);
-    if (p.work && wk) atomicAdd(p.work + 6, wk);
-    if (p.work && wpairs) atomicAdd(p.work + 5, wpairs);
+    if (p.work) {
+        // wpairs is the same in every lane of a warp: count it once
+        if (lane == 0 && wpairs) atomicAdd(p.work + 5, wpairs);
+        if (wk) atomicAdd(p.work + 6, wk);
+    }
 }
 
 __global__ void k_flag_range(const int64_t *uoff, int64_t n, int lo, int hi, uint32_t *flag) {
@@ -2098,9 +2177,11 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
         q.g4 = g4;
         q.n4 = n4;
         q.work = work;
-        // bitmap kernels for up lists up to kBitsCtaMax (a hash_slots cap
-        // below 64 sends every x0 to the hash-set kernel instead)
-        const int bits_max = t.hash_slots >= 64 ? kBitsCtaMax : 0;
+        // bitmap kernels: one word for up lists of at most 32 (warp per x0),
+        // padded rows of up to kRowsMaxWords words beyond (CTA per x0, in
+        // three widths); a hash_slots cap below 64 sends every x0 to the
+        // hash-set kernel instead
+        const int bits_max = t.hash_slots >= 64 ? 32 * kRowsMaxWords - 31 * L : 0;
         if (bits_max > 0) {
             TG_TRY(tg_allow_max_smem((const void *)k_k4_bits_warp));
             int wper = 0;
@@ -2112,11 +2193,17 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
             if (wgrid2 < 1) wgrid2 = 1;
             k_k4_bits_warp<<<(unsigned)wgrid2, kBitsWarps * 32, h4b, s>>>(q); tg_note_launch();
             TG_TRY_CUDA(cudaGetLastError());
-            if (maxup > (unsigned long long)kBitsWarpMax) {
-                DevBuf<uint32_t> flag, pos, list;
-                if (!flag.alloc(n, s) || !pos.alloc(n, s) || !list.alloc(n, s)) return TG_ENOMEM;
-                const unsigned egrid = (unsigned)std::min<int64_t>((n + 255) / 256, 65535LL * 16);
-                k_flag_range<<<egrid, 256, 0, s>>>(uoff.p, n, kBitsWarpMax + 1, bits_max, flag.p); tg_note_launch();
+            DevBuf<uint32_t> flag, pos, list;
+            const unsigned egrid = (unsigned)std::min<int64_t>((n + 255) / 256, 65535LL * 16);
+            for (int wpl = 1; wpl <= 4; wpl *= 2) {
+                // up lists whose padded rows need at most 32 * wpl words: every
+                // type range adds at most 31 positions of padding
+                const int lo = wpl == 1 ? kBitsWarpMax + 1 : 32 * 16 * wpl - 31 * L + 1;
+                const int hi = 32 * 32 * wpl - 31 * L;
+                if ((unsigned long long)lo > maxup || hi < lo) continue;
+                if (!flag.p && (!flag.alloc(n, s) || !pos.alloc(n, s) || !list.alloc(n, s)))
+                    return TG_ENOMEM;
+                k_flag_range<<<egrid, 256, 0, s>>>(uoff.p, n, lo, hi, flag.p); tg_note_launch();
                 TG_TRY_CUDA(cudaGetLastError());
                 TG_TRY(tg_scan_u32(flag.p, pos.p, n, s));
                 k_c4_compact<<<egrid, 256, 0, s>>>(flag.p, pos.p, n, list.p); tg_note_launch();
@@ -2126,22 +2213,38 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
                 TG_TRY_CUDA(cudaMemcpyAsync(&lastf, flag.p + n - 1, 4, cudaMemcpyDeviceToHost, s));
                 TG_TRY_CUDA(cudaStreamSynchronize(s));
                 const uint32_t nlist = lastp + lastf;
-                if (nlist > 0) {
-                    const int dmax = (int)std::min<unsigned long long>(maxup, (unsigned long long)bits_max);
-                    const int wmax = (dmax + 31) / 32;
-                    const size_t csmem = h4b + (size_t)(2 * 2048 + TG_MAX_TYPES * 32 + kBitsCtaMax) * 4 +
-                                         (size_t)dmax * wmax * 4;
-                    TG_TRY(tg_allow_max_smem((const void *)k_k4_bits_cta));
-                    int cper = 0;
-                    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cper, k_k4_bits_cta, 256,
-                                                                              csmem));
-                    if (cper < 1) cper = 1;
-                    int64_t cgrid = (int64_t)tg_num_sms() * cper;
-                    if (cgrid > nlist) cgrid = nlist;
-                    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
-                    k_k4_bits_cta<<<(unsigned)cgrid, 256, csmem, s>>>(q, list.p, nlist); tg_note_launch();
-                    TG_TRY_CUDA(cudaGetLastError());
-                }
+                if (nlist == 0) continue;
+                const int dmax = (int)std::min<unsigned long long>(maxup, (unsigned long long)hi);
+                int hlg = 5;
+                while ((1 << hlg) < 2 * dmax) ++hlg;
+                const size_t rsmem = h4b + (size_t)2 * (1u << hlg) * 4 +
+                                     (size_t)(kRowsMaxWords + 2 * (TG_MAX_TYPES + 1)) * 4 +
+                                     (size_t)(kRowsThreads / 32) * kRowsMaxWords * 4;
+                const void *kfn = wpl == 1 ? (const void *)k_k4_rows<1>
+                                  : wpl == 2 ? (const void *)k_k4_rows<2>
+                                             : (const void *)k_k4_rows<4>;
+                TG_TRY(tg_allow_max_smem(kfn));
+                int rper = 0;
+                TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rper, kfn, kRowsThreads,
+                                                                          rsmem));
+                if (rper < 1) rper = 1;
+                int64_t rgrid = (int64_t)tg_num_sms() * rper;
+                if (rgrid > nlist) rgrid = nlist;
+                K4GParams r = q;
+                r.hlg = hlg;
+                r.rows_stride = (int64_t)dmax * 32 * wpl;
+                DevBuf<uint32_t> rows;
+                if (!rows.alloc((size_t)rgrid * (size_t)r.rows_stride, s)) return TG_ENOMEM;
+                r.rows = rows.p;
+                TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
+                if (wpl == 1)
+                    k_k4_rows<1><<<(unsigned)rgrid, kRowsThreads, rsmem, s>>>(r, list.p, nlist);
+                else if (wpl == 2)
+                    k_k4_rows<2><<<(unsigned)rgrid, kRowsThreads, rsmem, s>>>(r, list.p, nlist);
+                else
+                    k_k4_rows<4><<<(unsigned)rgrid, kRowsThreads, rsmem, s>>>(r, list.p, nlist);
+                tg_note_launch();
+                TG_TRY_CUDA(cudaGetLastError());
             }
         }
         if (maxup <= (unsigned long long)bits_max) return TG_OK;

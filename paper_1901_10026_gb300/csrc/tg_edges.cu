@@ -291,42 +291,72 @@ __device__ void edge_finish(const EdgeParams &p, unsigned long long *shist, int6
     }
 }
 
-// One chunk of Gamma_i (one entry per lane): the lanes holding a T member y
-// (packed entry w, edge ids eiy of (i, y) and ejy of (j, y)) add tau_jy,
-// tau_iy and y's typed degrees, by the type of y, to this warp's B, C, DT.
-// All 32 lanes call it.
-__device__ __forceinline__ void tsum_chunk(const EdgeParams &p, bool isT, uint32_t w, uint32_t eiy,
-                                           uint32_t ejy, unsigned long long *Bm,
-                                           unsigned long long *Cm, unsigned long long *Dm) {
-    const int L = p.L;
-    const int lane = threadIdx.x & 31;
-    const int a = (int)(w >> TG_TSHIFT);
-    const unsigned tm = __match_any_sync(kFull, isT ? a : -1);
-    const bool lead = isT && lane == __ffs(tm) - 1;
-    const uint32_t *tiy = p.tau, *tjy = p.tau;
-    const int32_t *ty = p.toff;
-    if (isT) {
-        tiy = p.tau + (int64_t)eiy * L;
-        tjy = p.tau + (int64_t)ejy * L;
-        ty = p.toff + (int64_t)(w & TG_IDMASK) * (L + 1);
-    }
-    int prev = isT ? __ldg(ty) : 0;
-    for (int b = 0; b < L; ++b) {
-        uint32_t vb = 0, vc = 0, vd = 0;
-        if (isT) {
-            vb = __ldg(tjy + b);
-            vc = __ldg(tiy + b);
-            const int nx = __ldg(ty + b + 1);
-            vd = (uint32_t)(nx - prev);
-            prev = nx;
-        }
-        const uint32_t sb = __reduce_add_sync(tm, vb);
-        const uint32_t sc = __reduce_add_sync(tm, vc);
-        const uint32_t sd = __reduce_add_sync(tm, vd);
-        if (lead) {
-            Bm[a * L + b] += sb;
-            Cm[a * L + b] += sc;
-            Dm[a * L + b] += sd;
+// T sums of edge e = (i, j): B, C, DT (ordered [a][b], uint64, this warp's
+// shared memory, zeroed by the caller) over y in T = Gamma_i n Gamma_j.
+// Alg. 1's tau row of e gives |T^a| for every type a, and Gamma_i is sorted by
+// (type, id), so the scan skips the type ranges of Gamma_i that hold no T
+// member and leaves a range as soon as its |T^a| members are found (T members
+// have high degree, i.e. small ids, so they come early in their range).
+// find(w, ejy) tells whether the entry w of Gamma_i lies in Gamma_j, and gives
+// the edge id of (j, w).  The T members of a chunk (all of type a) go to lane
+// groups of 8 (L <= 8) or 16 lanes; lane b of a group reads tau_jy[b],
+// tau_iy[b] and d_y^b (three coalesced rows), the groups' values are added
+// across the warp and the first group adds them to B, C, DT.  Called by all
+// 32 lanes; adds the entries of Gamma_i it read to *read and the T members to
+// *nt (lane-uniform values).
+template <class Find>
+__device__ __forceinline__ void tsum_edge(const EdgeParams &p, int64_t e, int64_t bi,
+                                          const int32_t *toi, Find find, unsigned long long *Bm,
+                                          unsigned long long *Cm, unsigned long long *Dm,
+                                          unsigned long long &read, unsigned long long &nt) {
+    const int L = p.L, lane = threadIdx.x & 31;
+    const int gsz = L <= 8 ? 8 : 16, ng = 32 / gsz, grp = lane / gsz, b = lane % gsz;
+    const uint32_t *tn = p.tau + e * L;
+    for (int a = 0; a < L; ++a) {
+        const int need = (int)__ldg(tn + a);
+        if (need == 0) continue;
+        const int r0 = __ldg(toi + a), r1 = __ldg(toi + a + 1);
+        int found = 0;
+        for (int c0 = r0; c0 < r1 && found < need; c0 += 32) {
+            const int x = c0 + lane;
+            bool isT = false;
+            uint32_t w = 0, ejy = 0;
+            if (x < r1) {
+                w = __ldg(p.adj + bi + x);
+                isT = find(w, ejy);
+            }
+            unsigned tb = __ballot_sync(kFull, isT);
+            found += __popc(tb);
+            read += (unsigned long long)min(32, r1 - c0);
+            nt += (unsigned long long)__popc(tb);
+            while (tb) {
+                // group grp takes the grp-th remaining member
+                unsigned m = tb;
+                for (int k = 0; k < grp; ++k) m &= m - 1u;
+                const bool has = m != 0u;
+                const int src = has ? __ffs(m) - 1 : 0;
+                for (int k = 0; k < ng; ++k) tb &= tb - 1u;
+                const uint32_t wy = __shfl_sync(kFull, w, src);
+                const uint32_t ej = __shfl_sync(kFull, ejy, src);
+                uint32_t vb = 0, vc = 0, vd = 0;
+                if (has && b < L) {
+                    const uint32_t ei = __ldg(p.eid + bi + c0 + src);
+                    const int32_t *ty = p.toff + (int64_t)(wy & TG_IDMASK) * (L + 1);
+                    vb = __ldg(p.tau + (int64_t)ej * L + b);
+                    vc = __ldg(p.tau + (int64_t)ei * L + b);
+                    vd = (uint32_t)(__ldg(ty + b + 1) - __ldg(ty + b));
+                }
+                for (int o = gsz; o < 32; o <<= 1) {
+                    vb += __shfl_xor_sync(kFull, vb, o);
+                    vc += __shfl_xor_sync(kFull, vc, o);
+                    vd += __shfl_xor_sync(kFull, vd, o);
+                }
+                if (grp == 0 && b < L) {
+                    Bm[a * L + b] += vb;
+                    Cm[a * L + b] += vc;
+                    Dm[a * L + b] += vd;
+                }
+            }
         }
     }
 }
@@ -342,7 +372,7 @@ template <bool kWrite>
 __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc_edge(EdgeParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
-    const int L = p.L, P = p.P, L2 = L * L;
+    const int L = p.L, L2 = L * L;
     size_t off = 0;
     unsigned long long *shist = reinterpret_cast<unsigned long long *>(smem);
     if (p.hist_smem) off += ((size_t)p.hist_len * 8 + 15) & ~(size_t)15;
@@ -405,7 +435,6 @@ __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc
             const int i = max(ab.x, ab.y);
             const int ti = p.ntype[i], tj = p.ntype[j];
             const int64_t bi = rowptr[i];
-            const int di = (int)(rowptr[i + 1] - bi);
             const int32_t *toi = p.toff + (int64_t)i * (L + 1);
             const int32_t *toj = p.toff + (int64_t)j * (L + 1);
             const uint32_t *tn = p.tau + e * L;
@@ -413,35 +442,27 @@ __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc
                 for (int x = lane; x < 3 * L2; x += 32) Bm[x] = 0ull;
                 __syncwarp();
                 // T = Gamma_i n Gamma_j: sums of tau_jy, tau_iy and d_y by types
-                for (int c0 = 0; c0 < di; c0 += 32) {
-                    const int x = c0 + lane;
-                    bool isT = false;
-                    uint32_t w = 0;
-                    if (x < di) {
-                        w = __ldg(adj + bi + x);
-                        const uint32_t id = w & TG_IDMASK;
-                        if ((int)id != j)
-                            isT = (int64_t)id < p.nbits ? bm_test(bm, id)
-                                                        : contains(adj, bj, toj, w);
+                auto find = [&](uint32_t w, uint32_t &ejy) -> bool {
+                    const uint32_t id = w & TG_IDMASK;
+                    if ((int)id == j) return false;
+                    if ((int64_t)id < p.nbits) {
+                        if (!bm_test(bm, id)) return false;
+                        ejy = __ldcg(emap + id);  // written for this j before the barrier
+                        return true;
                     }
-                    uint32_t eiy = 0, ejy = 0;
-                    if (isT) {
-                        const uint32_t yid = w & TG_IDMASK;
-                        eiy = __ldg(p.eid + bi + x);
-                        if ((int64_t)yid < p.nbits) {
-                            ejy = __ldcg(emap + yid);  // written for this j before the barrier
-                        } else {
-                            const int pj = find_pos(adj, bj, toj, w);
-                            ejy = __ldg(p.eid + bj + (pj < 0 ? 0 : pj));
-                        }
-                    }
-                    tsum_chunk(p, isT, w, eiy, ejy, Bm, Cm, Dm);
-                    const unsigned tb = __ballot_sync(kFull, isT);
-                    if (lane == 0) wk_t += (unsigned long long)__popc(tb);
+                    const int pj = find_pos(adj, bj, toj, w);
+                    if (pj < 0) return false;
+                    ejy = __ldg(p.eid + bj + pj);
+                    return true;
+                };
+                unsigned long long rd = 0, nt = 0;
+                tsum_edge(p, e, bi, toi, find, Bm, Cm, Dm, rd, nt);
+                if (lane == 0) {
+                    wk_gamma += rd;
+                    wk_t += nt;
                 }
                 __syncwarp();
             }
-            if (lane == 0) wk_gamma += (unsigned long long)di;
             if (kWrite) {
                 // B, C, DT of this edge for the finishing kernel
                 unsigned long long *dst = p.tsum + (int64_t)q * 3 * L2;
@@ -502,28 +523,21 @@ __global__ void __launch_bounds__(kTsumLightWarps * 32) k_cyc_tsum_light(EdgePar
             const int2 ab = p.edges[e];
             const int i = max(ab.x, ab.y);
             const int64_t bi = rowptr[i];
-            const int di = (int)(rowptr[i + 1] - bi);
             for (int x = lane; x < 3 * L2; x += 32) Bm[x] = 0ull;
             __syncwarp();
-            for (int c0 = 0; c0 < di; c0 += 32) {
-                const int x = c0 + lane;
-                bool isT = false;
-                uint32_t w = 0, eiy = 0, ejy = 0;
-                if (x < di) {
-                    w = __ldg(adj + bi + x);
-                    const uint32_t id = w & TG_IDMASK;
-                    if ((int)id != j) {
-                        ejy = hmap_get(hk, hv, TG_LIGHT_LG, id);
-                        isT = ejy != 0xffffffffu;
-                        if (isT) eiy = __ldg(p.eid + bi + x);
-                    }
-                }
-                tsum_chunk(p, isT, w, eiy, ejy, Bm, Cm, Dm);
-                const unsigned tb = __ballot_sync(kFull, isT);
-                if (lane == 0) wk_t += (unsigned long long)__popc(tb);
-            }
+            auto find = [&](uint32_t w, uint32_t &ejy) -> bool {
+                const uint32_t id = w & TG_IDMASK;
+                if ((int)id == j) return false;
+                ejy = hmap_get(hk, hv, TG_LIGHT_LG, id);
+                return ejy != 0xffffffffu;
+            };
+            unsigned long long rd = 0, nt = 0;
+            tsum_edge(p, e, bi, p.toff + (int64_t)i * (L + 1), find, Bm, Cm, Dm, rd, nt);
             __syncwarp();
-            if (lane == 0) wk_gamma += (unsigned long long)di;
+            if (lane == 0) {
+                wk_gamma += rd;
+                wk_t += nt;
+            }
             unsigned long long *dst = p.tsum + (int64_t)q * 3 * L2;
             for (int x = lane; x < 3 * L2; x += 32) dst[x] = Bm[x];
             __syncwarp();

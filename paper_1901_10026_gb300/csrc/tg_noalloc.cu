@@ -214,8 +214,13 @@ __global__ void k_noalloc_finalize(unsigned long long *sums, uint64_t *out, int6
 std::mutex g_na_mu;
 void *g_na_ptr[kNaMaxDevices] = {nullptr};
 
-// Device address of the scratch array on the current device (set up once per
-// device, with that device current).
+// Device address of the scratch array on the current device, set up once per
+// device with that device current.  The set-up also loads the two kernels:
+// under the CUDA runtime's lazy module loading, the driver places a module's
+// code and its __device__ arrays on a device when they are first used there,
+// so this first call is where the driver itself may take device memory; later
+// calls take none.  The cached address belongs to the device's primary
+// context: resetting the device between calls is not supported.
 int scratch_address(unsigned long long **out) {
     int dev = 0;
     TG_TRY_CUDA(cudaGetDevice(&dev));
@@ -225,9 +230,14 @@ int scratch_address(unsigned long long **out) {
         void *ptr = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess || !ptr) {
+            tg_note_cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
             (void)cudaGetLastError();
             return TG_ECUDA;
         }
+        cudaFuncAttributes fa{};
+        TG_TRY_CUDA(cudaFuncGetAttributes(&fa, (const void *)k_noalloc_count));
+        TG_TRY_CUDA(cudaFuncGetAttributes(&fa, (const void *)k_noalloc_finalize));
+        TG_TRY(tg_allow_max_smem((const void *)k_noalloc_count));
         g_na_ptr[dev] = ptr;
     }
     *out = static_cast<unsigned long long *>(g_na_ptr[dev]);

@@ -3,6 +3,8 @@
 // All kernels here are this library's own; no vendor sort or scan is used.
 #include <atomic>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "tg_internal.cuh"
 
@@ -37,15 +39,27 @@ int tg_smem_optin() {
     return v > 0 ? v : 48 * 1024;
 }
 
+// (device, kernel) pairs whose limit is already raised: the attribute is set
+// once per kernel and device, not before every launch.
+static std::mutex g_smem_mu;
+static std::vector<std::pair<int, const void *>> g_smem_done;
+
 int tg_allow_max_smem(const void *func) {
     int dev = 0, optin = 0;
     TG_TRY_CUDA(cudaGetDevice(&dev));
+    {
+        std::lock_guard<std::mutex> lk(g_smem_mu);
+        for (const auto &d : g_smem_done)
+            if (d.first == dev && d.second == func) return TG_OK;
+    }
     TG_TRY_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     cudaFuncAttributes fa{};
     TG_TRY_CUDA(cudaFuncGetAttributes(&fa, func));
     const int v = optin - (int)fa.sharedSizeBytes;
     if (v <= 0) return TG_EINVAL;
     TG_TRY_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    g_smem_done.emplace_back(dev, func);
     return TG_OK;
 }
 

@@ -50,6 +50,24 @@ def test_noalloc_matches_count_global_twice(k):
             tg.tg_debug_fail_alloc(0)
 
 
+def test_noalloc_takes_no_device_memory_after_its_first_call():
+    """The device's free memory is the same before and after repeated calls
+    (the first call on the device, which may load the module, came before)."""
+    import torch
+    G = synth.er_1000(seed=1)
+    g = tg.tg_build_csr(G.n, G.src, G.dst, G.types, G.L)
+    out = torch.zeros(tg.tg_global_len(G.L, 4), dtype=torch.int64, device="cuda:0")
+    tg.tg_count_global_noalloc(g, 4, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(0)
+    for _ in range(3):
+        tg.tg_count_global_noalloc(g, 4, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(0)
+    assert free1 == free0
+    assert np.array_equal(out.cpu().numpy().view(np.uint64), tg.tg_count_global(g, 4))
+
+
 def test_noalloc_rejects_oversized_histograms():
     G = synth.tiny_random(40, 0.2, 10, synth.rng(992))  # k = 4 at L = 10 exceeds the array
     g = tg.tg_build_csr(G.n, G.src, G.dst, G.types, G.L)
