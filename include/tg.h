@@ -290,6 +290,11 @@ typedef struct {
                             when they fit in a quarter of free memory, else
                             runs the fused kernel; TG_EDGE_PASS_FUSED always
                             runs the fused kernel                           */
+    int32_t edge_batch;  /* CYCLES kernel, k = 4: most edges whose T sums are
+                            held in memory at once (the per-edge pass runs in
+                            batches of work units); 0: as many as fit in a
+                            quarter of free memory                          */
+    int32_t reserved;
 } tg_tune;
 
 #define TG_EDGE_PASS_AUTO 0

@@ -55,7 +55,8 @@ class TGError(RuntimeError):
 class TGTune(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("cta_threads", ctypes.c_int32), ("unroll", ctypes.c_int32),
                 ("hash_slots", ctypes.c_int32), ("bitmap_bits", ctypes.c_int64),
-                ("grid_limit", ctypes.c_int32), ("edge_pass", ctypes.c_int32)]
+                ("grid_limit", ctypes.c_int32), ("edge_pass", ctypes.c_int32),
+                ("edge_batch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class TGTiming(ctypes.Structure):
@@ -357,7 +358,7 @@ class Batch:
         self._graphs, self._outs = list(graphs), list(outs)
         G, hs, ps = _handles(self._graphs, self._outs)
         self._keep = (hs, ps)
-        tune = TGTune(0, cta_threads, 0, 0, 0, 0, 0) if cta_threads else None
+        tune = TGTune(0, cta_threads, 0, 0, 0, 0, 0, 0, 0) if cta_threads else None
         h = ctypes.c_void_p()
         _check(lib().tg_batch_create(G, hs, k, mode, ps, ctypes.byref(tune) if tune else None,
                                      _stream(stream), ctypes.byref(h)), "tg_batch_create")
@@ -386,7 +387,7 @@ class Batch:
 def tg_count_batch(graphs, k, mode, outs, cta_threads=0, stream=None):
     """One-shot batched count (autotuned unless ``cta_threads`` is given)."""
     G, hs, ps = _handles(list(graphs), list(outs))
-    tune = TGTune(0, cta_threads, 0, 0, 0, 0, 0) if cta_threads else None
+    tune = TGTune(0, cta_threads, 0, 0, 0, 0, 0, 0, 0) if cta_threads else None
     _check(lib().tg_count_batch(G, hs, k, mode, ps, ctypes.byref(tune) if tune else None,
                                 _stream(stream)), "tg_count_batch")
     return outs
@@ -473,12 +474,12 @@ def tg_work_model(g: Graph, stream=None) -> int:
 
 
 def tg_set_tune(kernel=0, cta_threads=0, unroll=0, hash_slots=0, bitmap_bits=0, grid_limit=0,
-                edge_pass=0, reset=False) -> None:
+                edge_pass=0, edge_batch=0, reset=False) -> None:
     """Set the counting kernels' launch configuration (``reset`` restores defaults)."""
     if reset:
         _check(lib().tg_set_tune(None), "tg_set_tune")
         return
-    t = TGTune(kernel, cta_threads, unroll, hash_slots, bitmap_bits, grid_limit, edge_pass)
+    t = TGTune(kernel, cta_threads, unroll, hash_slots, bitmap_bits, grid_limit, edge_pass, edge_batch, 0)
     _check(lib().tg_set_tune(ctypes.byref(t)), "tg_set_tune")
 
 

@@ -855,7 +855,7 @@ inline unsigned grid_for(int64_t n, int threads = 256) {
 // ----------------------------------------------------------- schedule -----
 // ------------------------------------------------------------- tuning -----
 static std::mutex g_tune_mu;
-static tg_tune g_tune = {TG_KERNEL_AUTO, 1024, 2, 4096, 0, 0, 0};
+static tg_tune g_tune = {TG_KERNEL_AUTO, 1024, 2, 4096, 0, 0, 0, 0, 0};
 
 static tg_tune tune_now() {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -863,7 +863,7 @@ static tg_tune tune_now() {
 }
 
 extern "C" int tg_set_tune(const tg_tune *t) {
-    tg_tune d = {TG_KERNEL_AUTO, 1024, 2, 4096, 0, 0, 0};
+    tg_tune d = {TG_KERNEL_AUTO, 1024, 2, 4096, 0, 0, 0, 0, 0};
     if (t) {
         if (t->kernel < 0 || t->kernel > TG_KERNEL_CYCLES) return TG_EINVAL;
         if (t->cta_threads && (t->cta_threads < 32 || t->cta_threads > 1024 || t->cta_threads % 32))
@@ -874,6 +874,7 @@ extern "C" int tg_set_tune(const tg_tune *t) {
         if (t->bitmap_bits < 0 || t->grid_limit < 0) return TG_EINVAL;
         if (t->edge_pass != TG_EDGE_PASS_AUTO && t->edge_pass != TG_EDGE_PASS_FUSED)
             return TG_EINVAL;
+        if (t->edge_batch < 0) return TG_EINVAL;
         d.kernel = t->kernel;
         if (t->cta_threads) d.cta_threads = t->cta_threads;
         if (t->unroll) d.unroll = t->unroll;
@@ -881,6 +882,7 @@ extern "C" int tg_set_tune(const tg_tune *t) {
         d.bitmap_bits = t->bitmap_bits;
         d.grid_limit = t->grid_limit;
         d.edge_pass = t->edge_pass;
+        d.edge_batch = t->edge_batch;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune = d;

@@ -729,7 +729,6 @@ constexpr int kC4WalkWarps = 8;
 
 __global__ void __launch_bounds__(kC4WalkWarps * 32) k_c4_walk(C4Params p) {
     const int lane = threadIdx.x & 31;
-    const int L = p.L;
     unsigned long long wk = 0;
     for (;;) {
         unsigned long long item = 0;
@@ -770,6 +769,355 @@ __global__ void __launch_bounds__(kC4WalkWarps * 32) k_c4_walk(C4Params p) {
         for (int o = 16; o > 0; o >>= 1) wk += __shfl_xor_sync(kFull, wk, o);
         if (lane == 0 && wk) atomicAdd(p.work + 4, wk);
     }
+}
+
+// One count into the histogram under the sorted multiset {a, b, c, d}.
+__device__ __forceinline__ void k4_hist_add(unsigned long long *h4, int a, int b, int c, int d,
+                                            unsigned long long v) {
+    sort2(a, b);
+    sort2(c, d);
+    sort2(a, c);
+    sort2(b, d);
+    sort2(b, c);
+    atomicAdd(h4 + colex4(a, b, c, d), v);
+}
+
+// ------------------------------------------------- binned waves (global) --
+// Anchors whose walk is long against the number of far-end windows it spans
+// (hubs): the counters stay on chip.  Every wedge a-u-b of a wave's walks
+// becomes the 16-bit entry (b mod 2^wlg) | (type of u) << wlg in the bucket of
+// (anchor, b >> wlg).  A count pass sizes the buckets and a fill pass writes
+// them, each with one counter add per distinct bucket among a warp's 32
+// wedges (a member's list is sorted by (type, id), so neighbouring wedges
+// mostly share a window).  k_c4_bin_pairs then gives each bucket to a CTA,
+// which counts its entries by (b, t) in a dense shared-memory table of the
+// window's 2^wlg far ends and adds each far end's cycle pairs to the
+// type-multiset histogram (c4_add).  DRAM sees the walk twice and 2 bytes
+// per wedge written and read once, instead of a counter read and write per
+// wedge.
+struct C4Bin {
+    const int64_t *rowptr;
+    const uint32_t *adj;
+    const uint8_t *ntype;
+    int32_t L, wlg, half;
+    const uint32_t *heavy;     // the binned anchors
+    const int64_t *mprefix;    // walk positions of their members (k_c4_prefix)
+    const int64_t *pbase;
+    const C4Unit *units;       // warp units of the wave
+    int64_t n_units;
+    int64_t q0;                // first anchor of the wave (bucket row = q - q0)
+    int64_t n;                 // nodes
+    int64_t W;                 // far-end windows, ceil(n / 2^wlg)
+    uint32_t *cnt;             // K W bucket sizes (count pass), write cursors (fill pass)
+    uint16_t *bins;            // the wave's entries, bucket after bucket
+    const uint32_t *offs;      // K W + 1 bucket offsets
+    int64_t nb;                // buckets of the wave, K W
+    unsigned long long *queue;
+    unsigned long long *g4;
+    int64_t n4;
+    unsigned long long *work;  // [4]: wedges
+};
+
+constexpr int kBinUnroll = 4;
+constexpr int kBinFill = 32;            // binned when a walk averages this many wedges per window
+constexpr size_t kBinTable = 64 * 1024;  // bytes of the dense far-end table
+
+// One chunk of 32 members (lane values len, bu, tu) of a binned walk unit; as
+// c4_chunk, with kBinUnroll batches of 32 positions per step.  Count pass:
+// adds each batch's wedges to their buckets' sizes.  Fill pass: takes a run
+// of slots from each bucket's cursor and writes the entries.
+template <bool kFill, class IT>
+__device__ __forceinline__ int64_t c4_chunk_bin(const C4Bin &p, uint32_t a, uint32_t *cb,
+                                                int64_t len64, int64_t bu, int tu, int64_t at,
+                                                int64_t f_lo, int64_t f_hi,
+                                                unsigned long long &wk) {
+    const int lane = threadIdx.x & 31;
+    const IT len = (IT)len64;
+    IT incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const IT y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const IT total = __shfl_sync(kFull, incl, 31);
+    const IT lo = (IT)(f_lo > at ? (f_lo - at < (int64_t)total ? f_lo - at : (int64_t)total) : 0);
+    const IT hi = (IT)(f_hi - at < (int64_t)total ? f_hi - at : (int64_t)total);
+    const uint32_t wmask = (1u << p.wlg) - 1u;
+    for (IT b0 = lo; b0 < hi; b0 += 32 * kBinUnroll) {
+        uint32_t bv[kBinUnroll], base[kBinUnroll];
+        int tv[kBinUnroll];
+        unsigned mm[kBinUnroll];
+        bool ok[kBinUnroll];
+#pragma unroll
+        for (int q = 0; q < kBinUnroll; ++q) {
+            const IT pos = b0 + 32 * q + lane;
+            int r = 0;  // the first member whose running sum exceeds pos
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const IT v = __shfl_sync(kFull, incl, r + st - 1);
+                if (v <= pos) r += st;
+            }
+            const int64_t bur = __shfl_sync(kFull, bu, r);
+            const IT str = __shfl_sync(kFull, incl - len, r);
+            const int tur = __shfl_sync(kFull, tu, r);
+            ok[q] = false;
+            bv[q] = 0;
+            tv[q] = 0;
+            if (pos < hi) {
+                const uint32_t b = __ldg(p.adj + bur + (int64_t)(pos - str)) & TG_IDMASK;
+                if (b > a) {
+                    ok[q] = true;
+                    bv[q] = b;
+                    tv[q] = tur;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kBinUnroll; ++q) {
+            const int key = ok[q] ? (int)(bv[q] >> p.wlg) : -1;
+            mm[q] = __match_any_sync(kFull, key);
+            base[q] = 0u;
+            if (ok[q] && lane == __ffs(mm[q]) - 1) {
+                if (kFill)
+                    base[q] = atomicAdd(cb + key, (uint32_t)__popc(mm[q]));
+                else
+                    atomicAdd(cb + key, (uint32_t)__popc(mm[q]));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kBinUnroll; ++q) {
+            if (kFill) {
+                const uint32_t bb = __shfl_sync(kFull, base[q], __ffs(mm[q]) - 1);
+                if (ok[q])
+                    p.bins[bb + (uint32_t)__popc(mm[q] & ((1u << lane) - 1u))] =
+                        (uint16_t)((bv[q] & wmask) | ((uint32_t)tv[q] << p.wlg));
+            } else if (ok[q]) {
+                ++wk;
+            }
+        }
+    }
+    return (int64_t)total;
+}
+
+// The count (kFill = false) or fill pass of a binned wave: one warp per unit.
+template <bool kFill>
+__global__ void __launch_bounds__(kC4WalkWarps * 32) k_c4_bin_walk(C4Bin p) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long wk = 0;
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(p.queue, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= (unsigned long long)p.n_units) break;
+        const C4Unit un = p.units[item];
+        const uint32_t a = p.heavy[un.q];
+        const int64_t ba = p.rowptr[a];
+        const int da = (int)(p.rowptr[a + 1] - ba);
+        uint32_t *cb = p.cnt + (un.q - p.q0) * p.W;
+        int64_t at = p.mprefix[p.pbase[un.q] + un.m];
+        for (int m = un.m; m < da && at < un.hi; m += 32) {
+            const int x = m + lane;
+            int64_t len = 0, bu = 0;
+            int tu = 0;
+            if (x < da) {
+                const uint32_t wu = __ldg(p.adj + ba + x);
+                const uint32_t u = wu & TG_IDMASK;
+                if (u > a) {
+                    bu = p.rowptr[u];
+                    const int64_t du = p.rowptr[u + 1] - bu;
+                    if (du > 1) {
+                        len = du;
+                        tu = (int)(wu >> TG_TSHIFT);
+                    }
+                }
+            }
+            if (__all_sync(kFull, len < ((int64_t)1 << 26)))
+                at += c4_chunk_bin<kFill, int>(p, a, cb, len, bu, tu, at, un.lo, un.hi, wk);
+            else
+                at += c4_chunk_bin<kFill, int64_t>(p, a, cb, len, bu, tu, at, un.lo, un.hi, wk);
+        }
+    }
+    if (!kFill && p.work) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wk += __shfl_xor_sync(kFull, wk, o);
+        if (lane == 0 && wk) atomicAdd(p.work + 4, wk);
+    }
+}
+
+// The buckets of a binned wave.  A CTA takes runs of kBinRun consecutive
+// buckets (consecutive windows of one anchor, mostly) from a queue.  A bucket
+// (anchor a of type ta, window w) has its entries counted by (b, t) in the
+// dense table (16-bit halves when the wave's anchors have fewer than 2^16
+// neighbours, else 32-bit counts), far ends marked on first touch in a
+// bitmap.  Then each warp takes bitmap words; for every marked far end b with
+// two or more middles, lane x of the warp adds, for its type pairs (t, t')
+// (pairs x and x + 32), C(c_t, 2) or c_t c_t' to its warp's table
+// acc[type of b][pair] in shared memory (a lane writes only its own
+// columns: no atomics, no conflicts), and the far end's counts and mark are
+// cleared.  The tables go into the histogram under {ta, tb, t, t'} when the
+// anchor changes.  Types beyond kBinAccL use c4_add straight into a shared
+// histogram instead.
+constexpr int kBinPairThreads = 256;
+constexpr int kBinRun = 16;
+constexpr int kBinAccL = 8;
+
+__device__ __forceinline__ void bin_flush(unsigned long long *acc, unsigned long long *h4, int L,
+                                          int P, int ta) {
+    const int lane = threadIdx.x & 31;
+    for (int k = lane; k < L * P; k += 32) {
+        const unsigned long long v = acc[k];
+        if (!v) continue;
+        acc[k] = 0ull;
+        int t, u;
+        unpair(L, k % P, t, u);
+        k4_hist_add(h4, ta, k / P, t, u, v);
+    }
+}
+
+__global__ void __launch_bounds__(kBinPairThreads) k_c4_bin_pairs(C4Bin p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = kBinPairThreads / 32;
+    const int L = p.L, Lp = L + (L & 1), P = L * (L + 1) / 2;
+    const bool acc_mode = L <= kBinAccL;
+    const int nfar = 1 << p.wlg;
+    unsigned long long *h4 = reinterpret_cast<unsigned long long *>(smem);
+    size_t off = ((size_t)p.n4 * 8 + 15) & ~(size_t)15;
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(smem + off) + (size_t)warp * L * P;
+    if (acc_mode) off += (size_t)NW * L * P * 8;
+    uint32_t *tab = reinterpret_cast<uint32_t *>(smem + off);
+    const int twords = p.half ? nfar * (Lp >> 1) : nfar * L;
+    uint32_t *tbits = tab + twords;  // nfar / 32 words
+    const volatile uint32_t *vtab = tab;
+    const volatile uint32_t *vbits = tbits;
+    __shared__ unsigned long long s_run;
+    for (int64_t q = tid; q < p.n4; q += blockDim.x) h4[q] = 0ull;
+    if (acc_mode)
+        for (int q = lane; q < L * P; q += 32) acc[q] = 0ull;
+    for (int q = tid; q < twords + nfar / 32; q += blockDim.x) tab[q] = 0u;
+    // this lane's type pairs (pair lane and lane + 32)
+    int pt[2], pu[2];
+    for (int r = 0; r < 2; ++r) {
+        pt[r] = pu[r] = -1;
+        if (acc_mode && lane + 32 * r < P) unpair(L, lane + 32 * r, pt[r], pu[r]);
+    }
+    const uint32_t wmask = (uint32_t)nfar - 1u;
+    int cur_ta = -1;
+    int64_t cur_row = -1;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_run = atomicAdd(p.queue, (unsigned long long)kBinRun);
+        __syncthreads();
+        const int64_t r0 = (int64_t)s_run;
+        if (r0 >= p.nb) break;
+        const int64_t r1 = r0 + kBinRun < p.nb ? r0 + kBinRun : p.nb;
+        for (int64_t item = r0; item < r1; ++item) {
+            const uint32_t c0 = p.offs[item], c1 = p.offs[item + 1];
+            if (c0 == c1) continue;  // uniform across the CTA
+            const int64_t row = item / p.W;
+            const int64_t wbase = (item % p.W) << p.wlg;
+            if (row != cur_row) {
+                if (acc_mode && cur_ta >= 0) bin_flush(acc, h4, L, P, cur_ta);
+                cur_row = row;
+                cur_ta = p.ntype[p.heavy[p.q0 + row]];
+            }
+            const int ta = cur_ta;
+            for (uint32_t k = c0 + tid; k < c1; k += blockDim.x) {
+                const uint32_t e = p.bins[k];
+                const uint32_t bl = e & wmask;
+                const int t = (int)(e >> p.wlg);
+                bool first;
+                if (p.half) {
+                    const uint32_t idx = bl * (uint32_t)Lp + (uint32_t)t;
+                    const int sh = (int)(idx & 1u) * 16;
+                    const uint32_t old = atomicAdd(tab + (idx >> 1), 1u << sh);
+                    first = ((old >> sh) & 0xffffu) == 0u;
+                } else {
+                    first = atomicAdd(tab + bl * (uint32_t)L + (uint32_t)t, 1u) == 0u;
+                }
+                if (first) atomicOr(tbits + (bl >> 5), 1u << (bl & 31u));
+            }
+            __syncthreads();
+            for (int wd = warp; wd < nfar / 32; wd += NW) {
+                const uint32_t bits = vbits[wd];
+                if (!bits) continue;
+                // lane x holds far end 32 wd + x: its counts and their sum
+                const uint32_t bl = (uint32_t)(wd * 32 + lane);
+                const bool mine = (bits >> lane) & 1u;
+                uint32_t c[TG_MAX_TYPES];
+                uint32_t sum = 0;
+                if (mine) {
+                    if (p.half) {
+                        const uint32_t w0 = bl * (uint32_t)(Lp >> 1);
+                        for (int q = 0; q < (Lp >> 1); ++q) {
+                            const uint32_t w = vtab[w0 + q];
+                            c[2 * q] = w & 0xffffu;
+                            if (2 * q + 1 < L) c[2 * q + 1] = w >> 16;
+                            sum += (w & 0xffffu) + (w >> 16);
+                        }
+                    } else {
+                        for (int t = 0; t < L; ++t) {
+                            c[t] = vtab[bl * (uint32_t)L + t];
+                            sum += c[t];
+                        }
+                    }
+                }
+                const int tb = mine ? (int)p.ntype[wbase + bl] : 0;
+                if (!acc_mode) {
+                    if (mine && sum > 1) c4_add(h4, L, ta, tb, c);
+                } else {
+                    // far ends with two or more middles, one at a time across the warp
+                    for (unsigned m = __ballot_sync(kFull, mine && sum > 1); m; m &= m - 1u) {
+                        const int src = __ffs(m) - 1;
+                        const uint32_t bs = (uint32_t)(wd * 32 + src);
+                        const int tbs = __shfl_sync(kFull, tb, src);
+                        unsigned long long *ar = acc + (size_t)tbs * P;
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+                            if (pt[r] < 0) continue;
+                            const unsigned long long ct = p.half
+                                ? (vtab[(bs * (uint32_t)Lp + (uint32_t)pt[r]) >> 1] >>
+                                   (((bs * (uint32_t)Lp + (uint32_t)pt[r]) & 1u) * 16)) & 0xffffu
+                                : vtab[bs * (uint32_t)L + (uint32_t)pt[r]];
+                            if (!ct) continue;
+                            unsigned long long v;
+                            if (pt[r] == pu[r]) {
+                                v = ct * (ct - 1) / 2;
+                            } else {
+                                const unsigned long long cu = p.half
+                                    ? (vtab[(bs * (uint32_t)Lp + (uint32_t)pu[r]) >> 1] >>
+                                       (((bs * (uint32_t)Lp + (uint32_t)pu[r]) & 1u) * 16)) & 0xffffu
+                                    : vtab[bs * (uint32_t)L + (uint32_t)pu[r]];
+                                v = ct * cu;
+                            }
+                            ar[lane + 32 * r] += v;
+                        }
+                    }
+                }
+                __syncwarp();
+                // clear this word's far ends
+                if (mine) {
+                    if (p.half) {
+                        for (int q = 0; q < (Lp >> 1); ++q) tab[bl * (uint32_t)(Lp >> 1) + q] = 0u;
+                    } else {
+                        for (int t = 0; t < L; ++t) tab[bl * (uint32_t)L + t] = 0u;
+                    }
+                }
+                if (lane == 0) tbits[wd] = 0u;
+            }
+            __syncthreads();
+        }
+    }
+    if (acc_mode && cur_ta >= 0) bin_flush(acc, h4, L, P, cur_ta);
+    __syncthreads();
+    for (int64_t q = tid; q < p.n4; q += blockDim.x)
+        if (h4[q]) atomicAdd(p.g4 + q, h4[q]);
+}
+
+__global__ void k_gather_u64(const unsigned long long *x, const uint32_t *idx, int64_t n,
+                             unsigned long long *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = x[idx[i]];
 }
 
 // ------------------------------------------------- light anchors (global) --
@@ -1474,15 +1822,6 @@ __device__ __forceinline__ uint32_t range_mask(int lo, int hi) {  // bits [lo, h
     return h & ~l;
 }
 
-__device__ __forceinline__ void k4_hist_add(unsigned long long *h4, int a, int b, int c, int d,
-                                            unsigned long long v) {
-    sort2(a, b);
-    sort2(c, d);
-    sort2(a, c);
-    sort2(b, d);
-    sort2(b, c);
-    atomicAdd(h4 + colex4(a, b, c, d), v);
-}
 
 __global__ void __launch_bounds__(kBitsWarps * 32) k_k4_bits_warp(K4GParams p) {
     __shared__ uint32_t hk[kBitsWarps][2 * kBitsWarpMax], hv[kBitsWarps][2 * kBitsWarpMax];
@@ -1880,6 +2219,159 @@ int c4_walk_waves(const C4Params &p, const tg_graph *g, const uint32_t *list, in
     return TG_OK;
 }
 
+// Window bits of the binned waves: the largest window whose dense table
+// (16-bit counts when half, else 32-bit) fits kBinTable bytes, with room for
+// the type in a 16-bit entry.
+int c4_bin_wlg(int L, int half) {
+    const int Lp = L + (L & 1);
+    const size_t per = half ? (size_t)Lp * 2 : (size_t)L * 4;
+    int tbits = 1;
+    while ((1 << tbits) < L) ++tbits;
+    int wlg = 5;
+    while (wlg < 16 - tbits && ((size_t)1 << (wlg + 1)) * per <= kBinTable) ++wlg;
+    return wlg;
+}
+
+// Global-mode binned waves of the anchors list[0 .. na) (degrees hdeg): walk
+// positions per anchor (k_c4_prefix), warp units (k_c4_units), then per wave
+// (anchors of one counter width, at most `ecap` walk positions in all) the
+// count pass, the bucket offsets, the fill pass and the bucket pairs.
+int c4_bin_waves(const tg_graph *g, const uint32_t *list, int64_t na,
+                 const std::vector<int64_t> &hdeg, int64_t n4, unsigned long long *g4,
+                 unsigned long long *work, int64_t ecap, cudaStream_t s) {
+    const int L = g->L;
+    const int64_t n = g->n;
+    std::vector<int64_t> pb((size_t)na + 1, 0);
+    for (int64_t q = 0; q < na; ++q) pb[q + 1] = pb[q] + hdeg[q];
+    DevBuf<int64_t> dpb, dmp;
+    DevBuf<unsigned long long> dtot;
+    if (!dpb.alloc(na + 1, s) || !dmp.alloc(pb[na], s) || !dtot.alloc(na, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemcpyAsync(dpb.p, pb.data(), (na + 1) * 8, cudaMemcpyHostToDevice, s));
+    k_c4_prefix<<<(unsigned)na, 256, 0, s>>>(list, dpb.p, g->rowptr, g->adj, dmp.p, dtot.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    std::vector<unsigned long long> tot_h((size_t)na);
+    TG_TRY_CUDA(cudaMemcpyAsync(tot_h.data(), dtot.p, na * 8, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    int wper = 0;
+    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wper, k_c4_bin_walk<false>,
+                                                              kC4WalkWarps * 32, 0));
+    if (wper < 1) wper = 1;
+    const int64_t walk_grid = (int64_t)tg_num_sms() * wper;
+    const int64_t warps = walk_grid * kC4WalkWarps;
+    // waves: consecutive anchors of one counter width, within ecap positions
+    // and 2^22 buckets
+    std::vector<int64_t> wq0, wq1;
+    std::vector<int> whalf;
+    int64_t wmax = 0;
+    for (int64_t q = 0; q < na;) {
+        const int half = hdeg[q] < 65536 ? 1 : 0;
+        const int64_t W = (n + ((int64_t)1 << c4_bin_wlg(L, half)) - 1) >> c4_bin_wlg(L, half);
+        int64_t e = q + 1;
+        unsigned long long tot = tot_h[q];
+        while (e < na && (hdeg[e] < 65536 ? 1 : 0) == half && tot + tot_h[e] <= (unsigned long long)ecap &&
+               (e - q + 1) * W <= ((int64_t)1 << 22)) {
+            tot += tot_h[e];
+            ++e;
+        }
+        wq0.push_back(q);
+        wq1.push_back(e);
+        whalf.push_back(half);
+        wmax = std::max<int64_t>(wmax, (e - q) * W);
+        q = e;
+    }
+    const int64_t nwaves = (int64_t)wq0.size();
+    std::vector<int64_t> us((size_t)na + 1, 0), tg((size_t)na, 1);
+    unsigned long long wtmax = 0;
+    for (int64_t w = 0; w < nwaves; ++w) {
+        unsigned long long wt = 0;
+        for (int64_t q = wq0[w]; q < wq1[w]; ++q) wt += tot_h[q];
+        wtmax = std::max(wtmax, wt);
+        const int64_t tgt =
+            std::max<int64_t>(kWalkUnitMin, (int64_t)((wt + 4 * warps - 1) / (4 * warps)));
+        for (int64_t q = wq0[w]; q < wq1[w]; ++q) {
+            tg[q] = tgt;
+            us[q + 1] = us[q] + (int64_t)((tot_h[q] + tgt - 1) / tgt);
+        }
+    }
+    const int64_t nunits = us[na];
+    DevBuf<int64_t> dus, dtg;
+    DevBuf<C4Unit> dun;
+    DevBuf<unsigned long long> dq;
+    DevBuf<uint32_t> cnt, offs;
+    DevBuf<uint16_t> bins;
+    if (!dus.alloc(na + 1, s) || !dtg.alloc(na, s) || !dun.alloc(nunits ? nunits : 1, s) ||
+        !dq.alloc(3 * nwaves, s) || !cnt.alloc(wmax + 1, s) || !offs.alloc(wmax + 1, s) ||
+        !bins.alloc(wtmax ? wtmax : 1, s))
+        return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemcpyAsync(dus.p, us.data(), (na + 1) * 8, cudaMemcpyHostToDevice, s));
+    TG_TRY_CUDA(cudaMemcpyAsync(dtg.p, tg.data(), na * 8, cudaMemcpyHostToDevice, s));
+    TG_TRY_CUDA(cudaMemsetAsync(dq.p, 0, 3 * nwaves * 8, s));
+    if (nunits > 0) {
+        const unsigned ug = (unsigned)std::min<int64_t>((nunits + 255) / 256, 65535LL * 16);
+        k_c4_units<<<ug, 256, 0, s>>>(dus.p, na, dtg.p, dtot.p, dmp.p, dpb.p, list, g->rowptr,
+                                      dun.p); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
+    C4Bin pb0{};
+    pb0.rowptr = g->rowptr;
+    pb0.adj = g->adj;
+    pb0.ntype = g->ntype;
+    pb0.L = L;
+    pb0.n = n;
+    pb0.heavy = list;
+    pb0.mprefix = dmp.p;
+    pb0.pbase = dpb.p;
+    pb0.cnt = cnt.p;
+    pb0.bins = bins.p;
+    pb0.offs = offs.p;
+    pb0.g4 = g4;
+    pb0.n4 = n4;
+    pb0.work = work;
+    TG_TRY(tg_allow_max_smem((const void *)k_c4_bin_pairs));
+    for (int64_t w = 0; w < nwaves; ++w) {
+        const int64_t q0 = wq0[w], q1 = wq1[w];
+        C4Bin pw = pb0;
+        pw.half = whalf[w];
+        pw.wlg = c4_bin_wlg(L, pw.half);
+        pw.W = (n + ((int64_t)1 << pw.wlg) - 1) >> pw.wlg;
+        pw.q0 = q0;
+        pw.nb = (q1 - q0) * pw.W;
+        pw.units = dun.p + us[q0];
+        pw.n_units = us[q1] - us[q0];
+        if (pw.n_units == 0) continue;
+        const int64_t need = (pw.n_units + kC4WalkWarps - 1) / kC4WalkWarps;
+        const int64_t grid = std::min<int64_t>(walk_grid, need);
+        // bucket sizes, then offsets (one more entry, zero, takes the total)
+        TG_TRY_CUDA(cudaMemsetAsync(cnt.p, 0, (pw.nb + 1) * 4, s));
+        pw.queue = dq.p + 3 * w;
+        k_c4_bin_walk<false><<<(unsigned)grid, kC4WalkWarps * 32, 0, s>>>(pw); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+        TG_TRY(tg_scan_u32(cnt.p, offs.p, pw.nb + 1, s));
+        TG_TRY_CUDA(cudaMemcpyAsync(cnt.p, offs.p, pw.nb * 4, cudaMemcpyDeviceToDevice, s));
+        pw.queue = dq.p + 3 * w + 1;
+        k_c4_bin_walk<true><<<(unsigned)grid, kC4WalkWarps * 32, 0, s>>>(pw); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+        const int Lp = L + (L & 1);
+        const size_t nfar = (size_t)1 << pw.wlg;
+        const int P = L * (L + 1) / 2;
+        const size_t psmem = (((size_t)n4 * 8 + 15) & ~(size_t)15) +
+                             (L <= kBinAccL ? (size_t)(kBinPairThreads / 32) * L * P * 8 : 0) +
+                             (pw.half ? nfar * (Lp >> 1) : nfar * L) * 4 + nfar / 32 * 4;
+        int pper = 0;
+        TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pper, k_c4_bin_pairs,
+                                                                  kBinPairThreads, psmem));
+        if (pper < 1) pper = 1;
+        const int64_t pgrid =
+            std::min<int64_t>((int64_t)tg_num_sms() * pper, (pw.nb + kBinRun - 1) / kBinRun);
+        pw.queue = dq.p + 3 * w + 2;
+        k_c4_bin_pairs<<<(unsigned)pgrid, kBinPairThreads, psmem, s>>>(pw); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
+    // the host vectors are read by the copies above before they go out of scope
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    return TG_OK;
+}
+
 }  // namespace
 
 int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long *g4,
@@ -2023,9 +2515,46 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
 
     if (nheavy > 0 && walk_waves) {
         // global mode: each split anchor's walk is cut into position ranges of
-        // about equal length (warp units of k_c4_walk), in waves of `slots`
-        // anchors; each wave's far ends are taken by k_c4_pairs
-        TG_TRY(c4_walk_waves(p, g, list, nheavy, hdeg, slots, s));
+        // about equal length (warp units); anchors whose walk averages
+        // kBinFill wedges per far-end window they span go to the binned waves,
+        // the others to waves of `slots` anchors counting in global memory,
+        // whose far ends k_c4_pairs takes
+        std::vector<unsigned long long> hcost((size_t)nheavy);
+        {
+            DevBuf<unsigned long long> hc;
+            if (!hc.alloc(nheavy, s)) return TG_ENOMEM;
+            k_gather_u64<<<(unsigned)std::min<int64_t>((nheavy + 255) / 256, 4096), 256, 0, s>>>(
+                cost.p, list, nheavy, hc.p); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+            TG_TRY_CUDA(cudaMemcpyAsync(hcost.data(), hc.p, nheavy * 8, cudaMemcpyDeviceToHost, s));
+            TG_TRY_CUDA(cudaStreamSynchronize(s));
+        }
+        size_t fb = 0, tb = 0;
+        TG_TRY_CUDA(cudaMemGetInfo(&fb, &tb));
+        // bucket entries of one wave: 2 bytes each, within an eighth of free memory
+        const int64_t ecap = std::min<int64_t>((int64_t)1 << 31, (int64_t)(fb / 16));
+        std::vector<uint32_t> lb, ls;
+        std::vector<int64_t> db, ds;
+        for (int64_t q = 0; q < nheavy; ++q) {
+            const int half = hdeg[q] < 65536 ? 1 : 0;
+            const int wlg = c4_bin_wlg(L, half);
+            const int64_t span = ((n - 1) >> wlg) - ((int64_t)heavy[q] >> wlg) + 1;
+            const bool bin = t.unroll != 1 && hcost[q] >= (unsigned long long)(kBinFill * span) &&
+                             hcost[q] <= (unsigned long long)ecap;
+            (bin ? lb : ls).push_back(heavy[q]);
+            (bin ? db : ds).push_back(hdeg[q]);
+        }
+        DevBuf<uint32_t> dlb, dls;
+        if (!dlb.alloc(lb.size() + 1, s) || !dls.alloc(ls.size() + 1, s)) return TG_ENOMEM;
+        if (!lb.empty()) {
+            TG_TRY_CUDA(cudaMemcpyAsync(dlb.p, lb.data(), lb.size() * 4, cudaMemcpyHostToDevice, s));
+            TG_TRY(c4_bin_waves(g, dlb.p, (int64_t)lb.size(), db, n4, g4, work, ecap, s));
+        }
+        if (!ls.empty()) {
+            TG_TRY_CUDA(cudaMemcpyAsync(dls.p, ls.data(), ls.size() * 4, cudaMemcpyHostToDevice, s));
+            TG_TRY(c4_walk_waves(p, g, dls.p, (int64_t)ls.size(), ds, slots, s));
+        }
+        TG_TRY_CUDA(cudaStreamSynchronize(s));
     } else if (nheavy > 0) {
         // member tiles of 'TM' members as units (both passes in per-edge mode)
         PairsConf pc;

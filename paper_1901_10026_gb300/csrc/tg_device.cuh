@@ -63,6 +63,19 @@ __device__ __forceinline__ bool contains(const uint32_t *__restrict__ adj, int64
     return lo < __ldg(to + t + 1) && __ldg(adj + base + lo) == w;
 }
 
+// Edge id of (j, y) when y (packed entry w) is a neighbour of j, else
+// 0xffffffff.  j's list (base bj, length dj, type offsets toj) and y's list
+// are both sorted by (type, id), and (j, y) is one edge: the typed range of
+// the shorter list is searched (w in Gamma_j, or j's packed entry pj in
+// Gamma_y), which for the low-degree nodes beyond a bitmap is a handful of
+// loads instead of a search through a hub's list.
+__device__ __forceinline__ uint32_t edge_to(const int64_t *__restrict__ rowptr,
+                                            const uint32_t *__restrict__ adj,
+                                            const uint32_t *__restrict__ eid,
+                                            const int32_t *__restrict__ toff, int L, int64_t bj,
+                                            int dj, const int32_t *__restrict__ toj, uint32_t pj,
+                                            uint32_t w);
+
 constexpr uint32_t kEmpty = 0xffffffffu;
 constexpr size_t kMiscBytes = 3 * 16 * 4 + 16;     // Tn, Si, Sj, work item
 constexpr size_t kStageBytes = 32 * 17;  // per-warp w_k slots (a multiple of 16 bytes)
@@ -81,6 +94,36 @@ __device__ __forceinline__ int find_pos(const uint32_t *__restrict__ adj, int64_
             hi = mid;
     }
     return (lo < end && __ldg(adj + base + lo) == w) ? lo : -1;
+}
+
+__device__ __forceinline__ uint32_t edge_to(const int64_t *__restrict__ rowptr,
+                                            const uint32_t *__restrict__ adj,
+                                            const uint32_t *__restrict__ eid,
+                                            const int32_t *__restrict__ toff, int L, int64_t bj,
+                                            int dj, const int32_t *__restrict__ toj, uint32_t pj,
+                                            uint32_t w) {
+    const uint32_t y = w & TG_IDMASK;
+    const int64_t by = __ldg(rowptr + y);
+    const int dy = (int)(__ldg(rowptr + y + 1) - by);
+    if (dy < dj) {
+        const int q = find_pos(adj, by, toff + (int64_t)y * (L + 1), pj);
+        return q < 0 ? 0xffffffffu : __ldg(eid + by + q);
+    }
+    const int q = find_pos(adj, bj, toj, w);
+    return q < 0 ? 0xffffffffu : __ldg(eid + bj + q);
+}
+
+// Is y (packed entry w) a neighbour of j?  As edge_to, without the edge id.
+__device__ __forceinline__ bool adjacent(const int64_t *__restrict__ rowptr,
+                                         const uint32_t *__restrict__ adj,
+                                         const int32_t *__restrict__ toff, int L, int64_t bj,
+                                         int dj, const int32_t *__restrict__ toj, uint32_t pj,
+                                         uint32_t w) {
+    const uint32_t y = w & TG_IDMASK;
+    const int64_t by = __ldg(rowptr + y);
+    const int dy = (int)(__ldg(rowptr + y + 1) - by);
+    if (dy < dj) return find_pos(adj, by, toff + (int64_t)y * (L + 1), pj) >= 0;
+    return find_pos(adj, bj, toj, w) >= 0;
 }
 
 // Per-warp hash sets of node ids in shared memory (open addressing, linear

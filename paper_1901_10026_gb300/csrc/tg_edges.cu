@@ -47,7 +47,8 @@ struct EdgeParams {
     int32_t L, P, k, level;
     int64_t nbits;
     uint32_t *emap;            // per CTA, nbits entries: edge id of (j, y) for y in Gamma_j
-    unsigned long long *tsum;  // split mode: per edge id, B, C and DT (3 L^2 uint64)
+    unsigned long long *tsum;  // split mode: B, C and DT (3 L^2 uint64) per order position
+    int64_t qbase;             // split mode: order position of tsum's first row
     unsigned long long *queue;
     uint64_t *rows;
     int64_t width;
@@ -442,6 +443,7 @@ __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc
                 for (int x = lane; x < 3 * L2; x += 32) Bm[x] = 0ull;
                 __syncwarp();
                 // T = Gamma_i n Gamma_j: sums of tau_jy, tau_iy and d_y by types
+                const uint32_t pj = ((uint32_t)tj << TG_TSHIFT) | (uint32_t)j;
                 auto find = [&](uint32_t w, uint32_t &ejy) -> bool {
                     const uint32_t id = w & TG_IDMASK;
                     if ((int)id == j) return false;
@@ -450,10 +452,8 @@ __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc
                         ejy = __ldcg(emap + id);  // written for this j before the barrier
                         return true;
                     }
-                    const int pj = find_pos(adj, bj, toj, w);
-                    if (pj < 0) return false;
-                    ejy = __ldg(p.eid + bj + pj);
-                    return true;
+                    ejy = edge_to(rowptr, adj, p.eid, p.toff, L, bj, dj, toj, pj, w);
+                    return ejy != 0xffffffffu;
                 };
                 unsigned long long rd = 0, nt = 0;
                 tsum_edge(p, e, bi, toi, find, Bm, Cm, Dm, rd, nt);
@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc
             }
             if (kWrite) {
                 // B, C, DT of this edge for the finishing kernel
-                unsigned long long *dst = p.tsum + (int64_t)q * 3 * L2;
+                unsigned long long *dst = p.tsum + ((int64_t)q - p.qbase) * 3 * L2;
                 for (int x = lane; x < 3 * L2; x += 32) dst[x] = Bm[x];
             } else {
                 edge_finish(p, shist, e, i, j, ti, tj, toi, toj, tn, Bm, Cm, Dm, xt);
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(kTsumLightWarps * 32) k_cyc_tsum_light(EdgePar
                 wk_gamma += rd;
                 wk_t += nt;
             }
-            unsigned long long *dst = p.tsum + (int64_t)q * 3 * L2;
+            unsigned long long *dst = p.tsum + ((int64_t)q - p.qbase) * 3 * L2;
             for (int x = lane; x < 3 * L2; x += 32) dst[x] = Bm[x];
             __syncwarp();
         }
@@ -549,7 +549,8 @@ __global__ void __launch_bounds__(kTsumLightWarps * 32) k_cyc_tsum_light(EdgePar
     }
 }
 
-// Warp per edge: B, C, DT from k_cyc_edge<true>, then edge_finish.
+// Warp per edge of the order positions [p.qbase, p.qbase + count): B, C, DT
+// from k_cyc_edge<true> or k_cyc_tsum_light, then edge_finish.
 __global__ void __launch_bounds__(256) k_cyc_finish(EdgeParams p, int64_t count) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -566,11 +567,11 @@ __global__ void __launch_bounds__(256) k_cyc_finish(EdgeParams p, int64_t count)
         __syncthreads();
     }
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5; q < count; q += nw) {
-        const int64_t e = p.order[q];
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + tid) >> 5; r < count; r += nw) {
+        const int64_t e = p.order[p.qbase + r];
         const int2 ab = p.edges[e];
         const int j = min(ab.x, ab.y), i = max(ab.x, ab.y);
-        const unsigned long long *src = p.tsum + q * 3 * L2;
+        const unsigned long long *src = p.tsum + r * 3 * L2;
         for (int x = lane; x < 3 * L2; x += 32) Bm[x] = __ldg(src + x);
         __syncwarp();
         edge_finish(p, shist, e, i, j, p.ntype[i], p.ntype[j], p.toff + (int64_t)i * (L + 1),
@@ -643,11 +644,54 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
     // per warp: B, C, DT; the kernels that finish edges add the term table
     const size_t tbytes = ((size_t)3 * L2 * 8 + 15) & ~(size_t)15;
     const size_t xbytes = tbytes + (size_t)XT_N * L2 * 8;
-    // B, C, DT through memory when they fit in a quarter of free memory
-    const size_t tsum_bytes = (size_t)count * 3 * L2 * 8;
+    // B, C, DT through memory, in batches of work units whose sums fit in a
+    // quarter of free memory; the fused kernel only when forced or when a
+    // single unit would not fit
+    const size_t row_bytes = (size_t)3 * L2 * 8;
     size_t free_b = 0, total_b = 0;
     TG_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const bool split = k == 4 && t.edge_pass != TG_EDGE_PASS_FUSED && tsum_bytes <= free_b / 4;
+    bool split = k == 4 && t.edge_pass != TG_EDGE_PASS_FUSED;
+    int64_t qcap = std::min<int64_t>(count, (int64_t)(free_b / 4 / row_bytes));
+    if (t.edge_batch > 0 && qcap > t.edge_batch) qcap = t.edge_batch;
+    // batches [bu[x], bu[x + 1]) of units, with their heavy and light sub-lists
+    std::vector<uint32_t> bu{0u, un.nunits}, bh{0u, un.nheavy}, bl{0u, un.nlight};
+    if (split && qcap < count) {
+        std::vector<uint32_t> us((size_t)un.nunits + 1), hv((size_t)un.nheavy), lv((size_t)un.nlight);
+        TG_TRY_CUDA(cudaMemcpyAsync(us.data(), un.ustart.p, us.size() * 4, cudaMemcpyDeviceToHost, s));
+        if (un.nheavy)
+            TG_TRY_CUDA(cudaMemcpyAsync(hv.data(), un.heavy.p, hv.size() * 4, cudaMemcpyDeviceToHost, s));
+        if (un.nlight)
+            TG_TRY_CUDA(cudaMemcpyAsync(lv.data(), un.light.p, lv.size() * 4, cudaMemcpyDeviceToHost, s));
+        TG_TRY_CUDA(cudaStreamSynchronize(s));
+        bu.assign(1, 0u);
+        for (uint32_t u0 = 0; u0 < un.nunits;) {
+            uint32_t u1 = u0;
+            while (u1 < un.nunits && (int64_t)us[u1 + 1] - us[u0] <= qcap) ++u1;
+            if (u1 == u0) {  // one unit beyond the cap
+                split = false;
+                break;
+            }
+            bu.push_back(u1);
+            u0 = u1;
+        }
+        if (split) {
+            bh.clear();
+            bl.clear();
+            for (uint32_t x : bu) {
+                bh.push_back((uint32_t)(std::lower_bound(hv.begin(), hv.end(), x) - hv.begin()));
+                bl.push_back((uint32_t)(std::lower_bound(lv.begin(), lv.end(), x) - lv.begin()));
+            }
+        }
+    }
+    std::vector<uint32_t> ustart_h;
+    if (split && bu.size() > 2) {
+        ustart_h.resize(bu.size());
+        for (size_t x = 0; x < bu.size(); ++x)
+            TG_TRY_CUDA(cudaMemcpyAsync(&ustart_h[x], un.ustart.p + bu[x], 4, cudaMemcpyDeviceToHost, s));
+        TG_TRY_CUDA(cudaStreamSynchronize(s));
+    } else {
+        ustart_h = {0u, (uint32_t)count};
+    }
     int threads = t.cta_threads;
     if (threads > (split ? kTsumThreads : kEdgeMaxThreads)) threads = split ? kTsumThreads : kEdgeMaxThreads;
     if (threads < 32) threads = 32;
@@ -667,70 +711,88 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
     p.nbits = nbits;
     const size_t smem = fixed + ((((size_t)((nbits + 31) >> 5)) * 4 + 15) & ~(size_t)15);
     DevBuf<unsigned long long> queue, tsum;
-    if (!queue.alloc(1, s)) return TG_ENOMEM;
-    if (split && !tsum.alloc((size_t)count * 3 * L2, s)) return TG_ENOMEM;
-    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
-    p.queue = queue.p;
+    if (!queue.alloc(2, s)) return TG_ENOMEM;
+    if (split && !tsum.alloc((size_t)(bu.size() > 2 ? qcap : count) * 3 * L2, s)) return TG_ENOMEM;
     p.tsum = tsum.p;
-    // heavy units (all units when fused): one CTA each, Gamma_j bitmap
-    p.ulist = split ? un.heavy.p : nullptr;
-    p.nunits = split ? un.nheavy : un.nunits;
-    if (p.nunits > 0) {
-        const void *kfn = split ? (const void *)k_cyc_edge<true> : (const void *)k_cyc_edge<false>;
-        TG_TRY(tg_allow_max_smem(kfn));
-        int per_sm = 0;
-        TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem));
-        if (per_sm < 1) per_sm = 1;
-        int64_t grid = (int64_t)num_sms_e() * per_sm;
-        if (grid > p.nunits) grid = p.nunits;
+    const void *kfn = split ? (const void *)k_cyc_edge<true> : (const void *)k_cyc_edge<false>;
+    TG_TRY(tg_allow_max_smem(kfn));
+    int per_sm = 0;
+    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    const int64_t hgrid_max = (int64_t)num_sms_e() * per_sm;
+    DevBuf<uint32_t> emap;
+    if (!emap.alloc((size_t)std::max<int64_t>(1, std::min<int64_t>(hgrid_max, split ? un.nheavy : un.nunits) * nbits), s))
+        return TG_ENOMEM;
+    p.emap = emap.p;
+    if (!split) {
+        // fused: every unit one CTA, Gamma_j bitmap, edges finished in place
+        TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
+        p.queue = queue.p;
+        p.ulist = nullptr;
+        p.nunits = un.nunits;
+        int64_t grid = std::min<int64_t>(hgrid_max, p.nunits);
         if (t.grid_limit > 0 && grid > t.grid_limit) grid = t.grid_limit;
         if (grid < 1) grid = 1;
-        DevBuf<uint32_t> emap;
-        if (!emap.alloc((size_t)std::max<int64_t>(1, grid * nbits), s)) return TG_ENOMEM;
-        p.emap = emap.p;
-        if (split)
-            k_cyc_edge<true><<<(unsigned)grid, threads, smem, s>>>(p);
-        else
-            k_cyc_edge<false><<<(unsigned)grid, threads, smem, s>>>(p);
+        k_cyc_edge<false><<<(unsigned)grid, threads, smem, s>>>(p);
         tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
+        return TG_OK;
     }
-    if (!split) return TG_OK;
-    // light units: one warp each, Gamma_j in a per-warp hash map
-    if (un.nlight > 0) {
-        DevBuf<unsigned long long> lq;
-        if (!lq.alloc(1, s)) return TG_ENOMEM;
-        TG_TRY_CUDA(cudaMemsetAsync(lq.p, 0, 8, s));
-        EdgeParams lp = p;
-        lp.queue = lq.p;
-        lp.ulist = un.light.p;
-        lp.nunits = un.nlight;
-        const size_t lw = (((size_t)3 * L2 * 8 + 15) & ~(size_t)15) + (size_t)2 * 4 * (1 << TG_LIGHT_LG);
-        const size_t lsmem = (size_t)kTsumLightWarps * lw;
-        TG_TRY(tg_allow_max_smem((const void *)k_cyc_tsum_light));
-        int lper = 0;
-        TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lper, k_cyc_tsum_light,
-                                                                  kTsumLightWarps * 32, lsmem));
-        if (lper < 1) lper = 1;
-        int64_t lgrid = (int64_t)num_sms_e() * lper;
-        const int64_t need = ((int64_t)un.nlight + kTsumLightWarps - 1) / kTsumLightWarps;
-        if (lgrid > need) lgrid = need;
-        if (t.grid_limit > 0 && lgrid > t.grid_limit) lgrid = t.grid_limit;
-        k_cyc_tsum_light<<<(unsigned)lgrid, kTsumLightWarps * 32, lsmem, s>>>(lp); tg_note_launch();
-        TG_TRY_CUDA(cudaGetLastError());
-    }
-    // finishing pass: warp per edge
-    p.hist_smem = hist_smem;
+    const size_t lw = (((size_t)3 * L2 * 8 + 15) & ~(size_t)15) + (size_t)2 * 4 * (1 << TG_LIGHT_LG);
+    const size_t lsmem = (size_t)kTsumLightWarps * lw;
+    TG_TRY(tg_allow_max_smem((const void *)k_cyc_tsum_light));
+    int lper = 0;
+    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lper, k_cyc_tsum_light,
+                                                              kTsumLightWarps * 32, lsmem));
+    if (lper < 1) lper = 1;
     const size_t fsmem = (hist_smem ? hist_bytes : 0) + (256 / 32) * xbytes;
     TG_TRY(tg_allow_max_smem((const void *)k_cyc_finish));
     int fper = 0;
     TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fper, k_cyc_finish, 256, fsmem));
     if (fper < 1) fper = 1;
-    int64_t fgrid = (int64_t)num_sms_e() * fper;
-    if (fgrid > (count + 7) / 8) fgrid = (count + 7) / 8;
-    if (t.grid_limit > 0 && fgrid > t.grid_limit) fgrid = t.grid_limit;
-    if (fgrid < 1) fgrid = 1;
-    k_cyc_finish<<<(unsigned)fgrid, 256, fsmem, s>>>(p, count); tg_note_launch();
-    TG_TRY_CUDA(cudaGetLastError());
+    for (size_t x = 0; x + 1 < bu.size(); ++x) {
+        p.qbase = ustart_h[x];
+        const int64_t nq = (int64_t)ustart_h[x + 1] - ustart_h[x];
+        if (nq <= 0) continue;
+        // heavy units: one CTA each, Gamma_j bitmap; B, C, DT to memory
+        EdgeParams hp = p;
+        hp.hist_smem = 0;
+        hp.ulist = un.heavy.p + bh[x];
+        hp.nunits = bh[x + 1] - bh[x];
+        if (hp.nunits > 0) {
+            TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
+            hp.queue = queue.p;
+            int64_t grid = std::min<int64_t>(hgrid_max, hp.nunits);
+            if (t.grid_limit > 0 && grid > t.grid_limit) grid = t.grid_limit;
+            if (grid < 1) grid = 1;
+            k_cyc_edge<true><<<(unsigned)grid, threads, smem, s>>>(hp);
+            tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+        }
+        // light units: one warp each, Gamma_j in a per-warp hash map
+        EdgeParams lp = p;
+        lp.hist_smem = 0;
+        lp.ulist = un.light.p + bl[x];
+        lp.nunits = bl[x + 1] - bl[x];
+        if (lp.nunits > 0) {
+            TG_TRY_CUDA(cudaMemsetAsync(queue.p + 1, 0, 8, s));
+            lp.queue = queue.p + 1;
+            int64_t lgrid = (int64_t)num_sms_e() * lper;
+            const int64_t need = ((int64_t)lp.nunits + kTsumLightWarps - 1) / kTsumLightWarps;
+            if (lgrid > need) lgrid = need;
+            if (t.grid_limit > 0 && lgrid > t.grid_limit) lgrid = t.grid_limit;
+            k_cyc_tsum_light<<<(unsigned)lgrid, kTsumLightWarps * 32, lsmem, s>>>(lp); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+        }
+        // finishing pass: warp per edge
+        EdgeParams fp = p;
+        fp.hist_smem = hist_smem;
+        int64_t fgrid = (int64_t)num_sms_e() * fper;
+        if (fgrid > (nq + 7) / 8) fgrid = (nq + 7) / 8;
+        if (t.grid_limit > 0 && fgrid > t.grid_limit) fgrid = t.grid_limit;
+        if (fgrid < 1) fgrid = 1;
+        k_cyc_finish<<<(unsigned)fgrid, 256, fsmem, s>>>(fp, nq); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
     return TG_OK;
 }

@@ -132,7 +132,8 @@ __device__ __forceinline__ uint32_t word_bits(int lo, int hi) {
 }
 
 __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32_t *adj,
-                                             const int32_t *toff, const int2 *edges,
+                                             const int32_t *toff, const uint8_t *ntype,
+                                             const int2 *edges,
                                              const uint32_t *order, const uint32_t *ustart,
                                              const uint32_t *ulist, uint32_t nunits, int32_t L,
                                              int64_t nbits, unsigned long long *queue,
@@ -160,6 +161,7 @@ __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32
         const int64_t bj = rowptr[j];
         const int dj = (int)(rowptr[j + 1] - bj);
         const int32_t *toj = toff + (int64_t)j * (L + 1);
+        const uint32_t pj = ((uint32_t)ntype[j] << TG_TSHIFT) | (uint32_t)j;
         if (j != cur_j) {
             for (int x = tid; x < cur_dj; x += blockDim.x) {
                 const uint32_t id = __ldg(adj + cur_bj + x) & TG_IDMASK;
@@ -193,7 +195,8 @@ __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32
                     const uint32_t w = __ldg(adj + bi + x);
                     const uint32_t id = w & TG_IDMASK;
                     if ((int)id != j)
-                        hit = (int64_t)id < nbits ? bm_test(bm, id) : contains(adj, bj, toj, w);
+                        hit = (int64_t)id < nbits ? bm_test(bm, id)
+                                                  : adjacent(rowptr, adj, toff, L, bj, dj, toj, pj, w);
                 }
                 const unsigned hm = __ballot_sync(kFull, hit);
                 if (lane < L) mine += __popc(hm & word_bits(ts0 - c0, ts1 - c0));
@@ -992,7 +995,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
             int64_t grid = (int64_t)tg_num_sms() * per_sm;
             if (grid > (int64_t)un.nheavy) grid = un.nheavy;
             if (grid < 1) grid = 1;
-            k_tau<<<(unsigned)grid, 512, smem, s>>>(g->rowptr, g->adj, g->toff, g->edges, ord,
+            k_tau<<<(unsigned)grid, 512, smem, s>>>(g->rowptr, g->adj, g->toff, g->ntype, g->edges, ord,
                                                     un.ustart.p, un.heavy.p, un.nheavy, L, nbits,
                                                     q.p, tau.p); tg_note_launch();
             TG_TRY_CUDA(cudaGetLastError());

@@ -26,6 +26,9 @@ VARIANTS = {
     "cycles-fused": dict(kernel=tg.TG_KERNEL_CYCLES, edge_pass=tg.TG_EDGE_PASS_FUSED),
     "cycles-fused-small": dict(kernel=tg.TG_KERNEL_CYCLES, edge_pass=tg.TG_EDGE_PASS_FUSED,
                                cta_threads=64, hash_slots=32, bitmap_bits=96, grid_limit=3),
+    # the per-edge pass in batches of work units (as on graphs whose T sums
+    # do not fit in memory at once)
+    "cycles-batched": dict(kernel=tg.TG_KERNEL_CYCLES, edge_batch=700),
     "reuse": dict(kernel=tg.TG_KERNEL_REUSE),
     "warp-search": dict(kernel=tg.TG_KERNEL_WARP_SEARCH),
     "cta-small": dict(kernel=tg.TG_KERNEL_CTA_BITMAP, cta_threads=128, unroll=1, hash_slots=32,

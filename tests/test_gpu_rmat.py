@@ -6,7 +6,7 @@ the C ABI against the oracles, bit-exact in uint64 (tolerance 0).
   global histogram against the second oracle, and per-edge orbit rows of a
   sample (random edges, the costliest edges, both ends of the edge order)
   against the paper-method oracle, for the default per-edge pass and for the
-  fused per-edge kernel that R-MAT-23 itself takes.
+  fused per-edge kernel and for the per-edge pass in batches of work units.
 * K_{2,b} for b = 2^16 - 1 and 2^16: every 4-cycle has the same highest-ranked
   node (a hub of degree b) and the other hub as its far end, so that far end
   collects b middles in one counter: 2^16 - 1 is the largest count the 16-bit
@@ -28,7 +28,9 @@ from tests import layout
 
 pytestmark = pytest.mark.gpu
 
-EDGE_PASSES = {"auto": tg.TG_EDGE_PASS_AUTO, "fused": tg.TG_EDGE_PASS_FUSED}
+EDGE_PASSES = {"auto": dict(edge_pass=tg.TG_EDGE_PASS_AUTO),
+               "fused": dict(edge_pass=tg.TG_EDGE_PASS_FUSED),
+               "batched": dict(edge_batch=50000)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -53,7 +55,7 @@ def rmat16():
 
 @pytest.fixture(params=list(EDGE_PASSES))
 def edge_pass(request):
-    tg.tg_set_tune(kernel=tg.TG_KERNEL_CYCLES, edge_pass=EDGE_PASSES[request.param])
+    tg.tg_set_tune(kernel=tg.TG_KERNEL_CYCLES, **EDGE_PASSES[request.param])
     yield request.param
     tg.tg_set_tune(reset=True)
 
