@@ -17,8 +17,9 @@ every synchronisation).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
 Prints one JSON line (rank 0).  N > 1 runs under torch.distributed.run: every
-rank builds the graph and counts a cost-balanced range of edges, then one
-NCCL sum of the histograms.  ``--impl reference`` times the CPU oracle on a
+rank builds the graph and counts its shard (tg_count_shard: a cost-balanced
+slice of the per-edge pass and its share of the 4-cycle and 4-clique
+enumerations), then one NCCL sum of the histograms.  ``--impl reference`` times the CPU oracle on a
 bounded sample of the same workload (rank 0 only).
 """
 from __future__ import annotations
@@ -78,8 +79,12 @@ def parse():
                          "fit) or always the fused kernel")
     ap.add_argument("--retain-gib", type=int, default=64,
                     help="tg_set_memory_retention for the graph mode, GiB (0: the default pool)")
-    ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--serve-load", type=float, default=0.9)
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-load", default="0.5,0.9",
+                    help="comma-separated loads: arrival rate as a fraction of the measured "
+                         "one-at-a-time capacity")
+    ap.add_argument("--gen-procs", type=int, default=0,
+                    help="host processes generating the request graphs (0: all cores)")
     return ap.parse_args()
 
 
@@ -355,42 +360,56 @@ def run_batch(args):
     return 0
 
 
+def _serve_graph_job(job):
+    from paper_1901_10026_gb300 import synth
+    e, key = job
+    G = synth.serve_graph(e, key)
+    return G.n, G.src, G.dst, G.types, G.L
+
+
 def run_serve(args):
-    """Poisson stream of Chung-Lu counting requests; continuous batching vs one at a time."""
+    """Poisson stream of Chung-Lu counting requests: the continuous-batching
+    server against a one-request-at-a-time server on the same arrivals, at
+    each load, plus both under saturation (every request queued at once)."""
+    import multiprocessing as mp
     import threading
 
-    import paper_1901_10026_gb300 as tg
     from paper_1901_10026_gb300 import synth
+
+    # request graphs, generated on the host cores before any device work
+    reqs = synth.serve_stream(args.serve_requests, rate=1.0)
+    t0 = time.perf_counter()
+    procs = args.gen_procs or os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(procs) as pool:
+        Gs = pool.map(_serve_graph_job, [(e, key) for _, e, key in reqs], chunksize=4)
+    gen_s = time.perf_counter() - t0
+
+    import paper_1901_10026_gb300 as tg
 
     # a serving process keeps its scratch mapped between requests (library setting)
     tg.tg_set_memory_retention(args.retain_gib << 30)
-    reqs = synth.serve_stream(args.serve_requests, rate=1.0)
-    t0 = time.perf_counter()
-    Gs = [synth.serve_graph(e, key) for _, e, key in reqs]
-    gen_s = time.perf_counter() - t0
     # solo service: one plain build + count per request, back to back
     solo = []
     t0 = time.perf_counter()
-    for G in Gs:
-        g = tg.tg_build_csr(G.n, G.src, G.dst, G.types, G.L)
+    for n, src, dst, types, L in Gs:
+        g = tg.tg_build_csr(n, src, dst, types, L)
         solo.append(tg.tg_count_global(g, 4))
         g.close()
     serial_s = time.perf_counter() - t0
     capacity = len(Gs) / serial_s
-    rate = args.serve_load * capacity
-    gaps = np.array([r[0] for r in reqs])
-    arrivals = gaps / rate  # the stream's unit-rate times scaled to the target rate
+    unit_times = np.array([r[0] for r in reqs])
 
-    def drive(server):
+    def drive(server, arrivals):
         tickets = [None] * len(Gs)
         start = time.perf_counter()
 
         def feeder():
-            for r, G in enumerate(Gs):
-                delay = arrivals[r] - (time.perf_counter() - start)
-                if delay > 0:
-                    time.sleep(delay)
-                tickets[r] = server.submit(G.n, G.src, G.dst, G.types, G.L, 4)
+            for r, (n, src, dst, types, L) in enumerate(Gs):
+                if arrivals is not None:
+                    delay = arrivals[r] - (time.perf_counter() - start)
+                    if delay > 0:
+                        time.sleep(delay)
+                tickets[r] = server.submit(n, src, dst, types, L, 4)
 
         th = threading.Thread(target=feeder)
         th.start()
@@ -401,24 +420,41 @@ def run_serve(args):
             ok = ok and bool(np.array_equal(got, solo[r]))
         st = server.stats()
         server.close()
-        return st, ok
+        keep = ("p50_ms", "p99_ms", "graphs_per_s", "peak_in_flight", "batched_launches",
+                "grouped_requests")
+        return {k: st[k] for k in keep}, ok
 
-    base_st, base_ok = drive(tg.Server(slots=1, batch_edges=0))
-    serv_st, serv_ok = drive(tg.Server(slots=4, batch_max=32, batch_edges=20000))
+    def served():
+        return tg.Server(slots=4, batch_max=32, batch_edges=20000)
+
+    def one_at_a_time():
+        return tg.Server(slots=1, batch_edges=0)
+
+    loads = [float(x) for x in str(args.serve_load).split(",") if x]
+    per_load, all_ok = {}, True
+    for rho in loads:
+        arrivals = unit_times / (rho * capacity)
+        sv, ok1 = drive(served(), arrivals)
+        base, ok2 = drive(one_at_a_time(), arrivals)
+        all_ok = all_ok and ok1 and ok2
+        per_load[str(rho)] = {"arrival_rate_per_s": rho * capacity, "served": sv, "one_at_a_time": base}
+    sat_sv, ok1 = drive(served(), None)
+    sat_base, ok2 = drive(one_at_a_time(), None)
+    all_ok = all_ok and ok1 and ok2
+    head = per_load[str(loads[-1])]["served"] if loads else sat_sv
     line = {
-        "metric": "served p99 latency", "value": serv_st["p99_ms"], "unit": "ms", "n_gpus": 1,
+        "metric": "served p99 latency", "value": head["p99_ms"], "unit": "ms", "n_gpus": 1,
         "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic", "mode": "serve",
         "config": {"workload": f"{len(Gs)} Poisson-arriving requests, Chung-Lu gamma 2.1, avg degree 16, "
                                "edges log-uniform [1e3, 2e6], L=6 uniform, global k=4",
-                   "requests": len(Gs), "edges": int(sum(G.m for G in Gs)),
-                   "arrival_rate_per_s": rate, "load": args.serve_load,
+                   "requests": len(Gs), "edges": int(sum(G[1].shape[0] for G in Gs)),
+                   "loads": loads, "headline_load": loads[-1] if loads else None,
                    "solo_capacity_graphs_per_s": capacity,
                    "memory_retention_bytes": args.retain_gib << 30},
-        "served": {k: serv_st[k] for k in ("p50_ms", "p99_ms", "graphs_per_s", "peak_in_flight",
-                                            "batched_launches", "grouped_requests")},
-        "one_at_a_time": {k: base_st[k] for k in ("p50_ms", "p99_ms", "graphs_per_s", "peak_in_flight")},
-        "results_equal_solo": bool(serv_ok and base_ok), "generation_s": gen_s,
+        "per_load": per_load,
+        "saturation": {"served": sat_sv, "one_at_a_time": sat_base},
+        "results_equal_solo": bool(all_ok), "generation_s": gen_s, "generation_procs": procs,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -460,15 +496,8 @@ def main():
     elif args.edge_pass == "fused":
         tg.tg_set_tune(kernel=tg.TG_KERNEL_CYCLES, edge_pass=tg.TG_EDGE_PASS_FUSED)
 
-    # shard ranges from the canonical edge list of the built graph (untimed)
     g0 = tg.tg_build_csr(G.n, src_d, dst_d, typ_d, L)
     M = g0.M
-    if world > 1:
-        eu, ev = tg.tg_edge_list(g0)
-        ranges = tgdist.shard_ranges(tgdist.edge_costs(G.n, eu, ev), world)
-        e0, e1 = ranges[rank]
-    else:
-        e0, e1 = 0, M
     work_entries = tg.tg_work_model(g0)
     log_delta = math.log2(max(2, g0.max_degree))
     g0.close()
@@ -488,7 +517,7 @@ def main():
                 tg.tg_count_global(g, k, out_d)
                 res = None
         else:
-            tg.tg_count_range(g, k, e0, e1, out_d)
+            tg.tg_count_shard(g, k, rank, world, out_d)
             tgdist.allreduce_sums(out_d)
             res = tg.tg_global_finalize(L, k, out_d.cpu().numpy().view(np.uint64)) if host else None
         g.close()
@@ -595,7 +624,7 @@ def main():
                        "memory_retention_bytes": args.retain_gib << 30,
                        "kernel": args.kernel,
                        "l2": "flushed between steps (256 MiB write)",
-                       "parallelism": f"edge ranges x{world}" if world > 1 else "single GPU"},
+                       "parallelism": f"shards x{world}" if world > 1 else "single GPU"},
             "clocks": clocks,
             "e2e": {"value": M / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "repeats": int(max(1, args.e2e_steps))},

@@ -197,6 +197,39 @@ int tg_count_per_edge(const tg_graph *g, int32_t k, int32_t level, uint64_t *row
                       void *stream);
 
 /*
+ * Sparse per-edge counts (Sec. "Sparse Typed Motif Format"): only the nonzero
+ * typed counts of each edge, as (id, count) pairs, edge after edge in
+ * canonical edge order, each edge's pairs in slot order.  An id numbers every
+ * typed graphlet (level TG_GRAPHLET: h1, h2, then h3..h8 for k = 4) or typed
+ * orbit (TG_ORBIT: g1, g2, then g3..g12) consecutively, block by block, one
+ * block per graphlet or orbit with its sorted type multisets of all the
+ * subgraph's nodes in colex order (C(L+2,3) entries for 3-node blocks,
+ * C(L+3,4) for 4-node ones); unlike a dense slot, an id means the same for
+ * every edge.  tg_sparse_id is the lookup table back to the graphlet or orbit
+ * and its types (tg_paper_hash of those gives the paper's key).
+ *   offsets  M + 1 int64, host or device: edge e's pairs are the entries
+ *            [offsets[e], offsets[e + 1]) of ids and counts
+ *   ids      capacity uint32, counts capacity uint64: host or device, both
+ *            or neither; with ids == counts == NULL only offsets and *nnz
+ *            are written (a sizing call)
+ *   nnz      receives the number of pairs (host)
+ * The dense rows are formed in device scratch first (M x tg_slots(L, k,
+ * level) uint64).  Errors: TG_EINVAL, TG_EOVERFLOW (nnz > capacity; offsets
+ * and *nnz are still written), TG_ENOMEM, TG_ECUDA.  Synchronises `stream`.
+ */
+int tg_count_per_edge_sparse(const tg_graph *g, int32_t k, int32_t level, int64_t *offsets,
+                             uint32_t *ids, uint64_t *counts, int64_t capacity, int64_t *nnz,
+                             void *stream);
+
+/* Number of sparse ids for (L, k, level); -1 for invalid arguments. */
+int64_t tg_sparse_ids(int32_t L, int32_t k, int32_t level);
+
+/* The graphlet (level TG_GRAPHLET: 1..8) or orbit (TG_ORBIT: 1..12) of a
+ * sparse id and the sorted types of its k_out (3 or 4) nodes. */
+int tg_sparse_id(int32_t L, int32_t k, int32_t level, int64_t id, int32_t *motif,
+                 int32_t *types, int32_t *k_out);
+
+/*
  * Undivided per-configuration sums over the canonical edge range [e0, e1):
  * sum over those edges of the per-edge graphlet counts, in the global layout.
  * Summing the outputs of disjoint ranges that cover [0, M) and passing the
@@ -205,6 +238,24 @@ int tg_count_per_edge(const tg_graph *g, int32_t k, int32_t level, uint64_t *row
  *   sums  tg_global_len(L, k) uint64, host or device
  */
 int tg_count_range(const tg_graph *g, int32_t k, int64_t e0, int64_t e1, uint64_t *sums,
+                   void *stream);
+
+/*
+ * One share of a global count split across `nshards` ranks (the unit of work
+ * of one GPU when the count is sharded): undivided sums in the global layout
+ * whose total over shard = 0 .. nshards - 1, passed to tg_global_finalize,
+ * is tg_count_global's result (Sec. "Global Typed Graphlet Counts": the
+ * global count is a sum over edges).  Every shard runs Alg. 1 over the whole
+ * graph (the identities read the triangle counts of edges outside its
+ * slice); the per-edge pass takes a slice of the edges balanced by their
+ * Gamma_i lengths; the whole-graph 4-cycle and 4-clique enumerations take the
+ * anchors and lowest nodes v with v mod nshards == shard, and each shard adds
+ * the correction of its own cycle and clique totals (the correction is
+ * linear in them).  No per-edge counters of the whole graph are kept.
+ *   sums  tg_global_len(L, k) uint64, host or device; synchronises `stream`
+ * Errors as tg_count_range; TG_EINVAL for shard outside [0, nshards).
+ */
+int tg_count_shard(const tg_graph *g, int32_t k, int32_t shard, int32_t nshards, uint64_t *sums,
                    void *stream);
 
 /*

@@ -22,7 +22,7 @@ from . import build as _build
 
 __all__ = [
     "TGError", "Graph", "lib", "tg_build_csr", "tg_free_graph", "tg_graph_info", "tg_edge_list",
-    "tg_count_global", "tg_count_global_noalloc", "tg_count_per_edge", "Batch", "tg_count_batch", "Server", "tg_count_range", "tg_global_finalize",
+    "tg_count_global", "tg_count_global_noalloc", "tg_count_per_edge", "tg_count_shard", "tg_count_per_edge_sparse", "tg_sparse_ids", "tg_sparse_id", "Batch", "tg_count_batch", "Server", "tg_count_range", "tg_global_finalize",
     "tg_work_model", "tg_slots", "tg_global_len", "tg_config_count", "tg_config_rank",
     "tg_config_unrank", "tg_paper_hash", "tg_slot_config", "tg_strerror", "tg_version",
     "tg_debug_fail_alloc", "tg_set_tune", "tg_get_tune", "tg_launch_count", "tg_last_timing",
@@ -139,6 +139,10 @@ def lib():
             "tg_count_global": (ctypes.c_int, [vp, i32, vp, vp]),
             "tg_count_per_edge": (ctypes.c_int, [vp, i32, i32, vp, vp]),
             "tg_count_range": (ctypes.c_int, [vp, i32, i64, i64, vp, vp]),
+            "tg_count_shard": (ctypes.c_int, [vp, i32, i32, i32, vp, vp]),
+            "tg_count_per_edge_sparse": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, i64, vp, vp]),
+            "tg_sparse_ids": (i64, [i32, i32, i32]),
+            "tg_sparse_id": (ctypes.c_int, [i32, i32, i32, i64, vp, vp, vp]),
             "tg_global_finalize": (ctypes.c_int, [i32, i32, vp, vp]),
             "tg_work_model": (ctypes.c_int, [vp, vp, vp]),
             "tg_set_allocator": (ctypes.c_int, [vp, vp, vp]),
@@ -457,6 +461,43 @@ def tg_count_range(g: Graph, k: int, e0: int, e1: int, sums=None, stream=None):
         sums = np.zeros(tg_global_len(g.L, k), np.uint64)
     _check(lib().tg_count_range(g.handle, k, int(e0), int(e1), _ptr(sums), _stream(stream)),
            "tg_count_range")
+    return sums
+
+
+def tg_count_per_edge_sparse(g: Graph, k: int = 4, level: int = TG_GRAPHLET, stream=None):
+    """Sparse per-edge counts: (offsets [M+1], ids, counts) as numpy arrays."""
+    offsets = np.zeros(g.M + 1, np.int64)
+    nnz = ctypes.c_int64(0)
+    _check(lib().tg_count_per_edge_sparse(g.handle, k, level, _ptr(offsets), None, None, 0,
+                                          ctypes.byref(nnz), _stream(stream)), "tg_count_per_edge_sparse")
+    ids = np.zeros(max(1, nnz.value), np.uint32)
+    counts = np.zeros(max(1, nnz.value), np.uint64)
+    _check(lib().tg_count_per_edge_sparse(g.handle, k, level, _ptr(offsets), _ptr(ids), _ptr(counts),
+                                          ids.shape[0], ctypes.byref(nnz), _stream(stream)),
+           "tg_count_per_edge_sparse")
+    return offsets, ids[: nnz.value], counts[: nnz.value]
+
+
+def tg_sparse_ids(L: int, k: int = 4, level: int = TG_GRAPHLET) -> int:
+    return int(lib().tg_sparse_ids(L, k, level))
+
+
+def tg_sparse_id(L: int, k: int, level: int, sid: int):
+    """(graphlet or orbit number, sorted types) of a sparse id."""
+    motif = ctypes.c_int32()
+    kk = ctypes.c_int32()
+    t = np.zeros(4, np.int32)
+    _check(lib().tg_sparse_id(L, k, level, int(sid), ctypes.byref(motif), _ptr(t), ctypes.byref(kk)),
+           "tg_sparse_id")
+    return int(motif.value), tuple(int(x) for x in t[: kk.value])
+
+
+def tg_count_shard(g: Graph, k: int, shard: int, nshards: int, sums=None, stream=None):
+    """Undivided sums of one shard of a global count split over ``nshards``."""
+    if sums is None:
+        sums = np.zeros(tg_global_len(g.L, k), np.uint64)
+    _check(lib().tg_count_shard(g.handle, k, int(shard), int(nshards), _ptr(sums), _stream(stream)),
+           "tg_count_shard")
     return sums
 
 

@@ -1178,6 +1178,100 @@ extern "C" int tg_count_range(const tg_graph *g, int32_t k, int64_t e0, int64_t 
     return TG_OK;
 }
 
+namespace {
+
+// Per order position: the work of its edge in the per-edge pass, d_i + 8
+// (d_i the smaller degree: the Gamma_i scan), for the cost-balanced slices.
+__global__ void k_order_cost(const uint32_t *order, const int2 *edges, const int64_t *rowptr,
+                             int64_t M, int64_t *cost) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q <= M;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        if (q == M) {
+            cost[q] = 0;
+            continue;
+        }
+        const int2 ab = edges[order[q]];
+        const int i = max(ab.x, ab.y);
+        cost[q] = rowptr[i + 1] - rowptr[i] + 8;
+    }
+}
+
+// The first position whose exclusive prefix reaches total * r / parts, for
+// r = first .. first + 1 (out[0], out[1]).
+__global__ void k_split_points(const int64_t *prefix, int64_t M, int32_t first, int32_t parts,
+                               int64_t *out) {
+    const int r = first + (int)threadIdx.x;
+    if (threadIdx.x > 1) return;
+    const int64_t total = prefix[M];
+    const int64_t want = (int64_t)((__int128)total * r / parts);
+    int64_t lo = 0, hi = M;  // first q with prefix[q] >= want
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (prefix[mid] < want)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    out[threadIdx.x] = r >= parts ? M : lo;
+}
+
+}  // namespace
+
+extern "C" int tg_count_shard(const tg_graph *g, int32_t k, int32_t shard, int32_t nshards,
+                              uint64_t *sums, void *stream) {
+    TG_TRY(check_counts(g, k));
+    if (!sums || nshards < 1 || shard < 0 || shard >= nshards) return TG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t len = tg_global_len(g->L, k);
+    DevBuf<unsigned long long> d;
+    unsigned long long *dsums = reinterpret_cast<unsigned long long *>(sums);
+    const bool dev_out = tg_is_device_ptr(sums);
+    if (!dev_out) {
+        if (!d.alloc(len, s)) return TG_ENOMEM;
+        dsums = d.p;
+    }
+    if (nshards == 1) {
+        TG_TRY(sums_impl(g, k, 0, g->M, dsums, s));
+    } else {
+        TG_TRY_CUDA(cudaMemsetAsync(dsums, 0, len * 8, s));
+        tg_sched *sc = nullptr;
+        TG_TRY(get_sched(g, s, &sc));
+        const int64_t M = g->M;
+        int64_t q[2] = {0, 0};
+        if (M > 0) {
+            DevBuf<int64_t> cost, pre, qs;
+            if (!cost.alloc(M + 1, s) || !pre.alloc(M + 1, s) || !qs.alloc(2, s)) return TG_ENOMEM;
+            k_order_cost<<<grid_for(M + 1), 256, 0, s>>>(sc->order, g->edges, g->rowptr, M, cost.p); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+            TG_TRY(tg_scan_i64(cost.p, pre.p, M + 1, s));
+            k_split_points<<<1, 32, 0, s>>>(pre.p, M, shard, nshards, qs.p); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+            TG_TRY_CUDA(cudaMemcpyAsync(q, qs.p, 16, cudaMemcpyDeviceToHost, s));
+            TG_TRY_CUDA(cudaStreamSynchronize(s));
+        }
+        const tg_tune t = tune_now();
+        if (t.kernel == TG_KERNEL_AUTO || t.kernel == TG_KERNEL_CYCLES) {
+            // a slice of the edges, and a share of the whole-graph enumerations
+            tg_part part;
+            part.index = shard;
+            part.count = nshards;
+            if (k == 4)
+                TG_TRY(tg_reuse_count(g, k, TG_GRAPHLET, sc->order, sc->order + q[0], q[1] - q[0],
+                                      nullptr, 0, dsums, t, s, part));
+            else if (q[1] > q[0])
+                TG_TRY(tg_reuse_count(g, k, TG_GRAPHLET, sc->order, sc->order + q[0], q[1] - q[0],
+                                      nullptr, 0, dsums, t, s));
+        } else if (q[1] > q[0]) {
+            // the per-edge kernels need nothing beyond the slice's edges
+            TG_TRY(launch_count(g, k, TG_GRAPHLET, sc->order, sc->order + q[0], 0, q[1] - q[0],
+                                nullptr, 0, dsums, s));
+        }
+    }
+    if (!dev_out) TG_TRY_CUDA(cudaMemcpyAsync(sums, dsums, len * 8, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    return TG_OK;
+}
+
 extern "C" int tg_count_per_edge(const tg_graph *g, int32_t k, int32_t level, uint64_t *rows,
                                  void *stream) {
     TG_TRY(check_counts(g, k));
@@ -1198,6 +1292,15 @@ extern "C" int tg_count_per_edge(const tg_graph *g, int32_t k, int32_t level, ui
     TG_TRY_CUDA(cudaMemcpyAsync(rows, d.p, (size_t)g->M * width * 8, cudaMemcpyDeviceToHost, s));
     TG_TRY_CUDA(cudaStreamSynchronize(s));
     return TG_OK;
+}
+
+int tg_rows_device(const tg_graph *g, int k, int level, uint64_t *rows, cudaStream_t s) {
+    TG_TRY(check_counts(g, k));
+    if (g->M == 0) return TG_OK;
+    tg_sched *sc = nullptr;
+    TG_TRY(get_sched(g, s, &sc));
+    return launch_count(g, k, level, sc->order, sc->order, 0, g->M, rows,
+                        tg_slots(g->L, k, level), nullptr, s);
 }
 
 extern "C" int tg_work_model(const tg_graph *g, uint64_t *entries, void *stream) {

@@ -957,7 +957,7 @@ __global__ void __launch_bounds__(kC4WalkWarps * 32) k_c4_bin_walk(C4Bin p) {
 // cleared.  The tables go into the histogram under {ta, tb, t, t'} when the
 // anchor changes.  Types beyond kBinAccL use c4_add straight into a shared
 // histogram instead.
-constexpr int kBinPairThreads = 256;
+constexpr int kBinPairThreads = 512;
 constexpr int kBinRun = 16;
 constexpr int kBinAccL = 8;
 
@@ -1021,20 +1021,30 @@ __global__ void __launch_bounds__(kBinPairThreads) k_c4_bin_pairs(C4Bin p) {
                 cur_ta = p.ntype[p.heavy[p.q0 + row]];
             }
             const int ta = cur_ta;
-            for (uint32_t k = c0 + tid; k < c1; k += blockDim.x) {
-                const uint32_t e = p.bins[k];
-                const uint32_t bl = e & wmask;
-                const int t = (int)(e >> p.wlg);
-                bool first;
-                if (p.half) {
-                    const uint32_t idx = bl * (uint32_t)Lp + (uint32_t)t;
-                    const int sh = (int)(idx & 1u) * 16;
-                    const uint32_t old = atomicAdd(tab + (idx >> 1), 1u << sh);
-                    first = ((old >> sh) & 0xffffu) == 0u;
-                } else {
-                    first = atomicAdd(tab + bl * (uint32_t)L + (uint32_t)t, 1u) == 0u;
+            // four entries in flight per thread
+            for (uint32_t k0 = c0 + tid; k0 < c1; k0 += 4 * blockDim.x) {
+                uint32_t ev[4];
+#pragma unroll
+                for (int z = 0; z < 4; ++z) {
+                    const uint32_t k = k0 + (uint32_t)z * blockDim.x;
+                    ev[z] = k < c1 ? (uint32_t)p.bins[k] : 0xffffffffu;
                 }
-                if (first) atomicOr(tbits + (bl >> 5), 1u << (bl & 31u));
+#pragma unroll
+                for (int z = 0; z < 4; ++z) {
+                    if (ev[z] == 0xffffffffu) continue;
+                    const uint32_t bl = ev[z] & wmask;
+                    const int t = (int)(ev[z] >> p.wlg);
+                    bool first;
+                    if (p.half) {
+                        const uint32_t idx = bl * (uint32_t)Lp + (uint32_t)t;
+                        const int sh = (int)(idx & 1u) * 16;
+                        const uint32_t old = atomicAdd(tab + (idx >> 1), 1u << sh);
+                        first = ((old >> sh) & 0xffffu) == 0u;
+                    } else {
+                        first = atomicAdd(tab + bl * (uint32_t)L + (uint32_t)t, 1u) == 0u;
+                    }
+                    if (first) atomicOr(tbits + (bl >> 5), 1u << (bl & 31u));
+                }
             }
             __syncthreads();
             for (int wd = warp; wd < nfar / 32; wd += NW) {
@@ -1295,10 +1305,11 @@ __global__ void k_c4_cost(const int64_t *rowptr, const uint32_t *adj, int64_t n,
 enum { kClsSplit = 0, kClsWarp, kClsCta, kClsSlot, kClsN };
 
 __global__ void k_c4_mark(const unsigned long long *cost, int64_t n, unsigned long long thr,
-                          unsigned long long lite, unsigned long long mid, uint32_t *flags) {
+                          unsigned long long lite, unsigned long long mid, int pidx, int pcnt,
+                          uint32_t *flags) {
     for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < n;
          a += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long c = cost[a];
+        const unsigned long long c = a % pcnt == pidx ? cost[a] : 0ull;  // other parts' anchors
         int cls = -1;
         if (c > thr)
             cls = kClsSplit;
@@ -1632,6 +1643,7 @@ struct K4GParams {
     unsigned long long *work;
     uint32_t *rows;       // k_k4_rows: per CTA rows_stride words of bitmap rows
     int64_t rows_stride;
+    int32_t pidx, pcnt;   // only lowest nodes x0 with x0 mod pcnt == pidx
 };
 
 constexpr int kK4GWarps = 8;
@@ -1678,7 +1690,8 @@ __global__ void __launch_bounds__(kK4GWarps * 32) k_k4_global(K4GParams p) {
         while (__ldg(p.uoff + x0 + 1) <= qq) ++x0;
         const int64_t b0 = __ldg(p.uoff + x0);
         const int d0 = (int)(__ldg(p.uoff + x0 + 1) - b0);
-        if (d0 < 3 || d0 <= p.min_d0) continue;  // three more above x0; or a bitmap kernel's
+        if (d0 < 3 || d0 <= p.min_d0 || x0 % p.pcnt != p.pidx) continue;  // three more above
+                                                  // x0; or a bitmap kernel's; or another part's
         const int t0 = p.ntype[x0];
         const int32_t *to0 = p.utoff + x0 * (L + 1);
         if (x0 != cur) {
@@ -1841,7 +1854,7 @@ __global__ void __launch_bounds__(kBitsWarps * 32) k_k4_bits_warp(K4GParams p) {
         const uint32_t x0 = (uint32_t)item;
         const int64_t b0 = __ldg(p.uoff + x0);
         const int d0 = (int)(__ldg(p.uoff + x0 + 1) - b0);
-        if (d0 < 3 || d0 > kBitsWarpMax) continue;
+        if (d0 < 3 || d0 > kBitsWarpMax || (int64_t)x0 % p.pcnt != p.pidx) continue;
         const int t0 = p.ntype[x0];
         const int32_t *to0 = p.utoff + (int64_t)x0 * (L + 1);
         // position of every up(x0) member, and the type ranges as masks
@@ -2053,11 +2066,12 @@ __global__ void __launch_bounds__(kRowsThreads) k_k4_rows(K4GParams p, const uin
     }
 }
 
-__global__ void k_flag_range(const int64_t *uoff, int64_t n, int lo, int hi, uint32_t *flag) {
+__global__ void k_flag_range(const int64_t *uoff, int64_t n, int lo, int hi, int pidx, int pcnt,
+                             uint32_t *flag) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t d = uoff[v + 1] - uoff[v];
-        flag[v] = (d >= lo && d <= hi) ? 1u : 0u;
+        flag[v] = (d >= lo && d <= hi && v % pcnt == pidx) ? 1u : 0u;
     }
 }
 
@@ -2375,7 +2389,7 @@ int c4_bin_waves(const tg_graph *g, const uint32_t *list, int64_t na,
 }  // namespace
 
 int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long *g4,
-                  unsigned long long *work, const tg_tune &t, cudaStream_t s) {
+                  unsigned long long *work, const tg_tune &t, const tg_part &part, cudaStream_t s) {
     if (g->M == 0) return TG_OK;
     const int L = g->L, L2 = L * L;
     const int64_t n = g->n;
@@ -2434,7 +2448,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     if (t.unroll == 1) thr = ~0ull;
     if (t.unroll == 4) thr = 0ull;
     const unsigned egrid = (unsigned)std::min<int64_t>((n + 255) / 256, 65535LL * 16);
-    k_c4_mark<<<egrid, 256, 0, s>>>(cost.p, n, thr, lite, mid, flags.p); tg_note_launch();
+    k_c4_mark<<<egrid, 256, 0, s>>>(cost.p, n, thr, lite, mid, part.index, part.count, flags.p); tg_note_launch();
     TG_TRY_CUDA(cudaGetLastError());
     for (int k = 0; k < kClsN; ++k) TG_TRY(tg_scan_u32(flags.p + (size_t)k * n, pos.p + (size_t)k * n, n, s));
     uint32_t lastp[kClsN], lastf[kClsN];
@@ -2642,7 +2656,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
 }
 
 int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long long *g4,
-                   unsigned long long *work, const tg_tune &t, cudaStream_t s) {
+                   unsigned long long *work, const tg_tune &t, const tg_part &part, cudaStream_t s) {
     if (g->M == 0) return TG_OK;
     const int L = g->L;
     const bool global = g4 != nullptr;
@@ -2706,6 +2720,8 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
         q.g4 = g4;
         q.n4 = n4;
         q.work = work;
+        q.pidx = part.index;
+        q.pcnt = part.count;
         // bitmap kernels: one word for up lists of at most 32 (warp per x0),
         // padded rows of up to kRowsMaxWords words beyond (CTA per x0, in
         // three widths); a hash_slots cap below 64 sends every x0 to the
@@ -2732,7 +2748,7 @@ int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long lon
                 if ((unsigned long long)lo > maxup || hi < lo) continue;
                 if (!flag.p && (!flag.alloc(n, s) || !pos.alloc(n, s) || !list.alloc(n, s)))
                     return TG_ENOMEM;
-                k_flag_range<<<egrid, 256, 0, s>>>(uoff.p, n, lo, hi, flag.p); tg_note_launch();
+                k_flag_range<<<egrid, 256, 0, s>>>(uoff.p, n, lo, hi, part.index, part.count, flag.p); tg_note_launch();
                 TG_TRY_CUDA(cudaGetLastError());
                 TG_TRY(tg_scan_u32(flag.p, pos.p, n, s));
                 k_c4_compact<<<egrid, 256, 0, s>>>(flag.p, pos.p, n, list.p); tg_note_launch();

@@ -113,6 +113,24 @@ __device__ __forceinline__ uint32_t edge_to(const int64_t *__restrict__ rowptr,
     return q < 0 ? 0xffffffffu : __ldg(eid + bj + q);
 }
 
+// As edge_to, but the index of the adjacency entry of the edge (j, y) (in
+// Gamma_j or in Gamma_y, whichever list was searched), 0xffffffff if absent.
+__device__ __forceinline__ uint32_t entry_to(const int64_t *__restrict__ rowptr,
+                                             const uint32_t *__restrict__ adj,
+                                             const int32_t *__restrict__ toff, int L, int64_t bj,
+                                             int dj, const int32_t *__restrict__ toj, uint32_t pj,
+                                             uint32_t w) {
+    const uint32_t y = w & TG_IDMASK;
+    const int64_t by = __ldg(rowptr + y);
+    const int dy = (int)(__ldg(rowptr + y + 1) - by);
+    if (dy < dj) {
+        const int q = find_pos(adj, by, toff + (int64_t)y * (L + 1), pj);
+        return q < 0 ? 0xffffffffu : (uint32_t)(by + q);
+    }
+    const int q = find_pos(adj, bj, toj, w);
+    return q < 0 ? 0xffffffffu : (uint32_t)(bj + q);
+}
+
 // Is y (packed entry w) a neighbour of j?  As edge_to, without the edge id.
 __device__ __forceinline__ bool adjacent(const int64_t *__restrict__ rowptr,
                                          const uint32_t *__restrict__ adj,

@@ -39,14 +39,15 @@ struct EdgeParams {
     const uint32_t *ustart;
     const uint32_t *ulist;     // units this launch takes (NULL: units 0 .. nunits - 1)
     uint32_t nunits;
-    const uint32_t *tau;
+    const uint32_t *tau;       // per edge id, L counts
+    const uint32_t *tau_adj;   // per adjacency entry: tau of its edge (L counts)
     const uint32_t *theta;
     const uint32_t *dsum;
     const unsigned long long *c4e;
     const unsigned long long *k4e;
     int32_t L, P, k, level;
     int64_t nbits;
-    uint32_t *emap;            // per CTA, nbits entries: edge id of (j, y) for y in Gamma_j
+    uint32_t *emap;            // per CTA, nbits entries: the entry of y in Gamma_j
     unsigned long long *tsum;  // split mode: B, C and DT (3 L^2 uint64) per order position
     int64_t qbase;             // split mode: order position of tsum's first row
     unsigned long long *queue;
@@ -298,11 +299,14 @@ __device__ void edge_finish(const EdgeParams &p, unsigned long long *shist, int6
 // (type, id), so the scan skips the type ranges of Gamma_i that hold no T
 // member and leaves a range as soon as its |T^a| members are found (T members
 // have high degree, i.e. small ids, so they come early in their range).
-// find(w, ejy) tells whether the entry w of Gamma_i lies in Gamma_j, and gives
-// the edge id of (j, w).  The T members of a chunk (all of type a) go to lane
-// groups of 8 (L <= 8) or 16 lanes; lane b of a group reads tau_jy[b],
-// tau_iy[b] and d_y^b (three coalesced rows), the groups' values are added
-// across the warp and the first group adds them to B, C, DT.  Called by all
+// find(w, pjy) tells whether the entry w of Gamma_i lies in Gamma_j, and gives
+// the adjacency entry of the edge (j, w).  Triangle counts are read per
+// adjacency entry: tau_iy at Gamma_i's own entry (along the scan) and tau_jy
+// at that entry (Gamma_j's rows stay in L2 while its unit runs).  The T
+// members of a chunk (all of type a) go to lane groups of 8 (L <= 8) or 16
+// lanes; lane b of a group reads tau_jy[b], tau_iy[b] and d_y^b (three
+// coalesced rows), the groups' values are added across the warp and the
+// first group adds them to B, C, DT.  Called by all
 // 32 lanes; adds the entries of Gamma_i it read to *read and the T members to
 // *nt (lane-uniform values).
 template <class Find>
@@ -341,10 +345,9 @@ __device__ __forceinline__ void tsum_edge(const EdgeParams &p, int64_t e, int64_
                 const uint32_t ej = __shfl_sync(kFull, ejy, src);
                 uint32_t vb = 0, vc = 0, vd = 0;
                 if (has && b < L) {
-                    const uint32_t ei = __ldg(p.eid + bi + c0 + src);
                     const int32_t *ty = p.toff + (int64_t)(wy & TG_IDMASK) * (L + 1);
-                    vb = __ldg(p.tau + (int64_t)ej * L + b);
-                    vc = __ldg(p.tau + (int64_t)ei * L + b);
+                    vb = __ldg(p.tau_adj + (int64_t)ej * L + b);
+                    vc = __ldg(p.tau_adj + (bi + c0 + src) * L + b);
                     vd = (uint32_t)(__ldg(ty + b + 1) - __ldg(ty + b));
                 }
                 for (int o = gsz; o < 32; o <<= 1) {
@@ -422,7 +425,7 @@ __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc
                 const uint32_t id = __ldg(adj + bj + x) & TG_IDMASK;
                 if ((int64_t)id < p.nbits) {
                     atomicOr(&bm[id >> 5], 1u << (id & 31u));
-                    emap[id] = __ldg(p.eid + bj + x);
+                    emap[id] = (uint32_t)(bj + x);
                 }
             }
             cur_j = j;
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(kWrite ? kTsumThreads : kEdgeMaxThreads) k_cyc
                         ejy = __ldcg(emap + id);  // written for this j before the barrier
                         return true;
                     }
-                    ejy = edge_to(rowptr, adj, p.eid, p.toff, L, bj, dj, toj, pj, w);
+                    ejy = entry_to(rowptr, adj, p.toff, L, bj, dj, toj, pj, w);
                     return ejy != 0xffffffffu;
                 };
                 unsigned long long rd = 0, nt = 0;
@@ -516,7 +519,7 @@ __global__ void __launch_bounds__(kTsumLightWarps * 32) k_cyc_tsum_light(EdgePar
         for (int q = lane; q < (1 << TG_LIGHT_LG); q += 32) hk[q] = 0u;
         __syncwarp();
         for (int x = lane; x < dj; x += 32)
-            hmap_put(hk, hv, TG_LIGHT_LG, __ldg(adj + bj + x) & TG_IDMASK, __ldg(p.eid + bj + x));
+            hmap_put(hk, hv, TG_LIGHT_LG, __ldg(adj + bj + x) & TG_IDMASK, (uint32_t)(bj + x));
         __syncwarp();
         for (uint32_t q = p0; q < p1; ++q) {
             const int64_t e = p.order[q];
@@ -604,7 +607,8 @@ int smem_optin_e() {
 
 int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int64_t count,
                  const tg_units &un, uint64_t *rows, int64_t width,
-                 unsigned long long *hist, const uint32_t *tau, const uint32_t *theta,
+                 unsigned long long *hist, const uint32_t *tau, const uint32_t *tau_adj,
+                 const uint32_t *theta,
                  const uint32_t *dsum, const unsigned long long *c4e,
                  const unsigned long long *k4e, unsigned long long *work, const tg_tune &t,
                  cudaStream_t s) {
@@ -621,6 +625,7 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
     p.order = order;
     p.ustart = un.ustart.p;
     p.tau = tau;
+    p.tau_adj = tau_adj;
     p.theta = theta;
     p.dsum = dsum;
     p.c4e = c4e;

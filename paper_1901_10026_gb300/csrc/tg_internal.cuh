@@ -158,15 +158,23 @@ struct tg_units {
 // type multiset (C(L+3,4) zeroed entries), the non-induced 4-cycles (cycles)
 // or the 4-cliques (cliques); tg_cyc_correct then adds their share
 // to undivided sums counted with Q = C4 = 0.
+// Share of the whole-graph enumerations a call takes when the global count is
+// split across ranks: the 4-cycle anchors and the 4-clique lowest nodes v
+// with v mod count == index (ids are degree-ordered, so hubs spread evenly).
+struct tg_part {
+    int32_t index = 0, count = 1;
+};
+
 int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long *g4,
-                  unsigned long long *work, const tg_tune &t, cudaStream_t s);
+                  unsigned long long *work, const tg_tune &t, const tg_part &part, cudaStream_t s);
 int tg_cyc_cliques(const tg_graph *g, unsigned long long *k4e, unsigned long long *g4,
-                   unsigned long long *work, const tg_tune &t, cudaStream_t s);
+                   unsigned long long *work, const tg_tune &t, const tg_part &part, cudaStream_t s);
 int tg_cyc_correct(unsigned long long *hist, int L, const unsigned long long *c4w,
                    const unsigned long long *k4, cudaStream_t s);
 int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int64_t count,
                  const tg_units &un, uint64_t *rows, int64_t width,
-                 unsigned long long *hist, const uint32_t *tau, const uint32_t *theta,
+                 unsigned long long *hist, const uint32_t *tau, const uint32_t *tau_adj,
+                 const uint32_t *theta,
                  const uint32_t *dsum, const unsigned long long *c4e,
                  const unsigned long long *k4e, unsigned long long *work, const tg_tune &t,
                  cudaStream_t s);
@@ -174,6 +182,14 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
 // Counts through Alg. 1's typed triangle counts (tg_reuse.cu).  full_order is
 // the grouped order of all M edges; order[0..count) the edges to count.  With
 // TG_KERNEL_CYCLES (or AUTO) the per-edge pass is tg_cyc_*, else k_count_reuse.
+// With part.count > 1 (global sums only, k = 4), the call is one share of a
+// split count: order[0..count) is its slice of the edges, and the 4-cycle and
+// 4-clique totals (with their correction of the sums) are the part's own.
 int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_order,
                    const uint32_t *order, int64_t count, uint64_t *rows, int64_t width,
-                   unsigned long long *hist, const tg_tune &t, cudaStream_t s);
+                   unsigned long long *hist, const tg_tune &t, cudaStream_t s,
+                   const tg_part &part = tg_part());
+
+// Per-edge rows of the whole graph into device memory `rows` (M x
+// tg_slots(L, k, level)), queued on s (tg_count.cu).
+int tg_rows_device(const tg_graph *g, int k, int level, uint64_t *rows, cudaStream_t s);

@@ -206,6 +206,17 @@ __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32
     }
 }
 
+// tau_adj[p L + b] = tau[eid[p] L + b]: the triangle counts of every
+// adjacency entry's edge, one thread per count.
+__global__ void k_tau_adj(const uint32_t *eid, const uint32_t *tau, int64_t entries, int32_t L,
+                          uint32_t *tau_adj) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < entries * L;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = x / L;
+        tau_adj[x] = __ldg(tau + (int64_t)__ldg(eid + q) * L + (x - q * L));
+    }
+}
+
 // Light units: one warp per unit, Gamma_j (at most TG_LIGHT_DEGREE entries)
 // in a per-warp hash set, the unit's edges one after the other; no CTA barrier.
 constexpr int kLightWarps = 8;
@@ -962,8 +973,9 @@ int launch_reuse_u(const ReuseParams &p, int threads, size_t smem, int grid_limi
 // counts for the edges order[0..count) (grouped by their high-degree end).
 int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_order,
                    const uint32_t *order, int64_t count, uint64_t *rows, int64_t width,
-                   unsigned long long *hist, const tg_tune &t, cudaStream_t s) {
-    if (count <= 0) return TG_OK;
+                   unsigned long long *hist, const tg_tune &t, cudaStream_t s,
+                   const tg_part &part) {
+    if (count <= 0 && part.count <= 1) return TG_OK;  // a share of a split count still enumerates
     const int L = g->L, L2 = L * L;
     const int64_t M = g->M, n = g->n;
     unsigned long long *work = nullptr;
@@ -1053,31 +1065,42 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
         DevBuf<unsigned long long> c4e, k4e, g4c, g4k;
         // whole-graph global sums: the 4-cycle and 4-clique terms come from
         // their type-multiset totals instead of per-edge counters
-        const bool fast = k == 4 && hist && !rows && order == full_order && count == M;
+        // (a share of a split count: the part's own enumeration totals)
+        const bool split_part = part.count > 1;
+        if (split_part && (k != 4 || !hist || rows)) return TG_EINVAL;
+        const bool fast =
+            k == 4 && hist && !rows && (split_part || (order == full_order && count == M));
         if (fast) {
             const int64_t n4 = tg_binom(L + 3, 4);
             if (!g4c.alloc(n4, s) || !g4k.alloc(n4, s)) return TG_ENOMEM;
             TG_TRY_CUDA(cudaMemsetAsync(g4c.p, 0, n4 * 8, s));
             TG_TRY_CUDA(cudaMemsetAsync(g4k.p, 0, n4 * 8, s));
-            TG_TRY(tg_cyc_cycles(g, nullptr, g4c.p, work, t, s));
+            TG_TRY(tg_cyc_cycles(g, nullptr, g4c.p, work, t, part, s));
         } else if (k == 4) {
             const int P = L * (L + 1) / 2;
             if (!c4e.alloc((size_t)M * L2, s) || !k4e.alloc((size_t)M * P, s)) return TG_ENOMEM;
             TG_TRY_CUDA(cudaMemsetAsync(c4e.p, 0, (size_t)M * L2 * 8, s));
             TG_TRY_CUDA(cudaMemsetAsync(k4e.p, 0, (size_t)M * P * 8, s));
-            TG_TRY(tg_cyc_cycles(g, c4e.p, nullptr, work, t, s));
+            TG_TRY(tg_cyc_cycles(g, c4e.p, nullptr, work, t, tg_part(), s));
         }
         TG_TRY_CUDA(cudaEventRecord(g_last.ev[3], s));
-        if (k == 4) TG_TRY(tg_cyc_cliques(g, k4e.p, g4k.p, work, t, s));
+        if (k == 4) TG_TRY(tg_cyc_cliques(g, k4e.p, g4k.p, work, t, fast ? part : tg_part(), s));
         TG_TRY_CUDA(cudaEventRecord(g_last.ev[4], s));
         tg_units un2;
         tg_units *ue = &un;
         if (order != full_order || count != M) {
-            TG_TRY(edge_units(g, order, count, s, un2));
+            if (count > 0) TG_TRY(edge_units(g, order, count, s, un2));
             ue = &un2;
         }
-        TG_TRY(tg_cyc_edges(g, k, level, order, count, *ue, rows, width, hist, tau.p, theta.p,
-                            dsum.p, c4e.p, k4e.p, work, t, s));
+        // triangle counts per adjacency entry, for the per-edge pass's reads
+        DevBuf<uint32_t> tau_adj;
+        if (k == 4 && count > 0) {
+            if (!tau_adj.alloc((size_t)2 * M * L, s)) return TG_ENOMEM;
+            k_tau_adj<<<grid_r(2 * M * L), 256, 0, s>>>(g->eid, tau.p, 2 * M, L, tau_adj.p); tg_note_launch();
+            TG_TRY_CUDA(cudaGetLastError());
+        }
+        TG_TRY(tg_cyc_edges(g, k, level, order, count, *ue, rows, width, hist, tau.p, tau_adj.p,
+                            theta.p, dsum.p, c4e.p, k4e.p, work, t, s));
         if (fast) TG_TRY(tg_cyc_correct(hist, L, g4c.p, g4k.p, s));
         TG_TRY_CUDA(cudaEventRecord(g_last.ev[5], s));
         g_last.edges = (uint64_t)count;

@@ -1,11 +1,15 @@
-"""Edge sharding across ranks for one graph's global count.
+"""Sharding one graph's global count across ranks.
 
-Edges are independent units (Sec. "Parallelization": each worker holds the
-graph and counts its own edges), so rank r counts a contiguous range of the
-canonical edge order with ``tg_count_range`` and the ranks add their
-undivided per-configuration sums; the division by |E(H)| happens once, after
-the sum.  The only exchange is that one sum-reduce of a histogram of
-``tg_global_len(L, k)`` entries.
+The global count is a sum over edges (Sec. "Global Typed Graphlet Counts";
+Sec. "Parallelization": each worker holds the graph and counts its own
+edges), so every rank forms undivided per-configuration sums of its share and
+the ranks add them; the division by |E(H)| happens once, after the sum.  The
+only exchange is that one sum-reduce of a histogram of ``tg_global_len(L, k)``
+entries.  On the GPU a rank's share is ``tg_count_shard(g, k, rank, world)``
+(a cost-balanced slice of the per-edge pass plus its share of the whole-graph
+4-cycle and 4-clique enumerations); the contiguous edge ranges below are the
+same decomposition for per-edge counters (``tg_count_range``) and for the CPU
+tests.
 
 Host logic only (no counting here); the device work is the library's.
 """
