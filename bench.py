@@ -68,9 +68,12 @@ def parse():
                     help="end-to-end repeats (host arrays in, histogram out)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="rmat23",
                     help="rmat23 is the benchmark; the others are profiling and scale cases")
-    ap.add_argument("--mode", choices=["graph", "batch", "serve"], default="graph",
+    ap.add_argument("--mode", choices=["graph", "batch", "serve", "sweeps"], default="graph",
                     help="graph: one graph per step (default); batch: the 10,000-graph batched "
-                         "workload; serve: the Poisson request stream")
+                         "workload; serve: the Poisson request stream; sweeps: the paper's "
+                         "synthetic series (Erdos-Renyi scalability, number of types, type "
+                         "permutations)")
+    ap.add_argument("--permutations", type=int, default=100)
     ap.add_argument("--batch-graphs", type=int, default=10000)
     ap.add_argument("--kernel", choices=["cycles", "reuse", "cta", "warp"], default="cycles",
                     help="counting kernel of the graph mode (tg_set_tune): cycles is the default path")
@@ -175,20 +178,57 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def committed_traffic(workload):
-    """DRAM bytes per edge of the per-edge pass from the committed ncu summary,
-    used only for the workload it was taken on (scaled by edges) and while the
-    kernel source still matches the one profiled."""
-    path = os.path.join(ROOT, "profiles", "k_cyc_edge_traffic.json")
-    src = os.path.join(ROOT, "paper_1901_10026_gb300", "csrc", "tg_edges.cu")
+# sources each phase's kernels are built from; a recorded traffic figure
+# stands only while they are unchanged
+PHASE_SOURCES = {
+    "tau": ["tg_reuse.cu", "tg_device.cuh"],
+    "count": ["tg_edges.cu", "tg_device.cuh"],
+    "cycles": ["tg_cycles.cu", "tg_device.cuh"],
+    "cliques": ["tg_cycles.cu", "tg_device.cuh"],
+}
+
+
+def phase_sources_sha256(phase):
+    h = hashlib.sha256()
+    for name in PHASE_SOURCES[phase]:
+        h.update(open(os.path.join(ROOT, "paper_1901_10026_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
+
+
+def committed_traffic(workload, phase):
+    """DRAM bytes per unit of one phase (per edge for tau and count, per wedge
+    for cycles) from the committed ncu record, used only for the workload it
+    was taken on and while the phase's kernel sources match the ones profiled."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     try:
-        rec = json.load(open(path))
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("source_sha256") != digest or rec.get("workload") != workload:
+        rec = json.load(open(path))[phase]
+        if rec.get("sources_sha256") != phase_sources_sha256(phase) or rec.get("workload") != workload:
             return None
-        return float(rec["dram_bytes_per_edge"])
-    except (OSError, KeyError, ValueError):
+        return float(rec["dram_bytes_per_unit"])
+    except (OSError, KeyError, ValueError, TypeError):
         return None
+
+
+def phase_bytes(tm, L, M, sum_min_deg):
+    """Algorithmic bytes of each phase of one count (what the phase must move at
+    least, whatever its kernels do):
+      tau     (Alg. 1) the shorter endpoint list of every edge (4 B an entry),
+              the edge's endpoints (8 B) and its L typed triangle counts
+              written (4L B);
+      count   (per-edge pass) 4 B per Gamma_i entry read, per T member its two
+              edge ids, its tau rows toward i and j and its typed offsets
+              (4(3L+3) B), per edge its order entry, endpoints, tau row,
+              typed offsets, degrees and types of i and j and their Theta and
+              D rows (28 + 12L + 16L^2 B);
+      cycles  4 B per degree-ordered wedge (the far end read once);
+      cliques no HBM minimum is stated (candidate tests are on-chip)."""
+    return {
+        "tau": 4.0 * sum_min_deg + (8.0 + 4.0 * L) * M,
+        "count": (4.0 * tm["gamma_entries"] + tm["t_members"] * 4.0 * (3 * L + 3) +
+                  tm["edges"] * (28.0 + 12.0 * L + 16.0 * L * L)),
+        "cycles": 4.0 * tm["wedges"],
+        "cliques": None,
+    }
 
 
 def oracle_sample(og, seconds, max_edges, seed):
@@ -460,6 +500,98 @@ def run_serve(args):
     return 0
 
 
+def _time_count(tg, g, k, reps=3):
+    """Median device time (CUDA events, seconds) of tg_count_global on a built graph."""
+    import torch
+    out = torch.zeros(tg.tg_global_len(g.L, k), dtype=torch.int64, device="cuda")
+    tg.tg_count_global(g, k, out)  # warm
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        tg.tg_count_global(g, k, out)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    return statistics.median(ts), out.cpu().numpy().view(np.uint64)
+
+
+def run_sweeps(args):
+    """The paper's synthetic series (Sec. "Scalability", Sec. "Synthetic Graph
+    Experiments", the type-permutation null model of Sec. "Exploratory
+    Analysis"), each count timed on the device after a warm-up."""
+    import torch
+
+    import paper_1901_10026_gb300 as tg
+    from paper_1901_10026_gb300 import synth
+
+    tg.tg_set_memory_retention(args.retain_gib << 30)
+    dev = torch.device("cuda", 0)
+
+    def built(G):
+        return tg.tg_build_csr(G.n, torch.from_numpy(G.src).to(dev), torch.from_numpy(G.dst).to(dev),
+                               torch.from_numpy(G.types).to(dev), G.L)
+
+    scal = []
+    for n in (100, 1000, 10000, 100000, 1000000):
+        G = synth.er_avg_degree(n, 10.0, 3)
+        g = built(G)
+        sec, _ = _time_count(tg, g, 4)
+        scal.append({"n": n, "M": g.M, "seconds": sec, "edges_per_s": g.M / sec})
+        g.close()
+    types = {"er": [], "cl": []}
+    for L in range(2, 10):
+        for fam, G in (("er", synth.er_exact(100000, 1000000, L)), ("cl", synth.cl_sweep(100000, 1000000, L))):
+            g = built(G)
+            sec, h = _time_count(tg, g, 4)
+            types[fam].append({"L": L, "M": g.M, "max_degree": g.max_degree, "seconds": sec,
+                               "edges_per_s": g.M / sec, "typed_graphlets_seen": int(np.count_nonzero(h))})
+            g.close()
+    # null model: one Chung-Lu topology, its Zipf types and random permutations
+    # of them, each counted by the single-graph path (graph build included)
+    r = synth.rng(13, 1)
+    base = synth.cl_sweep(100000, 1000000, 5)
+    base.types = synth.zipf_types(base.n, 5, 1.2, r)
+    perms = [base.types] + synth.type_permutations(base.types, args.permutations)
+    src_d = torch.from_numpy(base.src).to(dev)
+    dst_d = torch.from_numpy(base.dst).to(dev)
+    glen = tg.tg_global_len(5, 4)
+    hist = torch.zeros((len(perms), glen), dtype=torch.int64, device=dev)
+    typ_all = [torch.from_numpy(t).to(dev) for t in perms]
+    g = tg.tg_build_csr(base.n, src_d, dst_d, typ_all[0], 5)
+    tg.tg_count_global(g, 4, hist[0])  # warm
+    g.close()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for q, t in enumerate(typ_all):
+        g = tg.tg_build_csr(base.n, src_d, dst_d, t, 5)
+        tg.tg_count_global(g, 4, hist[q])
+        g.close()
+    b.record()
+    torch.cuda.synchronize()
+    null_s = a.elapsed_time(b) / 1e3
+    h = hist.cpu().numpy().view(np.uint64).astype(np.float64)
+    actual, null = h[0], h[1:]
+    mu, sd = null.mean(axis=0), null.std(axis=0)
+    z = np.where(sd > 0, (actual - mu) / np.where(sd > 0, sd, 1.0), 0.0)
+    line = {
+        "metric": "synthetic sweeps", "mode": "sweeps", "n_gpus": 1, "unit": "edges/s",
+        "higher_is_better": True, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "Erdos-Renyi n=1e2..1e6 avg degree 10 L=3; ER and Chung-Lu n=1e5 "
+                               "m=1e6 L=2..9 uniform; Chung-Lu n=1e5 m=1e6 L=5 Zipf(1.2) with "
+                               f"{args.permutations} type permutations; global k=4"},
+        "er_scalability": scal, "number_of_types": types,
+        "null_model": {"graphs": len(perms), "permutations": args.permutations, "seconds": null_s,
+                       "graphs_per_s": len(perms) / null_s,
+                       "how": "tg_build_csr + tg_count_global per type vector, one topology",
+                       "configs": glen, "configs_beyond_3_sd": int(np.count_nonzero(np.abs(z) > 3)),
+                       "configs_absent_in_actual_but_in_null": int(np.count_nonzero((actual == 0) & (mu > 0)))},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -469,6 +601,8 @@ def main():
         return run_batch(args) if rank == 0 else 0
     if args.mode == "serve":
         return run_serve(args) if rank == 0 else 0
+    if args.mode == "sweeps":
+        return run_sweeps(args) if rank == 0 else 0
 
     import torch
     import torch.distributed as tdist
@@ -499,7 +633,10 @@ def main():
     g0 = tg.tg_build_csr(G.n, src_d, dst_d, typ_d, L)
     M = g0.M
     work_entries = tg.tg_work_model(g0)
-    log_delta = math.log2(max(2, g0.max_degree))
+    eu, evv = tg.tg_edge_list(g0)
+    deg = np.bincount(np.concatenate([eu, evv]), minlength=G.n)
+    sum_min_deg = int(np.minimum(deg[eu], deg[evv]).astype(np.int64).sum())
+    del eu, evv, deg
     g0.close()
 
     out_d = torch.zeros(glen, dtype=torch.int64, device=dev)
@@ -530,7 +667,7 @@ def main():
     launches0 = tg.tg_launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    count_ms, timings = [], []
+    timings = []
     with ClockSampler(local) as clk:
         if world > 1:
             tdist.barrier()
@@ -540,9 +677,7 @@ def main():
             ev[s][0].record(stream)
             step()
             ev[s][1].record(stream)
-            tm = tg.tg_last_timing()
-            timings.append(tm)
-            count_ms.append(tm["count_ms"])
+            timings.append(tg.tg_last_timing())
         torch.cuda.synchronize()
         if world > 1:
             tdist.barrier()
@@ -577,39 +712,41 @@ def main():
     h2d = G.src.nbytes + G.dst.nbytes + G.types.nbytes
     d2h = glen * 8
 
-    # roofline of the per-edge pass (k_cyc_edge<1> on heavy units, the largest
-    # kernel of the launch list, with k_cyc_tsum_light and k_cyc_finish), one
-    # pass per step, timed by the library's events around it on this stream
+    # roofline per phase of the count (library events on this stream around
+    # each phase, mean over the timed steps); the slowest phase is reported
     peak, peak_kind = measured_peak_gbs()
-    kern_s = statistics.mean(count_ms) / 1e3
     tm = timings[-1]
-    units = tm["edges"]
-    paper_bytes = 4.0 * work_entries * (units / M)
-    # bytes the per-edge pass must read: Gamma_i; per T member its two edge
-    # ids, tau rows of (i, y) and (j, y) and its typed-degree offsets; per edge
-    # the order and endpoint entries, its tau row, the typed offsets, degrees
-    # and types of i and j and their Theta and D rows (L x L uint32 each)
-    own_bytes = (4.0 * tm["gamma_entries"] + tm["t_members"] * 4.0 * (3 * L + 3) +
-                 units * (4.0 + 8.0 + 4.0 * L + 8.0 * (L + 1) + 16.0 + 2.0 + 16.0 * L * L))
-    traffic_per_edge = committed_traffic(args.workload)
-    phase_ms = {"tau": tm["tau_ms"], "aggregate": tm["aggregate_ms"], "cycles": tm["cycles_ms"],
-                "cliques": tm["cliques_ms"], "count": tm["count_ms"]}
+    mean_ms = {ph: statistics.mean(t[f"{ph}_ms"] for t in timings)
+               for ph in ("tau", "aggregate", "count", "cycles", "cliques")}
+    pbytes = phase_bytes(tm, L, M, sum_min_deg)
+    phases = {}
+    for ph in ("tau", "count", "cycles", "cliques"):
+        ms = mean_ms[ph]
+        b = pbytes[ph]
+        units = M if ph in ("tau", "count") else tm["wedges"]
+        per_unit = committed_traffic(args.workload, ph)
+        phases[ph] = {"ms": ms, "algorithmic_bytes": b,
+                      "achieved_gbs": (b / (ms / 1e3) / 1e9) if (b and ms > 0) else None,
+                      "traffic": (per_unit * units) if (per_unit is not None and ph != "cliques") else None}
+        phases[ph]["frac"] = (phases[ph]["achieved_gbs"] / peak
+                              if phases[ph]["achieved_gbs"] is not None else None)
+    dominant = max(("tau", "count", "cycles"), key=lambda ph: phases[ph]["ms"])
+    kernels = {"tau": "k_tau (Alg. 1 typed triangle counts)",
+               "count": "per-edge pass: k_cyc_edge + k_cyc_tsum_light + k_cyc_finish",
+               "cycles": "4-cycle enumeration: k_c4_bin_walk + k_c4_bin_pairs + walk waves"}
+    d = phases[dominant]
     roofline = {
-        "bound": "hbm", "achieved": own_bytes / kern_s / 1e9, "peak": peak, "unit": "GB/s",
-        "frac": own_bytes / kern_s / 1e9 / peak,
-        "traffic": (traffic_per_edge * units) if traffic_per_edge is not None else None,
-        "peak_kind": peak_kind, "kernel": "per-edge pass: k_cyc_edge<1> + k_cyc_tsum_light + k_cyc_finish",
-        "kernel_ms": kern_s * 1e3,
-        "algorithmic_bytes": own_bytes,
-        "algorithmic_basis": "per-edge pass: 4 B per Gamma_i entry, 4(3L+3) B per T member, "
-                             "28+12L+16L^2 B per edge",
-        "paper_model_bytes": paper_bytes,
-        "paper_model_gbs": paper_bytes / (ms_per_step / 1e3) / 1e9,
-        "paper_model_basis": "paper work model (4 B x (2 d_i + d_j + sum of d_w over S_i u S_j u T) "
-                             "per edge) over the whole step",
-        "phase_ms": phase_ms,
-        "work": {"gamma_entries": tm["gamma_entries"], "t_members": tm["t_members"],
+        "bound": "hbm", "achieved": d["achieved_gbs"], "peak": peak, "unit": "GB/s",
+        "frac": d["frac"], "traffic": d["traffic"], "peak_kind": peak_kind,
+        "phase": dominant, "kernel": kernels[dominant], "kernel_ms": d["ms"],
+        "algorithmic_bytes": d["algorithmic_bytes"],
+        "phases": phases, "aggregate_ms": mean_ms["aggregate"],
+        "work": {"edges": tm["edges"], "sum_min_degree": int(sum_min_deg),
+                 "gamma_entries": tm["gamma_entries"], "t_members": tm["t_members"],
                  "wedges": tm["wedges"], "clique_tests": tm["clique_tests"], "cliques": tm["cliques"]},
+        "paper_work_model_bytes": 4.0 * work_entries,
+        "paper_work_model_basis": "4 B x (2 d_i + d_j + sum of d_w over S_i u S_j u T) per edge, "
+                                  "the paper's per-edge cost model; context only",
     }
 
     if rank == 0:

@@ -345,7 +345,10 @@ typedef struct {
                             held in memory at once (the per-edge pass runs in
                             batches of work units); 0: as many as fit in a
                             quarter of free memory                          */
-    int32_t reserved;
+    int32_t c4_bin_fill; /* CYCLES kernel, global counts: a costly 4-cycle
+                            anchor goes to the binned waves when its walk
+                            averages at least this many wedges per far-end
+                            window it spans (0: 32)                          */
 } tg_tune;
 
 #define TG_EDGE_PASS_AUTO 0
@@ -353,6 +356,22 @@ typedef struct {
 
 int tg_set_tune(const tg_tune *t); /* NULL restores the defaults */
 int tg_get_tune(tg_tune *t);
+
+/*
+ * Launch-configuration search for one graph class.  Times tg_count_global of
+ * `g` (CUDA events on `stream`, one warm-up count first) under a coordinate
+ * search that starts from the current tuning: unroll {2, 4}, then (k = 4)
+ * c4_bin_fill {8, 32, 128} and edge_pass {AUTO, FUSED}, then hash_slots
+ * {4096, 32}; a value is kept when it beats the best so far by 2 %.  The
+ * winner becomes the process-wide tuning (as tg_set_tune) and is written to
+ * `best` when non-NULL.  Results are cached per (device, L, k, bit length of
+ * M, bit length of the maximum degree): a graph of a cached class takes the
+ * cached tuning at once, with no count.  Uncached it costs about seven counts
+ * of `g`.  Counts never depend on the result.  On error the tuning in force
+ * before the call is restored.  Synchronises `stream`.
+ */
+int tg_autotune(const tg_graph *g, int32_t k, tg_tune *best, void *stream);
+int tg_autotune_reset(void); /* forgets every cached class */
 
 /* ---------------------------------------------------------- batches ----- */
 /*

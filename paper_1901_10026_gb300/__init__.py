@@ -25,7 +25,7 @@ __all__ = [
     "tg_count_global", "tg_count_global_noalloc", "tg_count_per_edge", "tg_count_shard", "tg_count_per_edge_sparse", "tg_sparse_ids", "tg_sparse_id", "Batch", "tg_count_batch", "Server", "tg_count_range", "tg_global_finalize",
     "tg_work_model", "tg_slots", "tg_global_len", "tg_config_count", "tg_config_rank",
     "tg_config_unrank", "tg_paper_hash", "tg_slot_config", "tg_strerror", "tg_version",
-    "tg_debug_fail_alloc", "tg_set_tune", "tg_get_tune", "tg_launch_count", "tg_last_timing",
+    "tg_debug_fail_alloc", "tg_set_tune", "tg_get_tune", "tg_autotune", "tg_autotune_reset", "tg_launch_count", "tg_last_timing",
     "tg_last_cuda_error", "tg_set_memory_retention", "tg_trim_memory", "TG_GRAPHLET", "TG_ORBIT",
 ]
 
@@ -56,7 +56,7 @@ class TGTune(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("cta_threads", ctypes.c_int32), ("unroll", ctypes.c_int32),
                 ("hash_slots", ctypes.c_int32), ("bitmap_bits", ctypes.c_int64),
                 ("grid_limit", ctypes.c_int32), ("edge_pass", ctypes.c_int32),
-                ("edge_batch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("edge_batch", ctypes.c_int32), ("c4_bin_fill", ctypes.c_int32)]
 
 
 class TGTiming(ctypes.Structure):
@@ -165,6 +165,8 @@ def lib():
             "tg_serve_destroy": (None, [vp]),
             "tg_last_timing": (ctypes.c_int, [vp]),
             "tg_get_tune": (ctypes.c_int, [vp]),
+            "tg_autotune": (ctypes.c_int, [vp, i32, vp, vp]),
+            "tg_autotune_reset": (ctypes.c_int, []),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -515,13 +517,27 @@ def tg_work_model(g: Graph, stream=None) -> int:
 
 
 def tg_set_tune(kernel=0, cta_threads=0, unroll=0, hash_slots=0, bitmap_bits=0, grid_limit=0,
-                edge_pass=0, edge_batch=0, reset=False) -> None:
+                edge_pass=0, edge_batch=0, c4_bin_fill=0, reset=False) -> None:
     """Set the counting kernels' launch configuration (``reset`` restores defaults)."""
     if reset:
         _check(lib().tg_set_tune(None), "tg_set_tune")
         return
-    t = TGTune(kernel, cta_threads, unroll, hash_slots, bitmap_bits, grid_limit, edge_pass, edge_batch, 0)
+    t = TGTune(kernel, cta_threads, unroll, hash_slots, bitmap_bits, grid_limit, edge_pass, edge_batch,
+               c4_bin_fill)
     _check(lib().tg_set_tune(ctypes.byref(t)), "tg_set_tune")
+
+
+def tg_autotune(g: Graph, k: int, stream=None) -> dict:
+    """Search the launch configuration for ``g``'s class (tg_autotune); the winner
+    becomes the process-wide tuning and is returned as a dict."""
+    t = TGTune()
+    _check(lib().tg_autotune(g.handle, int(k), ctypes.byref(t), _stream(stream)), "tg_autotune")
+    return {f: getattr(t, f) for f, _ in TGTune._fields_}
+
+
+def tg_autotune_reset() -> None:
+    """Forget every cached autotune class."""
+    _check(lib().tg_autotune_reset(), "tg_autotune_reset")
 
 
 def tg_get_tune() -> dict:

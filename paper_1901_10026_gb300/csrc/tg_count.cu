@@ -18,7 +18,10 @@
 // Membership of a neighbour w in Gamma_i or Gamma_j is a binary search inside
 // the typed range Gamma_i^{phi(w)} (lists are sorted by (type, id)).
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "tg_device.cuh"
@@ -875,6 +878,7 @@ extern "C" int tg_set_tune(const tg_tune *t) {
         if (t->edge_pass != TG_EDGE_PASS_AUTO && t->edge_pass != TG_EDGE_PASS_FUSED)
             return TG_EINVAL;
         if (t->edge_batch < 0) return TG_EINVAL;
+        if (t->c4_bin_fill < 0 || t->c4_bin_fill > (1 << 20)) return TG_EINVAL;
         d.kernel = t->kernel;
         if (t->cta_threads) d.cta_threads = t->cta_threads;
         if (t->unroll) d.unroll = t->unroll;
@@ -883,6 +887,7 @@ extern "C" int tg_set_tune(const tg_tune *t) {
         d.grid_limit = t->grid_limit;
         d.edge_pass = t->edge_pass;
         d.edge_batch = t->edge_batch;
+        d.c4_bin_fill = t->c4_bin_fill;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune = d;
@@ -892,6 +897,108 @@ extern "C" int tg_set_tune(const tg_tune *t) {
 extern "C" int tg_get_tune(tg_tune *t) {
     if (!t) return TG_EINVAL;
     *t = tune_now();
+    return TG_OK;
+}
+
+// ---------------------------------------------------------- autotune -----
+static int check_counts(const tg_graph *g, int k);
+
+namespace {
+struct TuneKey {
+    int device, L, k, mbits, dbits;
+    bool operator<(const TuneKey &o) const {
+        return std::tie(device, L, k, mbits, dbits) < std::tie(o.device, o.L, o.k, o.mbits, o.dbits);
+    }
+};
+std::mutex g_autotune_mu;
+std::map<TuneKey, tg_tune> g_autotune_cache;
+
+int bitlen(int64_t x) {
+    int b = 0;
+    while (x > 0) ++b, x >>= 1;
+    return b;
+}
+}  // namespace
+
+extern "C" int tg_autotune_reset(void) {
+    std::lock_guard<std::mutex> lk(g_autotune_mu);
+    g_autotune_cache.clear();
+    return TG_OK;
+}
+
+extern "C" int tg_autotune(const tg_graph *g, int32_t k, tg_tune *best, void *stream) {
+    TG_TRY(check_counts(g, k));
+    const TuneKey key{g->device, g->L, k, bitlen(g->M), bitlen(g->max_degree)};
+    {
+        std::lock_guard<std::mutex> lk(g_autotune_mu);
+        auto it = g_autotune_cache.find(key);
+        if (it != g_autotune_cache.end()) {
+            TG_TRY(tg_set_tune(&it->second));
+            if (best) *best = it->second;
+            return TG_OK;
+        }
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const tg_tune before = tune_now();
+    DevBuf<uint64_t> out;
+    if (!out.alloc(tg_global_len(g->L, k), s)) return TG_ENOMEM;
+    cudaEvent_t ev[2];
+    TG_TRY_CUDA(cudaEventCreate(&ev[0]));
+    if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+        cudaEventDestroy(ev[0]);
+        return TG_ECUDA;
+    }
+    // one count under candidate c, in milliseconds
+    auto timed = [&](const tg_tune &c, float &ms) -> int {
+        TG_TRY(tg_set_tune(&c));
+        TG_TRY_CUDA(cudaEventRecord(ev[0], s));
+        TG_TRY(tg_count_global(g, k, out.p, s));
+        TG_TRY_CUDA(cudaEventRecord(ev[1], s));
+        TG_TRY_CUDA(cudaEventSynchronize(ev[1]));
+        TG_TRY_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        return TG_OK;
+    };
+    tg_tune cur = before;
+    cur.kernel = TG_KERNEL_CYCLES;
+    float cur_ms = 0.f;
+    int rc = timed(cur, cur_ms);  // warm-up: schedule, pools, module loads
+    if (rc == TG_OK) rc = timed(cur, cur_ms);
+    struct Dim {
+        int32_t tg_tune::*field;
+        std::vector<int32_t> values;
+        bool k4_only;
+    };
+    const Dim dims[] = {{&tg_tune::unroll, {2, 4}, false},
+                        {&tg_tune::c4_bin_fill, {8, 32, 128}, true},
+                        {&tg_tune::edge_pass, {TG_EDGE_PASS_AUTO, TG_EDGE_PASS_FUSED}, true},
+                        {&tg_tune::hash_slots, {4096, 32}, false}};
+    for (const Dim &d : dims) {
+        if (rc != TG_OK || (d.k4_only && k != 4)) continue;
+        tg_tune base = cur;
+        for (int32_t v : d.values) {
+            if (rc != TG_OK) break;
+            // c4_bin_fill 0 means 32: do not time the default twice
+            const int32_t now = (d.field == &tg_tune::c4_bin_fill && base.*d.field == 0) ? 32 : base.*d.field;
+            if (v == now) continue;
+            tg_tune c = base;
+            c.*d.field = v;
+            float ms = 0.f;
+            rc = timed(c, ms);
+            if (rc == TG_OK && ms < 0.98f * cur_ms) cur = c, cur_ms = ms;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc != TG_OK) {
+        tg_set_tune(&before);
+        return rc;
+    }
+    TG_TRY(tg_set_tune(&cur));
+    {
+        std::lock_guard<std::mutex> lk(g_autotune_mu);
+        g_autotune_cache[key] = cur;
+    }
+    if (best) *best = cur;
     return TG_OK;
 }
 

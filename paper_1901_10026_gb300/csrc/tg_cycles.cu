@@ -819,7 +819,7 @@ struct C4Bin {
 };
 
 constexpr int kBinUnroll = 4;
-constexpr int kBinFill = 32;            // binned when a walk averages this many wedges per window
+constexpr int kBinFill = 32;            // default: binned when a walk averages this many wedges per window
 constexpr size_t kBinTable = 64 * 1024;  // bytes of the dense far-end table
 
 // One chunk of 32 members (lane values len, bu, tu) of a binned walk unit; as
@@ -2530,9 +2530,10 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
     if (nheavy > 0 && walk_waves) {
         // global mode: each split anchor's walk is cut into position ranges of
         // about equal length (warp units); anchors whose walk averages
-        // kBinFill wedges per far-end window they span go to the binned waves,
+        // bin_fill wedges per far-end window they span go to the binned waves,
         // the others to waves of `slots` anchors counting in global memory,
         // whose far ends k_c4_pairs takes
+        const int64_t bin_fill = t.c4_bin_fill > 0 ? t.c4_bin_fill : kBinFill;
         std::vector<unsigned long long> hcost((size_t)nheavy);
         {
             DevBuf<unsigned long long> hc;
@@ -2553,7 +2554,7 @@ int tg_cyc_cycles(const tg_graph *g, unsigned long long *c4e, unsigned long long
             const int half = hdeg[q] < 65536 ? 1 : 0;
             const int wlg = c4_bin_wlg(L, half);
             const int64_t span = ((n - 1) >> wlg) - ((int64_t)heavy[q] >> wlg) + 1;
-            const bool bin = t.unroll != 1 && hcost[q] >= (unsigned long long)(kBinFill * span) &&
+            const bool bin = t.unroll != 1 && hcost[q] >= (unsigned long long)bin_fill * span &&
                              hcost[q] <= (unsigned long long)ecap;
             (bin ? lb : ls).push_back(heavy[q]);
             (bin ? db : ds).push_back(hdeg[q]);

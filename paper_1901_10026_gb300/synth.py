@@ -46,6 +46,10 @@ __all__ = [
     "batch_graph",
     "serve_stream",
     "tiny_random",
+    "er_avg_degree",
+    "er_exact",
+    "cl_sweep",
+    "type_permutations",
 ]
 
 
@@ -301,6 +305,46 @@ def serve_graph(target_edges: int, key, L: int = 6, gamma: float = 2.1) -> Typed
     u, v = chung_lu_exact(n, min(target_edges, n * (n - 1) // 4), gamma, g)
     t = uniform_types(n, L, g)
     return TypedEdgeList(n, u, v, t, L, f"serve-{key[-1]}")
+
+
+def er_avg_degree(n: int, dbar: float, L: int, seed: int = 1) -> TypedEdgeList:
+    """Erdos-Renyi G(n, p = dbar / (n - 1)), L uniform types (the paper's
+    scalability series: average degree 10, n from 100 to 10^6)."""
+    g = rng(9, seed, n, int(round(dbar * 1000)), L)
+    u, v = erdos_renyi(n, min(1.0, dbar / max(n - 1, 1)), g)
+    return TypedEdgeList(n, u, v, uniform_types(n, L, g), L, f"er-n{n}-d{dbar:g}-L{L}")
+
+
+def er_exact(n: int, m: int, L: int, seed: int = 1) -> TypedEdgeList:
+    """G(n, m): m distinct pairs drawn uniformly (repeats redrawn), L uniform
+    types (the number-of-types sweep's Erdos-Renyi graph)."""
+    g = rng(10, seed, n, m, L)
+    total = n * (n - 1) // 2
+    if m > total:
+        raise ValueError("er_exact: more edges than pairs")
+    keys = np.zeros(0, np.int64)
+    while keys.shape[0] < m:
+        draw = g.integers(0, total, size=int((m - keys.shape[0]) * 1.1) + 16, dtype=np.int64)
+        keys = np.unique(np.concatenate([keys, draw]))
+    keys = g.permutation(keys)[:m]
+    u, v = _pair_index_to_uv(keys)
+    return TypedEdgeList(n, u.astype(np.int32), v.astype(np.int32), uniform_types(n, L, g), L,
+                         f"er-n{n}-m{m}-L{L}")
+
+
+def cl_sweep(n: int, m: int, L: int, gamma: float = 2.1, seed: int = 1) -> TypedEdgeList:
+    """Chung-Lu with exactly m distinct edges, L uniform types (the
+    number-of-types sweep's skewed graph)."""
+    g = rng(11, seed, n, m, L)
+    u, v = chung_lu_exact(n, m, gamma, g)
+    return TypedEdgeList(n, u, v, uniform_types(n, L, g), L, f"cl-n{n}-m{m}-L{L}")
+
+
+def type_permutations(types: np.ndarray, count: int, seed: int = 1):
+    """`count` random permutations of a node-type vector (the null model of
+    Sec. "Exploratory Analysis": same topology, same type counts)."""
+    g = rng(12, seed, int(types.shape[0]), count)
+    return [g.permutation(types).astype(np.uint8) for _ in range(count)]
 
 
 def tiny_random(n: int, density: float, L: int, g: np.random.Generator) -> TypedEdgeList:
