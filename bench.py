@@ -48,6 +48,7 @@ WORKLOADS = {
     "er1000": "Erdos-Renyi G(n=1000, p=0.01), L=3 uniform types, global k=4",
     "rmat23": "R-MAT scale 23, edge factor 16, (0.57,0.19,0.19,0.05), L=8 uniform types, global k=4",
     "rmat20": "R-MAT scale 20, edge factor 16, (0.57,0.19,0.19,0.05), L=8 uniform types, global k=4",
+    "rmat19": "R-MAT scale 19, edge factor 16, (0.57,0.19,0.19,0.05), L=8 uniform types, global k=4",
     "rmat18": "R-MAT scale 18, edge factor 16, (0.57,0.19,0.19,0.05), L=8 uniform types, global k=4",
 }
 L2_FLUSH_BYTES = 256 << 20
@@ -80,6 +81,9 @@ def parse():
     ap.add_argument("--edge-pass", choices=["auto", "fused"], default="auto",
                     help="per-edge pass of the cycles kernel: auto (T sums through memory when they "
                          "fit) or always the fused kernel")
+    ap.add_argument("--edge-batch", type=int, default=0,
+                    help="most edges whose T sums the per-edge pass holds at once (tg_tune "
+                         "edge_batch; 0: as many as fit in a quarter of free memory)")
     ap.add_argument("--retain-gib", type=int, default=64,
                     help="tg_set_memory_retention for the graph mode, GiB (0: the default pool)")
     ap.add_argument("--serve-requests", type=int, default=2000)
@@ -627,8 +631,9 @@ def main():
     if args.kernel != "cycles":
         tg.tg_set_tune(kernel={"reuse": tg.TG_KERNEL_REUSE, "cta": tg.TG_KERNEL_CTA_BITMAP,
                                "warp": tg.TG_KERNEL_WARP_SEARCH}[args.kernel])
-    elif args.edge_pass == "fused":
-        tg.tg_set_tune(kernel=tg.TG_KERNEL_CYCLES, edge_pass=tg.TG_EDGE_PASS_FUSED)
+    else:
+        tg.tg_set_tune(kernel=tg.TG_KERNEL_CYCLES, edge_batch=args.edge_batch,
+                       edge_pass=tg.TG_EDGE_PASS_FUSED if args.edge_pass == "fused" else 0)
 
     g0 = tg.tg_build_csr(G.n, src_d, dst_d, typ_d, L)
     M = g0.M
@@ -759,7 +764,8 @@ def main():
             "config": {"workload": WORKLOADS[args.workload], "n": G.n, "M": M, "m_input": G.m, "L": L, "k": k,
                        "step": "tg_build_csr + tg_count_global from device-resident inputs",
                        "memory_retention_bytes": args.retain_gib << 30,
-                       "kernel": args.kernel,
+                       "kernel": args.kernel, "edge_pass": args.edge_pass,
+                       "edge_batch": args.edge_batch,
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"shards x{world}" if world > 1 else "single GPU"},
             "clocks": clocks,

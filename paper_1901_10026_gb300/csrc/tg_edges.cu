@@ -322,14 +322,13 @@ __device__ __forceinline__ void tsum_edge(const EdgeParams &p, int64_t e, int64_
         if (need == 0) continue;
         const int r0 = __ldg(toi + a), r1 = __ldg(toi + a + 1);
         int found = 0;
+        uint32_t nxt = r0 + lane < r1 ? __ldg(p.adj + bi + r0 + lane) : 0u;  // next chunk, in flight
         for (int c0 = r0; c0 < r1 && found < need; c0 += 32) {
             const int x = c0 + lane;
             bool isT = false;
-            uint32_t w = 0, ejy = 0;
-            if (x < r1) {
-                w = __ldg(p.adj + bi + x);
-                isT = find(w, ejy);
-            }
+            uint32_t w = nxt, ejy = 0;
+            nxt = c0 + 32 + lane < r1 ? __ldg(p.adj + bi + c0 + 32 + lane) : 0u;
+            if (x < r1) isT = find(w, ejy);
             unsigned tb = __ballot_sync(kFull, isT);
             found += __popc(tb);
             read += (unsigned long long)min(32, r1 - c0);

@@ -131,6 +131,8 @@ __device__ __forceinline__ uint32_t word_bits(int lo, int hi) {
     return up & ~((1u << lo) - 1u);
 }
 
+constexpr int kTauUnroll = 4;
+
 __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32_t *adj,
                                              const int32_t *toff, const uint8_t *ntype,
                                              const int2 *edges,
@@ -188,18 +190,28 @@ __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32
             const int32_t *toi = toff + (int64_t)i * (L + 1);
             const int ts0 = lane < L ? __ldg(toi + lane) : 0, ts1 = lane < L ? __ldg(toi + lane + 1) : 0;
             unsigned mine = 0;
-            for (int c0 = 0; c0 < di; c0 += 32) {
-                const int x = c0 + lane;
-                bool hit = false;
-                if (x < di) {
-                    const uint32_t w = __ldg(adj + bi + x);
-                    const uint32_t id = w & TG_IDMASK;
-                    if ((int)id != j)
-                        hit = (int64_t)id < nbits ? bm_test(bm, id)
-                                                  : adjacent(rowptr, adj, toff, L, bj, dj, toj, pj, w);
+            // kTauUnroll chunks of 32 entries in flight per warp
+            for (int c0 = 0; c0 < di; c0 += 32 * kTauUnroll) {
+                uint32_t wv[kTauUnroll];
+#pragma unroll
+                for (int u = 0; u < kTauUnroll; ++u) {
+                    const int x = c0 + 32 * u + lane;
+                    wv[u] = x < di ? __ldg(adj + bi + x) : 0xffffffffu;
                 }
-                const unsigned hm = __ballot_sync(kFull, hit);
-                if (lane < L) mine += __popc(hm & word_bits(ts0 - c0, ts1 - c0));
+#pragma unroll
+                for (int u = 0; u < kTauUnroll; ++u) {
+                    bool hit = false;
+                    const uint32_t w = wv[u];
+                    if (w != 0xffffffffu) {
+                        const uint32_t id = w & TG_IDMASK;
+                        if ((int)id != j)
+                            hit = (int64_t)id < nbits ? bm_test(bm, id)
+                                                      : adjacent(rowptr, adj, toff, L, bj, dj, toj, pj, w);
+                    }
+                    const unsigned hm = __ballot_sync(kFull, hit);
+                    const int cb = c0 + 32 * u;
+                    if (lane < L) mine += __popc(hm & word_bits(ts0 - cb, ts1 - cb));
+                }
             }
             if (lane < L) tau[(int64_t)e * L + lane] = mine;
         }
