@@ -29,6 +29,9 @@ VARIANTS = {
     # the per-edge pass in batches of work units (as on graphs whose T sums
     # do not fit in memory at once)
     "cycles-batched": dict(kernel=tg.TG_KERNEL_CYCLES, edge_batch=700),
+    # every costly 4-cycle anchor in the binned waves, or none of them
+    "cycles-binned-all": dict(kernel=tg.TG_KERNEL_CYCLES, c4_bin_fill=1),
+    "cycles-binned-none": dict(kernel=tg.TG_KERNEL_CYCLES, c4_bin_fill=1 << 20),
     "reuse": dict(kernel=tg.TG_KERNEL_REUSE),
     "warp-search": dict(kernel=tg.TG_KERNEL_WARP_SEARCH),
     "cta-small": dict(kernel=tg.TG_KERNEL_CTA_BITMAP, cta_threads=128, unroll=1, hash_slots=32,
