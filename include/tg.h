@@ -81,6 +81,9 @@ typedef struct tg_graph tg_graph;
 
 /* tg_build_csr flags */
 #define TG_INPUT_DEVICE 1u /* src, dst, type are device pointers (else host) */
+#define TG_DIRECTED 2u     /* also keep the direction of every pair: (src, dst)
+                              is the arc src -> dst (Sec. "Directed Typed
+                              Graphlets"); needed by tg_count_directed_*     */
 
 /* Limits checked by tg_build_csr. */
 #define TG_MAX_TYPES 16
@@ -273,6 +276,47 @@ int tg_global_finalize(int32_t L, int32_t k, const uint64_t *sums, uint64_t *out
  * for Alg. 2-3.  Writes the total entry count; computed on the GPU.
  */
 int tg_work_model(const tg_graph *g, uint64_t *entries, void *stream);
+
+/* ------------------------------------------ directed typed graphlets ---- */
+/*
+ * Directed typed 3-node graphlets (Sec. "Directed Typed Graphlets": the typed
+ * neighbourhoods split into out- and in-neighbours, Gamma_i^{t,+} and
+ * Gamma_i^{t,-}, and every combination of the split sets enumerated, each
+ * directed typed motif with an id of its own).  The graph must have been
+ * built with TG_DIRECTED; the underlying undirected graph is the one every
+ * other call counts (a pair with arcs both ways is one edge whose two ends
+ * are each other's out- and in-neighbour).
+ *
+ * A directed 3-node graphlet is a connected induced subgraph on three nodes
+ * with its arcs; it is keyed by its isomorphism class and the sorted multiset
+ * of its node types (as Def. "Typed Graphlet Instance").  The 13 classes, in
+ * this order, are defined by these representatives on nodes A, B, C
+ * (labels after the M-A-N triad census; the representative defines the class):
+ *    0 021D  B->A, B->C            7 201   A<->B, B<->C
+ *    1 021U  A->B, C->B            8 120D  B->A, B->C, A<->C
+ *    2 021C  A->B, B->C            9 120U  A->B, C->B, A<->C
+ *    3 111D  A<->B, C->B          10 120C  A->B, B->C, A<->C
+ *    4 111U  A<->B, B->C          11 210   A->B, B<->C, A<->C
+ *    5 030T  A->B, C->B, A->C     12 300   A<->B, B<->C, A<->C
+ *    6 030C  A->B, B->C, C->A
+ * Classes 0-4 and 7 have two underlying edges (paths), the others three.
+ *
+ * Per-edge rows (tg_count_directed_per_edge): M rows of tg_dir_slots(L) =
+ * 13 L uint64 in canonical edge order (tg_edge_list); slot c L + t counts the
+ * graphlets of class c on {i, j, w} with phi(w) = t containing the edge.
+ * Global counts (tg_count_directed_global): tg_dir_global_len(L) =
+ * 13 C(L+2, 3) uint64, class c's block at c C(L+2, 3), inside it the colex
+ * rank of the sorted type multiset (as tg_config_rank with k = 3); each is
+ * the per-edge sum divided by the class's number of underlying edges.
+ * Errors: TG_EINVAL (NULL arguments, a graph built without TG_DIRECTED),
+ * TG_ENOMEM, TG_ECUDA, TG_EINTERNAL (a sum not divisible).  `out`/`rows` are
+ * host or device memory; synchronises `stream`.
+ */
+#define TG_TRIAD_CLASSES 13
+int64_t tg_dir_slots(int32_t L);
+int64_t tg_dir_global_len(int32_t L);
+int tg_count_directed_per_edge(const tg_graph *g, uint64_t *rows, void *stream);
+int tg_count_directed_global(const tg_graph *g, uint64_t *out, void *stream);
 
 /* ----------------------------------------------------- no allocation ---- */
 /*

@@ -22,7 +22,8 @@ from . import build as _build
 
 __all__ = [
     "TGError", "Graph", "lib", "tg_build_csr", "tg_free_graph", "tg_graph_info", "tg_edge_list",
-    "tg_count_global", "tg_count_global_noalloc", "tg_count_per_edge", "tg_count_shard", "tg_count_per_edge_sparse", "tg_sparse_ids", "tg_sparse_id", "Batch", "tg_count_batch", "Server", "tg_count_range", "tg_global_finalize",
+    "tg_count_global", "tg_count_global_noalloc", "tg_count_directed_global",
+    "tg_count_directed_per_edge", "tg_dir_slots", "tg_dir_global_len", "TRIAD_NAMES", "tg_count_per_edge", "tg_count_shard", "tg_count_per_edge_sparse", "tg_sparse_ids", "tg_sparse_id", "Batch", "tg_count_batch", "Server", "tg_count_range", "tg_global_finalize",
     "tg_work_model", "tg_slots", "tg_global_len", "tg_config_count", "tg_config_rank",
     "tg_config_unrank", "tg_paper_hash", "tg_slot_config", "tg_strerror", "tg_version",
     "tg_debug_fail_alloc", "tg_set_tune", "tg_get_tune", "tg_autotune", "tg_autotune_reset", "tg_launch_count", "tg_last_timing",
@@ -40,6 +41,10 @@ TG_ENOMEM_ADMIT = -7
 TG_ETIMEDOUT = -8
 TG_ENOTFOUND = -9
 TG_INPUT_DEVICE = 1
+TG_DIRECTED = 2
+TG_TRIAD_CLASSES = 13
+TRIAD_NAMES = ("021D", "021U", "021C", "111D", "111U", "030T", "030C", "201", "120D", "120U",
+               "120C", "210", "300")
 TG_GRAPHLET = 0
 TG_ORBIT = 1
 
@@ -137,6 +142,10 @@ def lib():
             "tg_paper_hash": (u64, [i32, vp, i32, i32]),
             "tg_slot_config": (ctypes.c_int, [i32, i32, i32, i32, i32, i64, vp, vp, vp]),
             "tg_count_global": (ctypes.c_int, [vp, i32, vp, vp]),
+            "tg_dir_slots": (i64, [i32]),
+            "tg_dir_global_len": (i64, [i32]),
+            "tg_count_directed_global": (ctypes.c_int, [vp, vp, vp]),
+            "tg_count_directed_per_edge": (ctypes.c_int, [vp, vp, vp]),
             "tg_count_per_edge": (ctypes.c_int, [vp, i32, i32, vp, vp]),
             "tg_count_range": (ctypes.c_int, [vp, i32, i64, i64, vp, vp]),
             "tg_count_shard": (ctypes.c_int, [vp, i32, i32, i32, vp, vp]),
@@ -256,8 +265,9 @@ class Graph:
                     max_degree=self.max_degree, device_bytes=self.device_bytes, L=self.L)
 
 
-def tg_build_csr(n: int, src, dst, types, L: int, stream=None) -> Graph:
-    """Build the resident typed CSR (host numpy or device tensors)."""
+def tg_build_csr(n: int, src, dst, types, L: int, stream=None, directed: bool = False) -> Graph:
+    """Build the resident typed CSR (host numpy or device tensors); ``directed``
+    keeps the arcs src -> dst for the directed counts (TG_DIRECTED)."""
     dev = _is_device(src)
     if dev != _is_device(dst) or dev != _is_device(types):
         raise ValueError("src, dst and types must all be host arrays or all device tensors")
@@ -270,7 +280,8 @@ def tg_build_csr(n: int, src, dst, types, L: int, stream=None) -> Graph:
         raise ValueError("length mismatch")
     h = ctypes.c_void_p()
     rc = lib().tg_build_csr(int(n), m, _ptr(src), _ptr(dst), _ptr(types), int(L),
-                            TG_INPUT_DEVICE if dev else 0, _stream(stream), ctypes.byref(h))
+                            (TG_INPUT_DEVICE if dev else 0) | (TG_DIRECTED if directed else 0),
+                            _stream(stream), ctypes.byref(h))
     _check(rc, "tg_build_csr")
     return Graph(h)
 
@@ -335,6 +346,33 @@ def tg_count_global(g: Graph, k: int = 4, out=None, stream=None):
         out = np.zeros(tg_global_len(g.L, k), np.uint64)
     _check(lib().tg_count_global(g.handle, k, _ptr(out), _stream(stream)), "tg_count_global")
     return out
+
+
+def tg_dir_slots(L: int) -> int:
+    return int(lib().tg_dir_slots(L))
+
+
+def tg_dir_global_len(L: int) -> int:
+    return int(lib().tg_dir_global_len(L))
+
+
+def tg_count_directed_global(g: Graph, out=None, stream=None):
+    """Directed typed 3-node graphlet counts of a graph built with ``directed=True``:
+    13 triad classes x C(L+2, 3) type multisets (``out`` host array or device tensor)."""
+    if out is None:
+        out = np.zeros(tg_dir_global_len(g.L), np.uint64)
+    _check(lib().tg_count_directed_global(g.handle, _ptr(out), _stream(stream)),
+           "tg_count_directed_global")
+    return out
+
+
+def tg_count_directed_per_edge(g: Graph, rows=None, stream=None):
+    """Per-edge directed typed 3-node rows (M x 13 L, slot c L + t)."""
+    if rows is None:
+        rows = np.zeros((g.M, tg_dir_slots(g.L)), np.uint64)
+    _check(lib().tg_count_directed_per_edge(g.handle, _ptr(rows), _stream(stream)),
+           "tg_count_directed_per_edge")
+    return rows
 
 
 def tg_count_global_noalloc(g: Graph, k: int, out, stream=None):

@@ -235,6 +235,7 @@ int build_impl(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
                 tg_dfree(g->edges, 0, s);
                 tg_dfree(g->new2old, 0, s);
                 tg_dfree(g->eid, 0, s);
+                tg_dfree(g->adir, 0, s);
                 delete g;
             }
         }
@@ -316,9 +317,11 @@ int build_impl(int64_t n, int64_t m, const int32_t *src, const int32_t *dst,
                                                         g->adj, g->eid, g->toff); tg_note_launch();
         TG_TRY_CUDA(cudaGetLastError());
     }
+    if (flags & TG_DIRECTED) TG_TRY(tg_attach_arcs(g, psrc, pdst, m, old2new.p, s));
     TG_TRY_CUDA(cudaStreamSynchronize(s));
     TG_TRY_CUDA(cudaGetLastError());
-    g->device_bytes = (n + 1) * 8 + 2 * total * 4 + n * (L + 1) * 4 + n + M * 8 + n * 4;
+    g->device_bytes = (n + 1) * 8 + 2 * total * 4 + n * (L + 1) * 4 + n + M * 8 + n * 4 +
+                      ((flags & TG_DIRECTED) ? ((2 * M + 3) & ~(int64_t)3) : 0);
     guard.g = nullptr;
     *out = g;
     return TG_OK;
@@ -348,6 +351,7 @@ extern "C" int tg_free_graph(tg_graph *g) {
     tg_dfree(g->edges, 0, s);
     tg_dfree(g->new2old, 0, s);
     tg_dfree(g->eid, 0, s);
+    tg_dfree(g->adir, 0, s);
     (void)cudaStreamSynchronize(s);
     delete g;
     return TG_OK;
@@ -363,6 +367,7 @@ int tg_free_graph_on(tg_graph *g, cudaStream_t s) {
     tg_dfree(g->edges, 0, s);
     tg_dfree(g->new2old, 0, s);
     tg_dfree(g->eid, 0, s);
+    tg_dfree(g->adir, 0, s);
     delete g;
     return TG_OK;
 }

@@ -1,0 +1,418 @@
+// Directed typed 3-node graphlets (Sec. "Directed Typed Graphlets").
+//
+// The paper splits every typed neighbourhood into out- and in-neighbours
+// (Gamma_i^{t,+}, Gamma_i^{t,-}) and runs Alg. 1 over the combinations of the
+// split sets.  Here the split is two bits per adjacency entry of the
+// undirected typed CSR (bit 0: owner -> neighbour, bit 1: neighbour ->
+// owner; both for a pair with arcs both ways), set once when the graph is
+// built with TG_DIRECTED.  Per edge (i, j) one warp runs Alg. 1 on the
+// shorter list: each triangle node w of T_ij comes with the state of (i, w)
+// and of (j, w), counted per (state pair, type of w); the 3-star nodes S_i,
+// S_j are not enumerated: their counts per (state, type) are the node's
+// split typed degrees less j (or i) and less the triangle nodes of that
+// state.  The triad class of {i, j, w} follows from the three pair states by
+// a table built on the host from the class representatives of the header.
+#include <algorithm>
+#include <mutex>
+
+#include "tg_device.cuh"
+
+using namespace tgd;
+
+namespace {
+
+constexpr int kDirThreads = 256;
+constexpr int kDirWarps = kDirThreads / 32;
+
+// Arc bits of the pairs of three labelled nodes 0, 1, 2: bit 2 p for the arc
+// from the lower to the higher node of pair p, bit 2 p + 1 for the reverse;
+// pairs (0, 1), (0, 2), (1, 2).
+int arc_bit(int a, int b) {
+    const int p = (a + b == 1) ? 0 : (a + b == 2) ? 1 : 2;
+    return 2 * p + (a < b ? 0 : 1);
+}
+
+// Class of every connected 3-node digraph, by arc mask; -1 for the others.
+struct TriadTable {
+    int8_t cls[64];
+    bool ok = false;
+};
+
+TriadTable build_triads() {
+    // representatives of the header on A = 0, B = 1, C = 2 (arcs from -> to)
+    static const int reps[TG_TRIAD_CLASSES][6][2] = {
+        {{1, 0}, {1, 2}, {-1, -1}},                                   // 021D
+        {{0, 1}, {2, 1}, {-1, -1}},                                   // 021U
+        {{0, 1}, {1, 2}, {-1, -1}},                                   // 021C
+        {{0, 1}, {1, 0}, {2, 1}, {-1, -1}},                           // 111D
+        {{0, 1}, {1, 0}, {1, 2}, {-1, -1}},                           // 111U
+        {{0, 1}, {2, 1}, {0, 2}, {-1, -1}},                           // 030T
+        {{0, 1}, {1, 2}, {2, 0}, {-1, -1}},                           // 030C
+        {{0, 1}, {1, 0}, {1, 2}, {2, 1}, {-1, -1}},                   // 201
+        {{1, 0}, {1, 2}, {0, 2}, {2, 0}, {-1, -1}},                   // 120D
+        {{0, 1}, {2, 1}, {0, 2}, {2, 0}, {-1, -1}},                   // 120U
+        {{0, 1}, {1, 2}, {0, 2}, {2, 0}, {-1, -1}},                   // 120C
+        {{0, 1}, {1, 2}, {2, 1}, {0, 2}, {2, 0}, {-1, -1}},           // 210
+        {{0, 1}, {1, 0}, {1, 2}, {2, 1}, {0, 2}, {2, 0}},             // 300
+    };
+    static const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2},
+                                   {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    TriadTable t;
+    std::fill(t.cls, t.cls + 64, (int8_t)-1);
+    bool ok = true;
+    for (int c = 0; c < TG_TRIAD_CLASSES; ++c)
+        for (int q = 0; q < 6; ++q) {
+            int mask = 0;
+            for (int r = 0; r < 6 && reps[c][r][0] >= 0; ++r)
+                mask |= 1 << arc_bit(perm[q][reps[c][r][0]], perm[q][reps[c][r][1]]);
+            if (t.cls[mask] >= 0 && t.cls[mask] != c) ok = false;
+            t.cls[mask] = (int8_t)c;
+        }
+    // every mask whose pairs connect the three nodes must have a class
+    for (int mask = 0; mask < 64; ++mask) {
+        const int pairs = ((mask & 3) != 0) + ((mask & 12) != 0) + ((mask & 48) != 0);
+        if ((pairs >= 2) != (t.cls[mask] >= 0)) ok = false;
+    }
+    t.ok = ok;
+    return t;
+}
+
+const TriadTable &triads() {
+    static std::once_flag once;
+    static TriadTable t;
+    std::call_once(once, [] { t = build_triads(); });
+    return t;
+}
+
+// arc mask of a pair state (bit 0: lower-labelled -> higher, bit 1: back)
+inline int pair_mask(int state, int a, int b) {
+    int m = 0;
+    if (state & 1) m |= 1 << arc_bit(a, b);
+    if (state & 2) m |= 1 << arc_bit(b, a);
+    return m;
+}
+
+struct DirParams {
+    const int64_t *rowptr;
+    const uint32_t *adj;
+    const uint8_t *adir;
+    const int32_t *toff;
+    const uint8_t *ntype;
+    const int2 *edges;
+    const uint32_t *nd;  // n x 3 L split typed degrees (state 1..3, type)
+    int64_t M;
+    int32_t L;
+    int64_t n3;           // C(L+2, 3)
+    uint64_t *rows;       // per-edge mode
+    unsigned long long *sums;  // global mode: 13 n3 undivided sums
+    unsigned long long *queue;
+    unsigned *err;
+    int8_t tri[27];  // class of (s_ij, s_iw, s_jw), states 1..3 each
+    int8_t path[9];  // class of a 3-path by the states of its ends seen from its centre
+};
+
+__global__ void k_arc_bits(const int32_t *src, const int32_t *dst, int64_t m,
+                           const int32_t *old2new, const int64_t *rowptr, const uint32_t *adj,
+                           const int32_t *toff, const uint8_t *ntype, int L, uint32_t *adir32,
+                           unsigned *err) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a0 = src[e], b0 = dst[e];
+        if (a0 == b0) continue;
+        const uint32_t a = (uint32_t)old2new[a0], b = (uint32_t)old2new[b0];
+        const int64_t ba = rowptr[a], bb = rowptr[b];
+        const int pa = find_pos(adj, ba, toff + (int64_t)a * (L + 1),
+                                ((uint32_t)ntype[b] << TG_TSHIFT) | b);
+        const int pb = find_pos(adj, bb, toff + (int64_t)b * (L + 1),
+                                ((uint32_t)ntype[a] << TG_TSHIFT) | a);
+        if (pa < 0 || pb < 0) {
+            atomicOr(err, TG_DERR_BOUNDS);
+            continue;
+        }
+        const int64_t qa = ba + pa, qb = bb + pb;
+        atomicOr(adir32 + (qa >> 2), 1u << (8 * (int)(qa & 3)));  // a -> b: out of a
+        atomicOr(adir32 + (qb >> 2), 2u << (8 * (int)(qb & 3)));  // a -> b: into b
+    }
+}
+
+// Split typed degrees: nd[v][(s - 1) L + t] = neighbours of v of type t whose
+// pair with v has state s.  One warp per node, counters in shared memory.
+__global__ void __launch_bounds__(kDirThreads) k_dir_degrees(const int64_t *rowptr,
+                                                             const uint32_t *adj,
+                                                             const uint8_t *adir, int64_t n,
+                                                             int L, uint32_t *nd) {
+    __shared__ uint32_t cnt[kDirWarps][3 * TG_MAX_TYPES];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nw = (int64_t)gridDim.x * kDirWarps;
+    for (int64_t v = blockIdx.x * (int64_t)kDirWarps + warp; v < n; v += nw) {
+        for (int k = lane; k < 3 * L; k += 32) cnt[warp][k] = 0u;
+        __syncwarp();
+        const int64_t b = rowptr[v], d = rowptr[v + 1] - b;
+        for (int64_t x = lane; x < d; x += 32) {
+            const int st = adir[b + x];
+            const int t = (int)(__ldg(adj + b + x) >> TG_TSHIFT);
+            if (st) atomicAdd(&cnt[warp][(st - 1) * L + t], 1u);
+        }
+        __syncwarp();
+        for (int k = lane; k < 3 * L; k += 32) nd[v * 3 * L + k] = cnt[warp][k];
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ int swap_state(int s) { return ((s & 1) << 1) | ((s >> 1) & 1); }
+
+// One warp per edge (dynamic queue).  kRows: per-edge rows, else the
+// undivided sums of the global count (per-CTA shared histogram).
+template <bool kRows>
+__global__ void __launch_bounds__(kDirThreads) k_dir3(DirParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int L = p.L, S = TG_TRIAD_CLASSES * L;
+    unsigned long long *h = reinterpret_cast<unsigned long long *>(smem);
+    const size_t hb = kRows ? 0 : (((size_t)TG_TRIAD_CLASSES * p.n3 * 8 + 15) & ~(size_t)15);
+    uint32_t *tri = reinterpret_cast<uint32_t *>(smem + hb) + (size_t)warp * 9 * L;
+    if (!kRows) {
+        for (int64_t q = threadIdx.x; q < TG_TRIAD_CLASSES * p.n3; q += blockDim.x) h[q] = 0ull;
+        __syncthreads();
+    }
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(p.queue, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= (unsigned long long)p.M) break;
+        const int64_t e = (int64_t)item;
+        const int2 ab = p.edges[e];
+        const uint32_t i = (uint32_t)ab.x, j = (uint32_t)ab.y;
+        const int ti = p.ntype[i], tj = p.ntype[j];
+        const int64_t bi = p.rowptr[i], bj = p.rowptr[j];
+        const int di = (int)(p.rowptr[i + 1] - bi), dj = (int)(p.rowptr[j + 1] - bj);
+        const int32_t *toi = p.toff + (int64_t)i * (L + 1);
+        const int32_t *toj = p.toff + (int64_t)j * (L + 1);
+        int sij = 0;
+        if (lane == 0) {
+            const int q = find_pos(p.adj, bi, toi, ((uint32_t)tj << TG_TSHIFT) | j);
+            sij = q >= 0 ? p.adir[bi + q] : 0;
+            if (sij == 0) atomicOr(p.err, TG_DERR_BOUNDS);
+        }
+        sij = __shfl_sync(kFull, sij, 0);
+        for (int k = lane; k < 9 * L; k += 32) tri[k] = 0u;
+        __syncwarp();
+        if (sij != 0) {
+            // Alg. 1 on the shorter list: x scanned, y searched
+            const bool xi = di <= dj;
+            const int64_t bx = xi ? bi : bj, by = xi ? bj : bi;
+            const int dx = xi ? di : dj;
+            const uint32_t yid = xi ? j : i;
+            const int32_t *toy = xi ? toj : toi;
+            for (int x = lane; x < dx; x += 32) {
+                const uint32_t w = __ldg(p.adj + bx + x);
+                if ((w & TG_IDMASK) == yid) continue;
+                const int q = find_pos(p.adj, by, toy, w);
+                if (q < 0) continue;
+                const int sx = p.adir[bx + x], sy = p.adir[by + q];
+                const int siw = xi ? sx : sy, sjw = xi ? sy : sx;
+                atomicAdd(&tri[((siw - 1) * 3 + (sjw - 1)) * L + (int)(w >> TG_TSHIFT)], 1u);
+            }
+        }
+        __syncwarp();
+        if (sij != 0) {
+            const int sji = swap_state(sij);
+            const uint32_t *ndi = p.nd + (int64_t)i * 3 * L, *ndj = p.nd + (int64_t)j * 3 * L;
+            for (int k = lane; k < S; k += 32) {
+                const int c = k / L, t = k - c * L;
+                unsigned long long v = 0;
+                for (int s1 = 0; s1 < 3; ++s1)
+                    for (int s2 = 0; s2 < 3; ++s2)
+                        if (p.tri[(sij - 1) * 9 + s1 * 3 + s2] == c) v += tri[(s1 * 3 + s2) * L + t];
+                for (int s = 0; s < 3; ++s) {
+                    if (p.path[(sij - 1) * 3 + s] == c) {
+                        // S_i members of state s + 1 and type t
+                        long long m = (long long)ndi[s * L + t] - ((s + 1 == sij && t == tj) ? 1 : 0);
+                        for (int s2 = 0; s2 < 3; ++s2) m -= tri[(s * 3 + s2) * L + t];
+                        v += (unsigned long long)m;
+                    }
+                    if (p.path[(sji - 1) * 3 + s] == c) {
+                        long long m = (long long)ndj[s * L + t] - ((s + 1 == sji && t == ti) ? 1 : 0);
+                        for (int s1 = 0; s1 < 3; ++s1) m -= tri[(s1 * 3 + s) * L + t];
+                        v += (unsigned long long)m;
+                    }
+                }
+                if (kRows) {
+                    p.rows[e * S + k] = v;
+                } else if (v) {
+                    int a = ti, b = tj, cc = t;
+                    sort2(a, b);
+                    sort2(b, cc);
+                    sort2(a, b);
+                    atomicAdd(h + (int64_t)c * p.n3 + colex3(a, b, cc), v);
+                }
+            }
+        } else if (kRows) {
+            for (int k = lane; k < S; k += 32) p.rows[e * S + k] = 0ull;
+        }
+        __syncwarp();
+    }
+    if (!kRows) {
+        __syncthreads();
+        for (int64_t q = threadIdx.x; q < TG_TRIAD_CLASSES * p.n3; q += blockDim.x)
+            if (h[q]) atomicAdd(p.sums + q, h[q]);
+    }
+}
+
+__global__ void k_dir_finalize(const unsigned long long *sums, uint64_t *out, int64_t n3,
+                               unsigned *err) {
+    const int64_t len = TG_TRIAD_CLASSES * n3;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < len;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(q / n3);
+        const unsigned long long div = (c <= 4 || c == 7) ? 2ull : 3ull;
+        if (sums[q] % div) atomicOr(err, TG_DERR_DIVISIBLE);
+        out[q] = sums[q] / div;
+    }
+}
+
+// Per-edge rows (rows != nullptr) or undivided global sums of a TG_DIRECTED graph.
+int dir_count(const tg_graph *g, uint64_t *rows, unsigned long long *sums, unsigned *err,
+              cudaStream_t s) {
+    const TriadTable &tt = triads();
+    if (!tt.ok) return TG_EINTERNAL;
+    const int L = g->L;
+    const int64_t n = g->n, M = g->M;
+    if (M == 0) return TG_OK;
+    DevBuf<uint32_t> nd;
+    DevBuf<unsigned long long> queue;
+    if (!nd.alloc((size_t)n * 3 * L, s) || !queue.alloc(1, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(queue.p, 0, 8, s));
+    const int64_t ngrid = std::min<int64_t>((n + kDirWarps - 1) / kDirWarps, (int64_t)tg_num_sms() * 16);
+    k_dir_degrees<<<(unsigned)ngrid, kDirThreads, 0, s>>>(g->rowptr, g->adj, g->adir, n, L, nd.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    DirParams p{};
+    p.rowptr = g->rowptr;
+    p.adj = g->adj;
+    p.adir = g->adir;
+    p.toff = g->toff;
+    p.ntype = g->ntype;
+    p.edges = g->edges;
+    p.nd = nd.p;
+    p.M = M;
+    p.L = L;
+    p.n3 = tg_binom(L + 2, 3);
+    p.rows = rows;
+    p.sums = sums;
+    p.queue = queue.p;
+    p.err = err;
+    for (int sij = 1; sij <= 3; ++sij)
+        for (int s1 = 1; s1 <= 3; ++s1) {
+            for (int s2 = 1; s2 <= 3; ++s2)
+                p.tri[(sij - 1) * 9 + (s1 - 1) * 3 + (s2 - 1)] =
+                    tt.cls[pair_mask(sij, 0, 1) | pair_mask(s1, 0, 2) | pair_mask(s2, 1, 2)];
+            // a 3-path: centre 0, ends 1 (state sij) and 2 (state s1), seen from 0
+            p.path[(sij - 1) * 3 + (s1 - 1)] = tt.cls[pair_mask(sij, 0, 1) | pair_mask(s1, 0, 2)];
+        }
+    const void *fn = rows ? (const void *)k_dir3<true> : (const void *)k_dir3<false>;
+    const size_t hb = rows ? 0 : (((size_t)TG_TRIAD_CLASSES * p.n3 * 8 + 15) & ~(size_t)15);
+    const size_t smem = hb + (size_t)kDirWarps * 9 * L * 4;
+    TG_TRY(tg_allow_max_smem(fn));
+    int per = 0;
+    TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kDirThreads, smem));
+    if (per < 1) return TG_ENOMEM;
+    const int64_t grid = std::min<int64_t>((int64_t)tg_num_sms() * per, (M + kDirWarps - 1) / kDirWarps);
+    if (rows)
+        k_dir3<true><<<(unsigned)grid, kDirThreads, smem, s>>>(p);
+    else
+        k_dir3<false><<<(unsigned)grid, kDirThreads, smem, s>>>(p);
+    tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    return TG_OK;
+}
+
+int check_dir(const tg_graph *g) {
+    if (!g || !g->adir) return TG_EINVAL;
+    return TG_OK;
+}
+
+}  // namespace
+
+int tg_attach_arcs(tg_graph *g, const int32_t *src, const int32_t *dst, int64_t m,
+                   const int32_t *old2new, cudaStream_t s) {
+    const int64_t words = (2 * g->M + 3) / 4;
+    g->adir = (uint8_t *)tg_dalloc((size_t)std::max<int64_t>(1, words) * 4, s);
+    if (!g->adir) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(g->adir, 0, (size_t)std::max<int64_t>(1, words) * 4, s));
+    if (m == 0 || g->M == 0) return TG_OK;
+    DevBuf<unsigned> err;
+    if (!err.alloc(1, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(err.p, 0, 4, s));
+    const unsigned grid = (unsigned)std::min<int64_t>((m + 255) / 256, 65535LL * 16);
+    k_arc_bits<<<grid, 256, 0, s>>>(src, dst, m, old2new, g->rowptr, g->adj, g->toff, g->ntype,
+                                    g->L, reinterpret_cast<uint32_t *>(g->adir), err.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    unsigned herr = 0;
+    TG_TRY_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    return herr ? TG_EINTERNAL : TG_OK;
+}
+
+extern "C" int64_t tg_dir_slots(int32_t L) {
+    if (L < 1 || L > TG_MAX_TYPES) return -1;
+    return (int64_t)TG_TRIAD_CLASSES * L;
+}
+
+extern "C" int64_t tg_dir_global_len(int32_t L) {
+    if (L < 1 || L > TG_MAX_TYPES) return -1;
+    return (int64_t)TG_TRIAD_CLASSES * tg_binom(L + 2, 3);
+}
+
+extern "C" int tg_count_directed_per_edge(const tg_graph *g, uint64_t *rows, void *stream) {
+    TG_TRY(check_dir(g));
+    if (!rows) return TG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->M == 0) return TG_OK;
+    const int64_t width = tg_dir_slots(g->L);
+    DevBuf<unsigned> err;
+    if (!err.alloc(1, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(err.p, 0, 4, s));
+    DevBuf<uint64_t> tmp;
+    uint64_t *dst = rows;
+    const bool dev_out = tg_is_device_ptr(rows);
+    if (!dev_out) {
+        if (!tmp.alloc((size_t)g->M * width, s)) return TG_ENOMEM;
+        dst = tmp.p;
+    }
+    TG_TRY(dir_count(g, dst, nullptr, err.p, s));
+    unsigned herr = 0;
+    TG_TRY_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, s));
+    if (!dev_out)
+        TG_TRY_CUDA(cudaMemcpyAsync(rows, dst, (size_t)g->M * width * 8, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    return herr ? TG_EINTERNAL : TG_OK;
+}
+
+extern "C" int tg_count_directed_global(const tg_graph *g, uint64_t *out, void *stream) {
+    TG_TRY(check_dir(g));
+    if (!out) return TG_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t len = tg_dir_global_len(g->L);
+    DevBuf<unsigned long long> sums;
+    DevBuf<unsigned> err;
+    if (!sums.alloc(len, s) || !err.alloc(1, s)) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaMemsetAsync(sums.p, 0, len * 8, s));
+    TG_TRY_CUDA(cudaMemsetAsync(err.p, 0, 4, s));
+    TG_TRY(dir_count(g, nullptr, sums.p, err.p, s));
+    const bool dev_out = tg_is_device_ptr(out);
+    DevBuf<uint64_t> tmp;
+    uint64_t *dst = out;
+    if (!dev_out) {
+        if (!tmp.alloc(len, s)) return TG_ENOMEM;
+        dst = tmp.p;
+    }
+    const unsigned grid = (unsigned)std::min<int64_t>((len + 255) / 256, 4096);
+    k_dir_finalize<<<grid, 256, 0, s>>>(sums.p, dst, tg_binom(g->L + 2, 3), err.p); tg_note_launch();
+    TG_TRY_CUDA(cudaGetLastError());
+    unsigned herr = 0;
+    TG_TRY_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, s));
+    if (!dev_out) TG_TRY_CUDA(cudaMemcpyAsync(out, dst, len * 8, cudaMemcpyDeviceToHost, s));
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    return herr ? TG_EINTERNAL : TG_OK;
+}

@@ -39,6 +39,8 @@ struct tg_graph {
     int2 *edges = nullptr;       // M, (new a, new b) in canonical order
     uint32_t *eid = nullptr;     // 2M, canonical edge id of each adjacency entry
     int32_t *new2old = nullptr;  // n
+    uint8_t *adir = nullptr;     // 2M (TG_DIRECTED only): arcs of each adjacency entry,
+                                 // bit 0 owner -> neighbour, bit 1 neighbour -> owner
 
     mutable std::mutex mu;           // guards the lazily built schedule
     mutable tg_sched *sched = nullptr;
@@ -97,6 +99,13 @@ void tg_note_cuda_error(cudaError_t e);
     } while (0)
 
 // ------------------------------------------------------------- primitives --
+// Direction bits of a graph built with TG_DIRECTED (tg_directed.cu): for
+// every non-loop input arc src -> dst (original ids, device arrays), marks the
+// entry of dst in the list of src as outgoing and the entry of src in the list
+// of dst as incoming.  old2new maps original ids to the graph's ids.
+int tg_attach_arcs(tg_graph *g, const int32_t *src, const int32_t *dst, int64_t m,
+                   const int32_t *old2new, cudaStream_t s);
+
 // Exclusive prefix sums (out may alias in).  n >= 0.
 int tg_scan_u32(const uint32_t *in, uint32_t *out, int64_t n, cudaStream_t s);
 int tg_scan_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);

@@ -50,6 +50,7 @@ __all__ = [
     "er_exact",
     "cl_sweep",
     "type_permutations",
+    "er_directed",
 ]
 
 
@@ -345,6 +346,18 @@ def type_permutations(types: np.ndarray, count: int, seed: int = 1):
     Sec. "Exploratory Analysis": same topology, same type counts)."""
     g = rng(12, seed, int(types.shape[0]), count)
     return [g.permutation(types).astype(np.uint8) for _ in range(count)]
+
+
+def er_directed(n: int, m: int, recip: float, L: int, seed: int = 1) -> TypedEdgeList:
+    """m arcs src -> dst with endpoints uniform (loops and repeats possible),
+    and the reverse of each arc added with probability ``recip`` (pairs with
+    arcs both ways); L uniform types.  Read with TG_DIRECTED."""
+    g = rng(14, seed, n, m, int(round(recip * 1000)), L)
+    src = g.integers(0, n, size=m, dtype=np.int64).astype(np.int32)
+    dst = g.integers(0, n, size=m, dtype=np.int64).astype(np.int32)
+    back = g.random(m) < recip
+    return TypedEdgeList(n, np.concatenate([src, dst[back]]), np.concatenate([dst, src[back]]),
+                         uniform_types(n, L, g), L, f"dir-er-n{n}-m{m}-r{recip:g}-L{L}")
 
 
 def tiny_random(n: int, density: float, L: int, g: np.random.Generator) -> TypedEdgeList:
