@@ -330,7 +330,8 @@ def recorded_oracle2(workload_name):
 
 # -------------------------------------------------------------------- gpu ---
 def run_batch(args):
-    """10,000 graphs, per-edge typed 3/4-node graphlet rows, one persistent launch."""
+    """10,000 graphs, per-edge typed 3/4-node graphlet rows through one batch plan
+    (union path or persistent launch, whichever the plan's tuner picks)."""
     import torch
 
     import paper_1901_10026_gb300 as tg
@@ -383,6 +384,19 @@ def run_batch(args):
     torch.cuda.synchronize()
     per_graph_s = time.perf_counter() - t0
     equal = all(torch.equal(saved[i], outs[i]) for i in pick)
+    # the single persistent launch alone, for comparison
+    pers = tg.Batch(graphs, 4, tg.TG_BATCH_PER_EDGE_GRAPHLET, outs, path="persistent")
+    pers_best = pers.tune()
+    pers.run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    pers.run()
+    b.record()
+    torch.cuda.synchronize()
+    pers_s = a.elapsed_time(b) / 1e3
+    pers.close()
+    equal = equal and all(torch.equal(saved[i], outs[i]) for i in pick)
     line = {
         "metric": "batched graphs/s", "value": len(graphs) / batch_s, "unit": "graphs/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": batch_s * 1e3,
@@ -390,9 +404,13 @@ def run_batch(args):
         "data": "synthetic", "mode": "batch",
         "config": {"workload": f"{len(graphs)} graphs, n log-uniform [20, 5000], half ER (avg degree 4-32), "
                                "half Chung-Lu (exponent 2.0-2.8), L uniform 2..8; per-edge typed 3/4-node "
-                               "graphlet rows (uint64) in one persistent launch",
+                               "graphlet rows (uint64), one batch plan (tuned: union of each "
+                               "type-count group through the whole-graph path, or one persistent launch)",
                    "graphs": len(graphs), "edges": edges, "output_bytes": total * 8,
-                   "l2": "inputs and outputs far larger than L2", "tuned_cta_threads": best},
+                   "l2": "inputs and outputs far larger than L2",
+                   "path": "union" if best == 0 else "persistent", "tuned_cta_threads": best},
+        "persistent_path": {"value": len(graphs) / pers_s, "unit": "graphs/s", "seconds": pers_s,
+                            "tuned_cta_threads": pers_best},
         "edges_per_s": edges / batch_s,
         "per_graph_baseline": {"value": len(graphs) / per_graph_s, "unit": "graphs/s",
                                "seconds": per_graph_s, "how": "one tg_count_per_edge call per graph"},

@@ -419,11 +419,21 @@ int tg_autotune_reset(void); /* forgets every cached class */
 
 /* ---------------------------------------------------------- batches ----- */
 /*
- * Many graphs in one persistent launch.  Every (graph, edge) pair is a work
- * item; items are ordered by an estimate of their Alg. 2-3 work (heaviest
- * first) in one shared queue that the warps of a single persistent launch
- * drain.  A plan holds the device descriptors, the queue and the scratch; its
- * runs are replayed from a captured CUDA graph.
+ * Many graphs counted together, by one of two paths:
+ *  - persistent: every (graph, edge) pair is a work item; items are ordered
+ *    by an estimate of their Alg. 2-3 work (heaviest first) in one shared
+ *    queue that the warps of a single persistent launch drain (the paper's
+ *    per-edge enumeration, binary-search membership); runs are replayed from
+ *    a captured CUDA graph;
+ *  - union: the graphs of each type count L form one disjoint union (built
+ *    once per plan), counted per edge by the whole-graph path of
+ *    tg_count_per_edge; each graph's rows are one block of the union's rows
+ *    (copied to its output, or summed into its global counts).
+ * The union is built unless tune->kernel is TG_KERNEL_WARP_SEARCH (persistent
+ * only; with TG_KERNEL_CYCLES a union that cannot be built fails the call,
+ * otherwise the plan falls back to the persistent path) and is used from the
+ * start; tg_batch_tune times both paths and keeps the faster.  A plan holds the descriptors, the queue, the unions and their
+ * row scratch (M_L x row width uint64 for the largest group).
  *
  * mode: TG_BATCH_GLOBAL        outs[g]: tg_global_len(L_g, k) uint64
  *       TG_BATCH_PER_EDGE_GRAPHLET / _ORBIT
@@ -448,9 +458,10 @@ int tg_batch_create(int32_t G, tg_graph *const *graphs, int32_t k, int32_t mode,
 int tg_batch_run(tg_batch *b, void *stream);
 
 /* Autotuner: times the persistent kernel with 4, 8 and 16 warps per CTA, with
- * and without the cost-ordered queue, keeps the fastest and re-captures the
- * CUDA graph.  *best_threads (may be NULL) receives the CTA size, negative
- * when the natural item order won. */
+ * and without the cost-ordered queue, and the union path when the plan has
+ * one; keeps the fastest (re-capturing the CUDA graph for the persistent
+ * path).  *best_threads (may be NULL) receives the CTA size, negative when
+ * the natural item order won, 0 when the union path won. */
 int tg_batch_tune(tg_batch *b, void *stream, int32_t *best_threads);
 
 int tg_batch_destroy(tg_batch *b);

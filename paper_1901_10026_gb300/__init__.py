@@ -398,11 +398,16 @@ class Batch:
     ``outs`` are device tensors, one per graph (global histograms or per-edge
     rows, by ``mode``).  The graphs and outputs must outlive the plan."""
 
-    def __init__(self, graphs, k, mode, outs, cta_threads=0, stream=None):
+    PATHS = {"auto": TG_KERNEL_AUTO, "union": TG_KERNEL_CYCLES, "persistent": TG_KERNEL_WARP_SEARCH}
+
+    def __init__(self, graphs, k, mode, outs, cta_threads=0, stream=None, path="auto"):
+        """``path``: "auto" (union when it can be built; tune() picks), "union"
+        (required) or "persistent" (the single persistent launch only)."""
         self._graphs, self._outs = list(graphs), list(outs)
         G, hs, ps = _handles(self._graphs, self._outs)
         self._keep = (hs, ps)
-        tune = TGTune(0, cta_threads, 0, 0, 0, 0, 0, 0, 0) if cta_threads else None
+        kern = self.PATHS[path]
+        tune = TGTune(kern, cta_threads, 0, 0, 0, 0, 0, 0, 0) if (cta_threads or kern) else None
         h = ctypes.c_void_p()
         _check(lib().tg_batch_create(G, hs, k, mode, ps, ctypes.byref(tune) if tune else None,
                                      _stream(stream), ctypes.byref(h)), "tg_batch_create")

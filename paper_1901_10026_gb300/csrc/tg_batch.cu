@@ -10,6 +10,16 @@
 // into per-graph undivided sums that a second kernel divides by |E(H)|.
 // The plan (descriptors, queue, scratch) is built once; runs are replayed
 // from a captured CUDA graph.
+//
+// Union path: the graphs of one type count L also form one disjoint union
+// (node ids offset per graph, built once per plan with the library's CSR
+// builder), counted per edge by the whole-graph path of the single-graph
+// calls (Alg. 1's triangle counts reused through the identities, 4-cycles
+// and 4-cliques enumerated once); the union's canonical edge order keeps each
+// graph's edges together and in the graph's own canonical order, so a
+// graph's rows are one block of the union's rows, copied out per graph
+// (per-edge modes) or summed per graph into its undivided sums (global mode).
+// The tuner times both paths and keeps the faster.
 #include <algorithm>
 #include <mutex>
 #include <new>
@@ -24,6 +34,8 @@ namespace {
 enum { B3 = 0, B6 = 1, B7 = 2, B8 = 3, B10 = 4, B12 = 5, BN = 6 };
 
 struct BatchGraph {
+    const int32_t *new2old;      // for the union inputs
+    int64_t n, M;
     const int64_t *rowptr;
     const uint32_t *adj;
     const int32_t *toff;
@@ -338,7 +350,96 @@ __global__ void k_batch_keys(const BatchGraph *gs, const int64_t *eoff, int32_t 
 }
 
 
+// Inputs of the union of one type-count group: block m copies graph
+// members[m]'s canonical edges (original ids offset by noff[m]) to
+// src/dst[eoff[m] ..] and its node types to types[noff[m] ..].
+__global__ void k_union_inputs(const BatchGraph *gs, const int32_t *members, const int64_t *eoff,
+                               const int64_t *noff, int32_t *src, int32_t *dst, uint8_t *types) {
+    const int m = blockIdx.x;
+    const BatchGraph &B = gs[members[m]];
+    const int64_t e0 = eoff[m], n0 = noff[m];
+    for (int64_t e = threadIdx.x; e < B.M; e += blockDim.x) {
+        const int2 ab = B.edges[e];
+        src[e0 + e] = (int32_t)(n0 + B.new2old[ab.x]);
+        dst[e0 + e] = (int32_t)(n0 + B.new2old[ab.y]);
+    }
+    for (int64_t x = threadIdx.x; x < B.n; x += blockDim.x) types[n0 + B.new2old[x]] = B.ntype[x];
+}
+
+// Per-edge modes: graph members[m]'s block of the union rows to its output.
+__global__ void k_union_scatter(const uint64_t *stage, int64_t width, const BatchGraph *gs,
+                                const int32_t *members, const int64_t *eoff) {
+    const int m = blockIdx.x;
+    const BatchGraph &B = gs[members[m]];
+    const uint64_t *src = stage + eoff[m] * width;
+    const int64_t words = B.M * width;
+    for (int64_t x = threadIdx.x; x < words; x += blockDim.x) B.rows[x] = src[x];
+}
+
+// Global mode: graph members[m]'s undivided sums from its block of the union's
+// per-edge graphlet rows (k = 3: [h1: L][h2: L]; k = 4: then six blocks of P
+// type pairs), each row entry added under the sorted type multiset of the
+// edge's endpoints and the slot's types, plus one per edge in the edge block.
+// One CTA per graph owns its sums: a shared histogram, then plain stores.
+__global__ void k_union_sums(const uint64_t *stage, int64_t width, const int2 *uedges,
+                             const uint8_t *untype, const BatchGraph *gs, const int32_t *members,
+                             const int64_t *eoff, int k) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *h = reinterpret_cast<unsigned long long *>(smem);
+    const int m = blockIdx.x;
+    const BatchGraph &B = gs[members[m]];
+    const int L = B.L, P = B.P;
+    for (int64_t x = threadIdx.x; x < B.glen; x += blockDim.x) h[x] = 0ull;
+    __syncthreads();
+    const int64_t e0 = eoff[m], ne = eoff[m + 1] - e0;
+    for (int64_t q = threadIdx.x; q < ne * width; q += blockDim.x) {
+        const int64_t e = e0 + q / width;
+        const int sl = (int)(q % width);
+        const int2 ab = uedges[e];
+        const int ti = untype[ab.x], tj = untype[ab.y];
+        if (sl == 0) {
+            int a = ti, b = tj;
+            sort2(a, b);
+            atomicAdd(h + (int64_t)a + (int64_t)(b + 1) * b / 2, 1ull);
+        }
+        const uint64_t v = stage[e * width + sl];
+        if (!v) continue;
+        int64_t idx;
+        if (sl < 2 * L) {
+            int a = ti, b = tj, c = sl % L;
+            sort2(a, b);
+            sort2(b, c);
+            sort2(a, b);
+            idx = (sl < L ? B.off1 : B.off2) + colex3(a, b, c);
+        } else {
+            const int r = sl - 2 * L, blk = r / P;
+            int t, u;
+            unpair(L, r % P, t, u);
+            int a = ti, b = tj, c = t, d = u;
+            sort2(a, b);
+            sort2(c, d);
+            sort2(a, c);
+            sort2(b, d);
+            sort2(b, c);
+            idx = B.off4 + blk * B.n4 + colex4(a, b, c, d);
+        }
+        atomicAdd(h + idx, (unsigned long long)v);
+    }
+    (void)k;
+    __syncthreads();
+    for (int64_t x = threadIdx.x; x < B.glen; x += blockDim.x) B.sums[x] = h[x];
+}
+
 }  // namespace
+
+struct UnionGroup {
+    int32_t L = 0;
+    int32_t nm = 0;             // member graphs
+    tg_graph *U = nullptr;      // their disjoint union
+    int32_t *d_members = nullptr;
+    int64_t *d_eoff = nullptr;  // nm + 1 edge offsets in the union
+    int64_t width = 0;          // row width of the union count
+};
 
 struct tg_batch {
     int32_t G = 0, k = 4, mode = TG_BATCH_GLOBAL, Pmax = 1;
@@ -355,6 +456,10 @@ struct tg_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     bool no_graph = false;  // enqueue the launches directly instead of replaying a graph
+    std::vector<UnionGroup> groups;  // union path (empty when not built)
+    uint64_t *d_stage = nullptr;     // union rows of the largest group
+    size_t stage_words = 0;
+    bool use_union = false;
     std::mutex mu;
 };
 
@@ -369,6 +474,12 @@ static void batch_release(tg_batch *b) {
     tg_dfree(b->d_queue, 0, nullptr);
     tg_dfree(b->d_sums, 0, nullptr);
     tg_dfree(b->d_err, 0, nullptr);
+    for (UnionGroup &u : b->groups) {
+        tg_free_graph(u.U);
+        tg_dfree(u.d_members, 0, nullptr);
+        tg_dfree(u.d_eoff, 0, nullptr);
+    }
+    tg_dfree(b->d_stage, 0, nullptr);
     (void)cudaDeviceSynchronize();
     delete b;
 }
@@ -453,6 +564,85 @@ static int batch_capture(tg_batch *b, cudaStream_t s) {
     return r;
 }
 
+// Build the union of each type-count group (host vectors hg: descriptors as
+// copied to b->d_gs).  Any failure leaves the plan without the union path.
+static int build_union(tg_batch *b, tg_graph *const *gs, const std::vector<BatchGraph> &hg,
+                       cudaStream_t s) {
+    std::vector<std::vector<int32_t>> byL(TG_MAX_TYPES + 1);
+    for (int g = 0; g < b->G; ++g) byL[hg[g].L].push_back(g);
+    const int level = b->mode == TG_BATCH_PER_EDGE_ORBIT ? TG_ORBIT : TG_GRAPHLET;
+    for (int L = 1; L <= TG_MAX_TYPES; ++L) {
+        const std::vector<int32_t> &mem = byL[L];
+        if (mem.empty()) continue;
+        UnionGroup u;
+        u.L = L;
+        u.nm = (int32_t)mem.size();
+        std::vector<int64_t> eoff(mem.size() + 1, 0), noff(mem.size() + 1, 0);
+        for (size_t q = 0; q < mem.size(); ++q) {
+            eoff[q + 1] = eoff[q] + gs[mem[q]]->M;
+            noff[q + 1] = noff[q] + gs[mem[q]]->n;
+        }
+        if (noff.back() > TG_MAX_NODES || eoff.back() >= ((int64_t)1 << 31)) return TG_EOVERFLOW;
+        u.width = tg_slots(L, b->k, level);
+        u.d_members = (int32_t *)tg_dalloc(mem.size() * 4, s);
+        u.d_eoff = (int64_t *)tg_dalloc((mem.size() + 1) * 8, s);
+        if (!u.d_members || !u.d_eoff) {
+            tg_dfree(u.d_members, 0, s);
+            tg_dfree(u.d_eoff, 0, s);
+            return TG_ENOMEM;
+        }
+        b->groups.push_back(u);  // released with the plan from here on
+        TG_TRY_CUDA(cudaMemcpyAsync(u.d_members, mem.data(), mem.size() * 4, cudaMemcpyHostToDevice, s));
+        TG_TRY_CUDA(cudaMemcpyAsync(u.d_eoff, eoff.data(), (mem.size() + 1) * 8, cudaMemcpyHostToDevice, s));
+        DevBuf<int64_t> dnoff;
+        DevBuf<int32_t> src, dst;
+        DevBuf<uint8_t> types;
+        if (!dnoff.alloc(mem.size() + 1, s) || !src.alloc(std::max<int64_t>(1, eoff.back()), s) ||
+            !dst.alloc(std::max<int64_t>(1, eoff.back()), s) || !types.alloc(noff.back(), s))
+            return TG_ENOMEM;
+        TG_TRY_CUDA(cudaMemcpyAsync(dnoff.p, noff.data(), (mem.size() + 1) * 8, cudaMemcpyHostToDevice, s));
+        k_union_inputs<<<(unsigned)mem.size(), 256, 0, s>>>(b->d_gs, u.d_members, u.d_eoff, dnoff.p,
+                                                            src.p, dst.p, types.p); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+        tg_graph *U = nullptr;
+        TG_TRY(tg_build_csr(noff.back(), eoff.back(), src.p, dst.p, types.p, L, TG_INPUT_DEVICE, s, &U));
+        b->groups.back().U = U;
+        if (U->M != eoff.back()) return TG_EINTERNAL;  // graphs of a union never share an edge
+        b->stage_words = std::max(b->stage_words, (size_t)U->M * (size_t)u.width);
+    }
+    b->d_stage = (uint64_t *)tg_dalloc(std::max<size_t>(1, b->stage_words) * 8, s);
+    if (!b->d_stage) return TG_ENOMEM;
+    TG_TRY_CUDA(cudaStreamSynchronize(s));
+    return TG_OK;
+}
+
+// One run through the unions: per group the whole-graph per-edge count, then
+// the rows out per graph, or (global mode) the per-graph sums and the division.
+static int union_run(tg_batch *b, cudaStream_t s) {
+    const int level = b->mode == TG_BATCH_PER_EDGE_ORBIT ? TG_ORBIT : TG_GRAPHLET;
+    for (const UnionGroup &u : b->groups) {
+        if (u.U->M > 0) TG_TRY(tg_rows_device(u.U, b->k, level, b->d_stage, s));
+        if (b->mode == TG_BATCH_GLOBAL) {
+            const size_t smem = (size_t)tg_global_len(u.L, b->k) * 8;
+            TG_TRY(tg_allow_max_smem((const void *)k_union_sums));
+            k_union_sums<<<(unsigned)u.nm, 512, smem, s>>>(b->d_stage, u.width, u.U->edges, u.U->ntype,
+                                                           b->d_gs, u.d_members, u.d_eoff, b->k);
+        } else {
+            k_union_scatter<<<(unsigned)u.nm, 512, 0, s>>>(b->d_stage, u.width, b->d_gs, u.d_members,
+                                                           u.d_eoff);
+        }
+        tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
+    if (b->mode == TG_BATCH_GLOBAL && b->G > 0) {
+        TG_TRY_CUDA(cudaMemsetAsync(b->d_err, 0, 4, s));
+        dim3 grid(4, (unsigned)b->G);
+        k_batch_finalize<<<grid, 256, 0, s>>>(b->d_gs, b->G, b->d_err); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+    }
+    return TG_OK;
+}
+
 extern "C" int tg_batch_create(int32_t G, tg_graph *const *gs, int32_t k, int32_t mode,
                                uint64_t *const *outs, const tg_tune *tune, void *stream,
                                tg_batch **out) {
@@ -490,6 +680,9 @@ extern "C" int tg_batch_create(int32_t G, tg_graph *const *gs, int32_t k, int32_
         }
         BatchGraph &B = hg[g];
         const int L = x->L;
+        B.new2old = x->new2old;
+        B.n = x->n;
+        B.M = x->M;
         B.rowptr = x->rowptr;
         B.adj = x->adj;
         B.toff = x->toff;
@@ -559,6 +752,27 @@ extern "C" int tg_batch_create(int32_t G, tg_graph *const *gs, int32_t k, int32_
             return fail(TG_ECUDA);
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(TG_ECUDA);
+    // union path: built unless the tuning asks for the persistent warp kernel
+    const int kern = tune ? tune->kernel : TG_KERNEL_AUTO;
+    if (kern != TG_KERNEL_WARP_SEARCH && G > 0) {
+        const int ur = build_union(b, gs, hg, s);
+        if (ur != TG_OK && kern == TG_KERNEL_CYCLES) return fail(ur);  // the union was asked for
+        if (ur == TG_OK) {
+            b->use_union = true;
+        } else {
+            (void)cudaGetLastError();
+            (void)cudaStreamSynchronize(s);
+            for (UnionGroup &u : b->groups) {
+                tg_free_graph(u.U);
+                tg_dfree(u.d_members, 0, s);
+                tg_dfree(u.d_eoff, 0, s);
+            }
+            b->groups.clear();
+            tg_dfree(b->d_stage, 0, s);
+            b->d_stage = nullptr;
+            (void)cudaStreamSynchronize(s);
+        }
+    }
     *out = b;
     return TG_OK;
 }
@@ -567,10 +781,13 @@ extern "C" int tg_batch_run(tg_batch *b, void *stream) {
     if (!b) return TG_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     std::lock_guard<std::mutex> lk(b->mu);
-    // replay of the captured graph; when a capture cannot be made (or the plan
-    // asks for none) the same launches are enqueued directly
-    if (!b->exec && !b->no_graph && batch_capture(b, s) != TG_OK) b->no_graph = true;
-    if (b->exec && !b->no_graph) {
+    // the union path; else a replay of the captured graph, and when a capture
+    // cannot be made (or the plan asks for none) the same launches directly
+    if (!b->use_union && !b->exec && !b->no_graph && batch_capture(b, s) != TG_OK)
+        b->no_graph = true;
+    if (b->use_union) {
+        TG_TRY(union_run(b, s));
+    } else if (b->exec && !b->no_graph) {
         TG_TRY_CUDA(cudaGraphLaunch(b->exec, s));
         if (b->count > 0) tg_note_launch();                      // persistent count kernel
         if (b->mode == TG_BATCH_GLOBAL && b->G > 0) tg_note_launch();  // finalize
@@ -627,14 +844,29 @@ extern "C" int tg_batch_tune(tg_batch *b, void *stream, int32_t *best_threads) {
                 bo = o;
             }
         }
+    // the union path, when the plan has one
+    bool uni = false;
+    if (r == TG_OK && !b->groups.empty()) {
+        r = union_run(b, s);  // warm
+        if (r == TG_OK && cudaEventRecord(e0, s) != cudaSuccess) r = TG_ECUDA;
+        if (r == TG_OK) r = union_run(b, s);
+        if (r == TG_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+            r = TG_ECUDA;
+        if (r == TG_OK) {
+            float ms = 0;
+            (void)cudaEventElapsedTime(&ms, e0, e1);
+            uni = ms < best;
+        }
+    }
     (void)cudaEventDestroy(e0);
     (void)cudaEventDestroy(e1);
     b->warps = bw;
     b->ordered = bo;
+    b->use_union = uni;
     if (r != TG_OK) return r;
     // the chosen configuration as a graph (runs enqueue directly if it fails)
-    if (!b->no_graph && batch_capture(b, s) != TG_OK) b->no_graph = true;
-    if (best_threads) *best_threads = bw * 32 * (bo ? 1 : -1);
+    if (!uni && !b->no_graph && batch_capture(b, s) != TG_OK) b->no_graph = true;
+    if (best_threads) *best_threads = uni ? 0 : bw * 32 * (bo ? 1 : -1);
     return TG_OK;
 }
 

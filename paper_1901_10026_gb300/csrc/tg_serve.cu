@@ -115,8 +115,11 @@ void run_job(tg_server *sv, std::vector<std::unique_ptr<Request>> &job, cudaStre
             std::vector<uint64_t *> outs;
             for (size_t q = 0; q < ok.size() && st == TG_OK; ++q) outs.push_back(d + off[q]);
             // requests of one group share k (the dispatcher groups by k)
+            // small requests: the single persistent launch (no union build, no
+            // per-launch autotuning on the serving path)
             tg_tune fixed{};
-            fixed.cta_threads = 256;  // no per-launch autotuning on the serving path
+            fixed.kernel = TG_KERNEL_WARP_SEARCH;
+            fixed.cta_threads = 256;
             if (st == TG_OK)
                 st = tg_count_batch((int32_t)ok.size(), ok.data(), job[idx[0]]->k, TG_BATCH_GLOBAL,
                                     outs.data(), &fixed, s);

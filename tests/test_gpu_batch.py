@@ -1,5 +1,6 @@
-"""Batched counting (one persistent launch over many graphs) against per-graph
-counts and the oracle, bit-exact."""
+"""Batched counting against per-graph counts and the oracle, bit-exact: the
+single persistent launch, the union of each type-count group through the
+whole-graph path, and the tuner's choice between them."""
 import numpy as np
 import pytest
 
@@ -41,8 +42,9 @@ def _dev(n):
     return torch.zeros(n, dtype=torch.int64, device="cuda:0")
 
 
+@pytest.mark.parametrize("path", ["auto", "union", "persistent"])
 @pytest.mark.parametrize("mode", [tg.TG_BATCH_GLOBAL, tg.TG_BATCH_PER_EDGE_GRAPHLET, tg.TG_BATCH_PER_EDGE_ORBIT])
-def test_batch_matches_oracle(mode):
+def test_batch_matches_oracle(mode, path):
     Gs = _batch_graphs(40, 3)
     graphs = [tg.tg_build_csr(G.n, G.src, G.dst, G.types, G.L) for G in Gs]
     if mode == tg.TG_BATCH_GLOBAL:
@@ -50,10 +52,12 @@ def test_batch_matches_oracle(mode):
     else:
         level = tg.TG_ORBIT if mode == tg.TG_BATCH_PER_EDGE_ORBIT else tg.TG_GRAPHLET
         outs = [_dev(max(1, g.M * tg.tg_slots(G.L, 4, level))) for G, g in zip(Gs, graphs)]
-    plan = tg.Batch(graphs, 4, mode, outs)
-    best = plan.tune()
-    assert best != 0
-    for rep in range(2):  # first run captures the CUDA graph, second replays it
+    plan = tg.Batch(graphs, 4, mode, outs, path=path)
+    if path == "auto":
+        plan.tune()
+    elif path == "persistent":
+        assert plan.tune() != 0  # the union path is not built
+    for rep in range(2):  # persistent path: the first run captures the CUDA graph, the second replays it
         for o in outs:
             o.zero_()
         plan.run()
@@ -69,13 +73,29 @@ def test_batch_matches_oracle(mode):
     plan.close()
 
 
-def test_one_shot_batch_equals_single_graph_counts():
+@pytest.mark.parametrize("cta", [256, 0])
+def test_one_shot_batch_equals_single_graph_counts(cta):
     Gs = _batch_graphs(25, 4)
     graphs = [tg.tg_build_csr(G.n, G.src, G.dst, G.types, G.L) for G in Gs]
     outs = [_dev(tg.tg_global_len(G.L, 3)) for G in Gs]
-    tg.tg_count_batch(graphs, 3, tg.TG_BATCH_GLOBAL, outs, cta_threads=256)
+    tg.tg_count_batch(graphs, 3, tg.TG_BATCH_GLOBAL, outs, cta_threads=cta)
     for g, o, G in zip(graphs, outs, Gs):
         assert np.array_equal(o.cpu().numpy().view(np.uint64), tg.tg_count_global(g, 3)), G.name
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_union_path_k3_and_medium_graphs(k):
+    # several graphs per type count, some large enough for the CTA kernels
+    Gs = [synth.cl_sweep(4000, 24000, L, seed=s) for L in (2, 3) for s in (1, 2)] + \
+         [synth.er_avg_degree(3000, 12.0, 2, seed=3)]
+    graphs = [tg.tg_build_csr(G.n, G.src, G.dst, G.types, G.L) for G in Gs]
+    outs = [_dev(max(1, g.M * tg.tg_slots(G.L, k, tg.TG_GRAPHLET))) for G, g in zip(Gs, graphs)]
+    plan = tg.Batch(graphs, k, tg.TG_BATCH_PER_EDGE_GRAPHLET, outs, path="union")
+    plan.run()
+    for G, g, o in zip(Gs, graphs, outs):
+        want = tg.tg_count_per_edge(g, k, tg.TG_GRAPHLET)
+        assert np.array_equal(o.cpu().numpy().view(np.uint64).reshape(want.shape), want), G.name
+    plan.close()
 
 
 def test_batch_rejects_host_outputs():
