@@ -210,6 +210,10 @@ __global__ void __launch_bounds__(kDirThreads) k_dir3(DirParams p) {
                 const int q = find_pos(p.adj, by, toy, w);
                 if (q < 0) continue;
                 const int sx = p.adir[bx + x], sy = p.adir[by + q];
+                if (sx == 0 || sy == 0) {  // every entry carries an arc; never taken
+                    atomicOr(p.err, TG_DERR_BOUNDS);
+                    continue;
+                }
                 const int siw = xi ? sx : sy, sjw = xi ? sy : sx;
                 atomicAdd(&tri[((siw - 1) * 3 + (sjw - 1)) * L + (int)(w >> TG_TSHIFT)], 1u);
             }
