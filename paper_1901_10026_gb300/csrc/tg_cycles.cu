@@ -948,15 +948,13 @@ __global__ void __launch_bounds__(kC4WalkWarps * 32) k_c4_bin_walk(C4Bin p) {
 // buckets (consecutive windows of one anchor, mostly) from a queue.  A bucket
 // (anchor a of type ta, window w) has its entries counted by (b, t) in the
 // dense table (16-bit halves when the wave's anchors have fewer than 2^16
-// neighbours, else 32-bit counts), far ends marked on first touch in a
-// bitmap.  Then each warp takes bitmap words; for every marked far end b with
-// two or more middles, lane x of the warp adds, for its type pairs (t, t')
-// (pairs x and x + 32), C(c_t, 2) or c_t c_t' to its warp's table
-// acc[type of b][pair] in shared memory (a lane writes only its own
-// columns: no atomics, no conflicts), and the far end's counts and mark are
-// cleared.  The tables go into the histogram under {ta, tb, t, t'} when the
-// anchor changes.  Types beyond kBinAccL use c4_add straight into a shared
-// histogram instead.
+// neighbours, else 32-bit counts); the first entry of a far end puts it on a
+// list (a bit per far end keeps it there once).  Then one thread per listed
+// far end reads its counts, clears them, and for the types it has (usually
+// few) adds C(c_t, 2) and c_t c_t' to its warp's table acc[type of b][pair]
+// in shared memory (atomic adds), which goes into the histogram under
+// {ta, tb, t, t'} when the anchor changes.  Types beyond kBinAccL use c4_add
+// straight into a shared histogram instead.
 constexpr int kBinPairThreads = 512;
 constexpr int kBinRun = 16;
 constexpr int kBinAccL = 8;
@@ -986,20 +984,16 @@ __global__ void __launch_bounds__(kBinPairThreads) k_c4_bin_pairs(C4Bin p) {
     if (acc_mode) off += (size_t)NW * L * P * 8;
     uint32_t *tab = reinterpret_cast<uint32_t *>(smem + off);
     const int twords = p.half ? nfar * (Lp >> 1) : nfar * L;
-    uint32_t *tbits = tab + twords;  // nfar / 32 words
+    uint32_t *tbits = tab + twords;                                      // nfar / 32 words
+    uint16_t *flist = reinterpret_cast<uint16_t *>(tbits + nfar / 32);  // touched far ends
     const volatile uint32_t *vtab = tab;
-    const volatile uint32_t *vbits = tbits;
     __shared__ unsigned long long s_run;
+    __shared__ uint32_t s_nl;
     for (int64_t q = tid; q < p.n4; q += blockDim.x) h4[q] = 0ull;
     if (acc_mode)
         for (int q = lane; q < L * P; q += 32) acc[q] = 0ull;
     for (int q = tid; q < twords + nfar / 32; q += blockDim.x) tab[q] = 0u;
-    // this lane's type pairs (pair lane and lane + 32)
-    int pt[2], pu[2];
-    for (int r = 0; r < 2; ++r) {
-        pt[r] = pu[r] = -1;
-        if (acc_mode && lane + 32 * r < P) unpair(L, lane + 32 * r, pt[r], pu[r]);
-    }
+    if (tid == 0) s_nl = 0u;
     const uint32_t wmask = (uint32_t)nfar - 1u;
     int cur_ta = -1;
     int64_t cur_row = -1;
@@ -1021,7 +1015,8 @@ __global__ void __launch_bounds__(kBinPairThreads) k_c4_bin_pairs(C4Bin p) {
                 cur_ta = p.ntype[p.heavy[p.q0 + row]];
             }
             const int ta = cur_ta;
-            // four entries in flight per thread
+            // count the entries by (far end, type); a far end's first entry
+            // puts it on the list
             for (uint32_t k0 = c0 + tid; k0 < c1; k0 += 4 * blockDim.x) {
                 uint32_t ev[4];
 #pragma unroll
@@ -1043,77 +1038,59 @@ __global__ void __launch_bounds__(kBinPairThreads) k_c4_bin_pairs(C4Bin p) {
                     } else {
                         first = atomicAdd(tab + bl * (uint32_t)L + (uint32_t)t, 1u) == 0u;
                     }
-                    if (first) atomicOr(tbits + (bl >> 5), 1u << (bl & 31u));
+                    if (first) {
+                        const uint32_t bit = 1u << (bl & 31u);
+                        if (!(atomicOr(tbits + (bl >> 5), bit) & bit)) flist[atomicAdd(&s_nl, 1u)] = (uint16_t)bl;
+                    }
                 }
             }
             __syncthreads();
-            for (int wd = warp; wd < nfar / 32; wd += NW) {
-                const uint32_t bits = vbits[wd];
-                if (!bits) continue;
-                // lane x holds far end 32 wd + x: its counts and their sum
-                const uint32_t bl = (uint32_t)(wd * 32 + lane);
-                const bool mine = (bits >> lane) & 1u;
+            // one far end per thread: its nonzero types, the pairs among them
+            const uint32_t nl = s_nl;
+            for (uint32_t x = tid; x < nl; x += blockDim.x) {
+                const uint32_t bl = flist[x];
                 uint32_t c[TG_MAX_TYPES];
-                uint32_t sum = 0;
-                if (mine) {
-                    if (p.half) {
-                        const uint32_t w0 = bl * (uint32_t)(Lp >> 1);
-                        for (int q = 0; q < (Lp >> 1); ++q) {
-                            const uint32_t w = vtab[w0 + q];
-                            c[2 * q] = w & 0xffffu;
-                            if (2 * q + 1 < L) c[2 * q + 1] = w >> 16;
-                            sum += (w & 0xffffu) + (w >> 16);
-                        }
-                    } else {
-                        for (int t = 0; t < L; ++t) {
-                            c[t] = vtab[bl * (uint32_t)L + t];
-                            sum += c[t];
-                        }
+                uint32_t sum = 0, mask = 0;
+                if (p.half) {
+                    const uint32_t w0 = bl * (uint32_t)(Lp >> 1);
+                    for (int q = 0; q < (Lp >> 1); ++q) {
+                        const uint32_t w = vtab[w0 + q];
+                        tab[w0 + q] = 0u;
+                        c[2 * q] = w & 0xffffu;
+                        if (2 * q + 1 < L) c[2 * q + 1] = w >> 16;
+                        sum += (w & 0xffffu) + (w >> 16);
+                        if (w & 0xffffu) mask |= 1u << (2 * q);
+                        if (w >> 16) mask |= 1u << (2 * q + 1);
                     }
-                }
-                const int tb = mine ? (int)p.ntype[wbase + bl] : 0;
-                if (!acc_mode) {
-                    if (mine && sum > 1) c4_add(h4, L, ta, tb, c);
                 } else {
-                    // far ends with two or more middles, one at a time across the warp
-                    for (unsigned m = __ballot_sync(kFull, mine && sum > 1); m; m &= m - 1u) {
-                        const int src = __ffs(m) - 1;
-                        const uint32_t bs = (uint32_t)(wd * 32 + src);
-                        const int tbs = __shfl_sync(kFull, tb, src);
-                        unsigned long long *ar = acc + (size_t)tbs * P;
-#pragma unroll
-                        for (int r = 0; r < 2; ++r) {
-                            if (pt[r] < 0) continue;
-                            const unsigned long long ct = p.half
-                                ? (vtab[(bs * (uint32_t)Lp + (uint32_t)pt[r]) >> 1] >>
-                                   (((bs * (uint32_t)Lp + (uint32_t)pt[r]) & 1u) * 16)) & 0xffffu
-                                : vtab[bs * (uint32_t)L + (uint32_t)pt[r]];
-                            if (!ct) continue;
-                            unsigned long long v;
-                            if (pt[r] == pu[r]) {
-                                v = ct * (ct - 1) / 2;
-                            } else {
-                                const unsigned long long cu = p.half
-                                    ? (vtab[(bs * (uint32_t)Lp + (uint32_t)pu[r]) >> 1] >>
-                                       (((bs * (uint32_t)Lp + (uint32_t)pu[r]) & 1u) * 16)) & 0xffffu
-                                    : vtab[bs * (uint32_t)L + (uint32_t)pu[r]];
-                                v = ct * cu;
-                            }
-                            ar[lane + 32 * r] += v;
-                        }
+                    for (int t = 0; t < L; ++t) {
+                        c[t] = vtab[bl * (uint32_t)L + t];
+                        tab[bl * (uint32_t)L + t] = 0u;
+                        sum += c[t];
+                        if (c[t]) mask |= 1u << t;
                     }
                 }
-                __syncwarp();
-                // clear this word's far ends
-                if (mine) {
-                    if (p.half) {
-                        for (int q = 0; q < (Lp >> 1); ++q) tab[bl * (uint32_t)(Lp >> 1) + q] = 0u;
-                    } else {
-                        for (int t = 0; t < L; ++t) tab[bl * (uint32_t)L + t] = 0u;
+                if (sum < 2) continue;
+                const int tb = (int)p.ntype[wbase + bl];
+                if (!acc_mode) {
+                    c4_add(h4, L, ta, tb, c);
+                    continue;
+                }
+                unsigned long long *ar = acc + (size_t)tb * P;
+                for (uint32_t mt = mask; mt; mt &= mt - 1u) {
+                    const int t = __ffs(mt) - 1;
+                    const unsigned long long ct = c[t];
+                    const int rowt = t * L - (t * (t - 1)) / 2;  // pair_index(L, t, u) = rowt + u - t
+                    if (ct > 1) atomicAdd(ar + rowt, ct * (ct - 1) / 2);
+                    for (uint32_t mu = mt & (mt - 1u); mu; mu &= mu - 1u) {
+                        const int u = __ffs(mu) - 1;
+                        atomicAdd(ar + rowt + (u - t), ct * c[u]);
                     }
                 }
-                if (lane == 0) tbits[wd] = 0u;
             }
+            __syncthreads();
+            for (int q = tid; q < nfar / 32; q += blockDim.x) tbits[q] = 0u;
+            if (tid == 0) s_nl = 0u;
             __syncthreads();
         }
     }
@@ -2370,7 +2347,7 @@ int c4_bin_waves(const tg_graph *g, const uint32_t *list, int64_t na,
         const int P = L * (L + 1) / 2;
         const size_t psmem = (((size_t)n4 * 8 + 15) & ~(size_t)15) +
                              (L <= kBinAccL ? (size_t)(kBinPairThreads / 32) * L * P * 8 : 0) +
-                             (pw.half ? nfar * (Lp >> 1) : nfar * L) * 4 + nfar / 32 * 4;
+                             (pw.half ? nfar * (Lp >> 1) : nfar * L) * 4 + nfar / 32 * 4 + nfar * 2;
         int pper = 0;
         TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pper, k_c4_bin_pairs,
                                                                   kBinPairThreads, psmem));
