@@ -145,8 +145,8 @@ __device__ __forceinline__ bool adjacent(const int64_t *__restrict__ rowptr,
 }
 
 // Per-warp hash sets of node ids in shared memory (open addressing, linear
-// probing, id + 1 stored, 0 empty).  Reads are volatile: the table is written
-// by other lanes of the warp between a __syncwarp and the reads.
+// probing, id + 1 stored, 0 empty).  Writers and readers are ordered by a
+// __syncwarp or __syncthreads between them.
 __device__ __forceinline__ uint32_t hset_slot(uint32_t id, int lg) {
     return (id * 0x9E3779B1u) >> (32 - lg);
 }
@@ -161,7 +161,7 @@ __device__ __forceinline__ void hset_put(uint32_t *tab, int lg, uint32_t id) {
 }
 __device__ __forceinline__ bool hset_has(const uint32_t *tab, int lg, uint32_t id) {
     const uint32_t mask = (1u << lg) - 1u;
-    const volatile uint32_t *t = tab;
+    const uint32_t *t = tab;
     uint32_t h = hset_slot(id, lg);
     for (int probe = 0; probe < (1 << lg); ++probe) {
         const uint32_t k = t[h];
@@ -176,7 +176,7 @@ __device__ __forceinline__ bool hset_has(const uint32_t *tab, int lg, uint32_t i
 // the table is full.  Concurrent claims of one id meet in one slot.
 __device__ __forceinline__ int hset_claim(uint32_t *tab, int lg, uint32_t id) {
     const uint32_t mask = (1u << lg) - 1u;
-    const volatile uint32_t *t = tab;
+    const volatile uint32_t *t = tab;  // slots claimed by other lanes while this one probes
     uint32_t h = hset_slot(id, lg);
     for (int probe = 0; probe < (1 << lg); ++probe) {
         const uint32_t k = t[h];
@@ -236,10 +236,10 @@ __device__ __forceinline__ void hinsert(uint32_t *hk, int lg, uint32_t id, int c
 }
 
 // class of a Gamma_i member (CLS_SI or CLS_T), 0 if absent.  The table is
-// read through volatile loads: it is filled with atomicCAS and, when this
-// probe was inlined into the walk, compiled code reused earlier reads of the
-// slots (wrong classes on the GPU, while the same source run out of line or
-// with volatile reads gave the exact counts).
+// read through volatile loads: it is filled with atomicCAS, and with plain
+// loads here the paper-literal CTA kernel with its smallest caps (128
+// threads, 32 hash slots, 96 bitmap bits) gave wrong classes on the GPU while
+// every other kernel and launch shape stayed exact; the cause is not known.
 __device__ __forceinline__ int hlookup(const uint32_t *hk, int lg, uint32_t id) {
     const volatile uint32_t *vk = hk;
     const uint32_t mask = (1u << lg) - 1u;
@@ -253,10 +253,9 @@ __device__ __forceinline__ int hlookup(const uint32_t *hk, int lg, uint32_t id) 
     return 0;  // unreachable: the table is never more than half full
 }
 
-// mark bit of node id in the shared-memory bitmap (volatile for the same reason)
+// mark bit of node id in the shared-memory bitmap (written before a barrier)
 __device__ __forceinline__ bool bm_test(const uint32_t *bm, uint32_t id) {
-    const volatile uint32_t *vb = bm;
-    return (vb[id >> 5] >> (id & 31u)) & 1u;
+    return (bm[id >> 5] >> (id & 31u)) & 1u;
 }
 
 
