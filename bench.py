@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--edge-pass", choices=["auto", "fused"], default="auto",
                     help="per-edge pass of the cycles kernel: auto (T sums through memory when they "
                          "fit) or always the fused kernel")
+    ap.add_argument("--autotune", action="store_true",
+                    help="tg_autotune on the workload before the warm-up steps (untimed; about "
+                         "seven counts)")
     ap.add_argument("--edge-batch", type=int, default=0,
                     help="most edges whose T sums the per-edge pass holds at once (tg_tune "
                          "edge_batch; 0: as many as fit in a quarter of free memory)")
@@ -717,6 +720,7 @@ def main():
 
     g0 = tg.tg_build_csr(G.n, src_d, dst_d, typ_d, L)
     M = g0.M
+    tuned = tg.tg_autotune(g0, k) if (args.autotune and args.kernel == "cycles") else None
     work_entries = tg.tg_work_model(g0)
     eu, evv = tg.tg_edge_list(g0)
     deg = np.bincount(np.concatenate([eu, evv]), minlength=G.n)
@@ -845,7 +849,7 @@ def main():
                        "step": "tg_build_csr + tg_count_global from device-resident inputs",
                        "memory_retention_bytes": args.retain_gib << 30,
                        "kernel": args.kernel, "edge_pass": args.edge_pass,
-                       "edge_batch": args.edge_batch,
+                       "edge_batch": args.edge_batch, "autotuned": tuned,
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": f"shards x{world}" if world > 1 else "single GPU"},
             "clocks": clocks,
