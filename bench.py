@@ -223,16 +223,17 @@ def phase_bytes(tm, L, M, sum_min_deg):
       tau     (Alg. 1) the shorter endpoint list of every edge (4 B an entry),
               the edge's endpoints (8 B) and its L typed triangle counts
               written (4L B);
-      count   (per-edge pass, given Alg. 1's triangle nodes) per T member its
-              entry, the entry of its pair with j, its tau rows toward i and j
-              and its typed offsets (4(3L+4) B), per edge its order entry,
-              endpoints, tau row, typed offsets, degrees and types of i and j
-              and their Theta and D rows (28 + 12L + 16L^2 B);
+      count   (per-edge pass) 4 B per Gamma_i entry read, per T member its two
+              edge ids, its tau rows toward i and j and its typed offsets
+              (4(3L+3) B), per edge its order entry, endpoints, tau row,
+              typed offsets, degrees and types of i and j and their Theta and
+              D rows (28 + 12L + 16L^2 B);
       cycles  4 B per degree-ordered wedge (the far end read once);
       cliques no HBM minimum is stated (candidate tests are on-chip)."""
     return {
         "tau": 4.0 * sum_min_deg + (8.0 + 4.0 * L) * M,
-        "count": (tm["t_members"] * 4.0 * (3 * L + 4) + tm["edges"] * (28.0 + 12.0 * L + 16.0 * L * L)),
+        "count": (4.0 * tm["gamma_entries"] + tm["t_members"] * 4.0 * (3 * L + 3) +
+                  tm["edges"] * (28.0 + 12.0 * L + 16.0 * L * L)),
         "cycles": 4.0 * tm["wedges"],
         "cliques": None,
     }

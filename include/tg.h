@@ -584,8 +584,7 @@ typedef struct {
     double count_ms;          /* per-edge pass: identities, closed forms,
                                  output                                      */
     uint64_t edges;           /* edges counted                               */
-    uint64_t gamma_entries;   /* positions of Gamma_i the per-edge pass covered
-                                 (scanned entries, or 32 per hit word read)  */
+    uint64_t gamma_entries;   /* entries of Gamma_i read by the per-edge pass */
     uint64_t walked_entries;  /* REUSE: entries of S_i / T lists walked      */
     uint64_t probe_pairs;     /* REUSE: (T member, T member) adjacency probes */
     uint64_t t_members;       /* T members whose tau rows were read          */

@@ -41,8 +41,6 @@ struct EdgeParams {
     uint32_t nunits;
     const uint32_t *tau;       // per edge id, L counts
     const uint32_t *tau_adj;   // per adjacency entry: tau of its edge (L counts)
-    const int64_t *hoff;       // Alg. 1's hit words of edge e from hoff[e] (NULL: none)
-    const uint32_t *hits;
     const uint32_t *theta;
     const uint32_t *dsum;
     const unsigned long long *c4e;
@@ -319,75 +317,11 @@ __device__ __forceinline__ void tsum_edge(const EdgeParams &p, int64_t e, int64_
     const int L = p.L, lane = threadIdx.x & 31;
     const int gsz = L <= 8 ? 8 : 16, ng = 32 / gsz, grp = lane / gsz, b = lane % gsz;
     const uint32_t *tn = p.tau + e * L;
-    const uint32_t *hw = p.hits ? p.hits + __ldg(p.hoff + e) : nullptr;
-    // the T members of a chunk of 32 positions of Gamma_i^a (tb: their bits,
-    // w and ejy: each member lane's entry and the entry of (j, w)) into the sums
-    auto add_members = [&](int a, int c0, unsigned tb, uint32_t w, uint32_t ejy) {
-        while (tb) {
-            // group grp takes the grp-th remaining member
-            unsigned m = tb;
-            for (int k = 0; k < grp; ++k) m &= m - 1u;
-            const bool has = m != 0u;
-            const int src = has ? __ffs(m) - 1 : 0;
-            for (int k = 0; k < ng; ++k) tb &= tb - 1u;
-            const uint32_t wy = __shfl_sync(kFull, w, src);
-            const uint32_t ej = __shfl_sync(kFull, ejy, src);
-            uint32_t vb = 0, vc = 0, vd = 0;
-            if (has && b < L) {
-                const int32_t *ty = p.toff + (int64_t)(wy & TG_IDMASK) * (L + 1);
-                vb = __ldg(p.tau_adj + (int64_t)ej * L + b);
-                vc = __ldg(p.tau_adj + (bi + c0 + src) * L + b);
-                vd = (uint32_t)(__ldg(ty + b + 1) - __ldg(ty + b));
-            }
-            for (int o = gsz; o < 32; o <<= 1) {
-                vb += __shfl_xor_sync(kFull, vb, o);
-                vc += __shfl_xor_sync(kFull, vc, o);
-                vd += __shfl_xor_sync(kFull, vd, o);
-            }
-            if (grp == 0 && b < L) {
-                Bm[a * L + b] += vb;
-                Cm[a * L + b] += vc;
-                Dm[a * L + b] += vd;
-            }
-        }
-    };
     for (int a = 0; a < L; ++a) {
         const int need = (int)__ldg(tn + a);
         if (need == 0) continue;
         const int r0 = __ldg(toi + a), r1 = __ldg(toi + a + 1);
         int found = 0;
-        if (hw) {
-            // Alg. 1 marked the members: 32 hit words per step, only the
-            // non-zero ones visited, only member entries loaded
-            const int wlast = (r1 - 1) >> 5;
-            for (int w0 = r0 >> 5; w0 <= wlast && found < need; w0 += 32) {
-                const int wi = w0 + lane;
-                uint32_t bits = 0;
-                if (wi <= wlast) {
-                    bits = __ldg(hw + wi);
-                    const int base = wi << 5;
-                    if (base < r0) bits &= ~0u << (r0 - base);
-                    if (r1 - base < 32) bits &= (1u << (r1 - base)) - 1u;
-                }
-                read += 32ull * (unsigned long long)min(32, wlast - w0 + 1);
-                unsigned nz = __ballot_sync(kFull, bits != 0u);
-                while (nz && found < need) {
-                    const int src = __ffs(nz) - 1;
-                    nz &= nz - 1u;
-                    const unsigned tb = __shfl_sync(kFull, bits, src);
-                    const int c0 = (w0 + src) << 5;
-                    uint32_t w = 0, ejy = 0;
-                    if ((tb >> lane) & 1u) {
-                        w = __ldg(p.adj + bi + c0 + lane);
-                        find(w, ejy);
-                    }
-                    found += __popc(tb);
-                    nt += (unsigned long long)__popc(tb);
-                    add_members(a, c0, tb, w, ejy);
-                }
-            }
-            continue;
-        }
         uint32_t nxt = r0 + lane < r1 ? __ldg(p.adj + bi + r0 + lane) : 0u;  // next chunk, in flight
         for (int c0 = r0; c0 < r1 && found < need; c0 += 32) {
             const int x = c0 + lane;
@@ -395,11 +329,37 @@ __device__ __forceinline__ void tsum_edge(const EdgeParams &p, int64_t e, int64_
             uint32_t w = nxt, ejy = 0;
             nxt = c0 + 32 + lane < r1 ? __ldg(p.adj + bi + c0 + 32 + lane) : 0u;
             if (x < r1) isT = find(w, ejy);
-            const unsigned tb = __ballot_sync(kFull, isT);
+            unsigned tb = __ballot_sync(kFull, isT);
             found += __popc(tb);
             read += (unsigned long long)min(32, r1 - c0);
             nt += (unsigned long long)__popc(tb);
-            add_members(a, c0, tb, w, ejy);
+            while (tb) {
+                // group grp takes the grp-th remaining member
+                unsigned m = tb;
+                for (int k = 0; k < grp; ++k) m &= m - 1u;
+                const bool has = m != 0u;
+                const int src = has ? __ffs(m) - 1 : 0;
+                for (int k = 0; k < ng; ++k) tb &= tb - 1u;
+                const uint32_t wy = __shfl_sync(kFull, w, src);
+                const uint32_t ej = __shfl_sync(kFull, ejy, src);
+                uint32_t vb = 0, vc = 0, vd = 0;
+                if (has && b < L) {
+                    const int32_t *ty = p.toff + (int64_t)(wy & TG_IDMASK) * (L + 1);
+                    vb = __ldg(p.tau_adj + (int64_t)ej * L + b);
+                    vc = __ldg(p.tau_adj + (bi + c0 + src) * L + b);
+                    vd = (uint32_t)(__ldg(ty + b + 1) - __ldg(ty + b));
+                }
+                for (int o = gsz; o < 32; o <<= 1) {
+                    vb += __shfl_xor_sync(kFull, vb, o);
+                    vc += __shfl_xor_sync(kFull, vc, o);
+                    vd += __shfl_xor_sync(kFull, vd, o);
+                }
+                if (grp == 0 && b < L) {
+                    Bm[a * L + b] += vb;
+                    Cm[a * L + b] += vc;
+                    Dm[a * L + b] += vd;
+                }
+            }
         }
     }
 }
@@ -649,8 +609,8 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
                  unsigned long long *hist, const uint32_t *tau, const uint32_t *tau_adj,
                  const uint32_t *theta,
                  const uint32_t *dsum, const unsigned long long *c4e,
-                 const unsigned long long *k4e, const int64_t *hoff, const uint32_t *hits,
-                 unsigned long long *work, const tg_tune &t, cudaStream_t s) {
+                 const unsigned long long *k4e, unsigned long long *work, const tg_tune &t,
+                 cudaStream_t s) {
     if (un.nunits == 0 || count <= 0) return TG_OK;
     const int L = g->L, L2 = L * L;
     if (g->max_degree >= ((int64_t)1 << 27)) return TG_EOVERFLOW;  // 32-lane uint32 sums
@@ -665,8 +625,6 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
     p.ustart = un.ustart.p;
     p.tau = tau;
     p.tau_adj = tau_adj;
-    p.hoff = hits ? hoff : nullptr;
-    p.hits = hoff ? hits : nullptr;
     p.theta = theta;
     p.dsum = dsum;
     p.c4e = c4e;

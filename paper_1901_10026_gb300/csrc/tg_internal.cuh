@@ -185,8 +185,8 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
                  unsigned long long *hist, const uint32_t *tau, const uint32_t *tau_adj,
                  const uint32_t *theta,
                  const uint32_t *dsum, const unsigned long long *c4e,
-                 const unsigned long long *k4e, const int64_t *hoff, const uint32_t *hits,
-                 unsigned long long *work, const tg_tune &t, cudaStream_t s);
+                 const unsigned long long *k4e, unsigned long long *work, const tg_tune &t,
+                 cudaStream_t s);
 
 // Counts through Alg. 1's typed triangle counts (tg_reuse.cu).  full_order is
 // the grouped order of all M edges; order[0..count) the edges to count.  With

@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32
                                              const uint32_t *order, const uint32_t *ustart,
                                              const uint32_t *ulist, uint32_t nunits, int32_t L,
                                              int64_t nbits, unsigned long long *queue,
-                                             uint32_t *tau, const int64_t *hoff, uint32_t *hits) {
+                                             uint32_t *tau) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
     const int64_t bwords = (nbits + 31) >> 5;
@@ -211,27 +211,10 @@ __global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32
                     const unsigned hm = __ballot_sync(kFull, hit);
                     const int cb = c0 + 32 * u;
                     if (lane < L) mine += __popc(hm & word_bits(ts0 - cb, ts1 - cb));
-                    if (hits && lane == 31 && cb < di) hits[hoff[e] + (cb >> 5)] = hm;
                 }
             }
             if (lane < L) tau[(int64_t)e * L + lane] = mine;
         }
-    }
-}
-
-// Hit words of Alg. 1: for edge e = (i, j), i its lower-degree end, one bit
-// per position of Gamma_i (set when the entry is a triangle node, i.e. in
-// T_ij), ceil(d_i / 32) words from hoff[e].  cnt[e] = that word count.
-__global__ void k_hit_words(const int2 *edges, const int64_t *rowptr, int64_t M, int64_t *cnt) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= M;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        if (e == M) {
-            cnt[M] = 0;
-            continue;
-        }
-        const int2 ab = edges[e];
-        const int i = max(ab.x, ab.y);
-        cnt[e] = (rowptr[i + 1] - rowptr[i] + 31) >> 5;
     }
 }
 
@@ -254,7 +237,7 @@ __global__ void __launch_bounds__(kLightWarps * 32) k_tau_light(
     const int64_t *rowptr, const uint32_t *adj, const int32_t *toff, const int2 *edges,
     const uint32_t *order,
     const uint32_t *ustart, const uint32_t *ulist, uint32_t nlist, int32_t L,
-    unsigned long long *queue, uint32_t *tau, const int64_t *hoff, uint32_t *hits) {
+    unsigned long long *queue, uint32_t *tau) {
     __shared__ uint32_t keys[kLightWarps][1 << TG_LIGHT_LG];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *hk = keys[warp];
@@ -292,7 +275,6 @@ __global__ void __launch_bounds__(kLightWarps * 32) k_tau_light(
                 }
                 const unsigned hm = __ballot_sync(kFull, hit);
                 if (lane < L) mine += __popc(hm & word_bits(ts0 - c0, ts1 - c0));
-                if (hits && lane == 31) hits[hoff[e] + (c0 >> 5)] = hm;
             }
             if (lane < L) tau[(int64_t)e * L + lane] = mine;
         }
@@ -1012,25 +994,9 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
     TG_TRY(timing_begin(s, &work));
     // tau for every edge of the graph (the identities need tau of edges
     // outside the counted range as well)
-    DevBuf<uint32_t> tau, theta, dsum, hits;
-    DevBuf<int64_t> hoff;
+    DevBuf<uint32_t> tau, theta, dsum;
     tg_units un;
     if (!tau.alloc((size_t)M * L, s)) return TG_ENOMEM;
-    // hit words of Alg. 1 for the per-edge pass (cycles kernel, k = 4), when
-    // they fit in an eighth of free memory; without them the pass finds the
-    // triangle nodes again by membership tests
-    if (k == 4 && (t.kernel == TG_KERNEL_CYCLES || t.kernel == TG_KERNEL_AUTO) && count > 0 && M > 0) {
-        if (!hoff.alloc(M + 1, s)) return TG_ENOMEM;
-        k_hit_words<<<grid_r(M + 1), 256, 0, s>>>(g->edges, g->rowptr, M, hoff.p); tg_note_launch();
-        TG_TRY_CUDA(cudaGetLastError());
-        TG_TRY(tg_scan_i64(hoff.p, hoff.p, M + 1, s));
-        int64_t words = 0;
-        TG_TRY_CUDA(cudaMemcpyAsync(&words, hoff.p + M, 8, cudaMemcpyDeviceToHost, s));
-        TG_TRY_CUDA(cudaStreamSynchronize(s));
-        size_t fb = 0, tb = 0;
-        TG_TRY_CUDA(cudaMemGetInfo(&fb, &tb));
-        if ((size_t)words * 4 > fb / 8 || !hits.alloc((size_t)std::max<int64_t>(1, words), s)) hoff.reset();
-    }
     {
         // tau of every edge, in the grouped order of the whole graph
         const uint32_t *ord = full_order;
@@ -1055,7 +1021,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
             if (grid < 1) grid = 1;
             k_tau<<<(unsigned)grid, 512, smem, s>>>(g->rowptr, g->adj, g->toff, g->ntype, g->edges, ord,
                                                     un.ustart.p, un.heavy.p, un.nheavy, L, nbits,
-                                                    q.p, tau.p, hoff.p, hoff.p ? hits.p : nullptr); tg_note_launch();
+                                                    q.p, tau.p); tg_note_launch();
             TG_TRY_CUDA(cudaGetLastError());
         }
         if (un.nlight > 0) {
@@ -1068,7 +1034,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
             if (grid > need) grid = need;
             k_tau_light<<<(unsigned)grid, kLightWarps * 32, 0, s>>>(
                 g->rowptr, g->adj, g->toff, g->edges, ord, un.ustart.p, un.light.p, un.nlight, L,
-                q.p + 1, tau.p, hoff.p, hoff.p ? hits.p : nullptr); tg_note_launch();
+                q.p + 1, tau.p); tg_note_launch();
             TG_TRY_CUDA(cudaGetLastError());
         }
     }
@@ -1146,7 +1112,7 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
             TG_TRY_CUDA(cudaGetLastError());
         }
         TG_TRY(tg_cyc_edges(g, k, level, order, count, *ue, rows, width, hist, tau.p, tau_adj.p,
-                            theta.p, dsum.p, c4e.p, k4e.p, hoff.p, hoff.p ? hits.p : nullptr, work, t, s));
+                            theta.p, dsum.p, c4e.p, k4e.p, work, t, s));
         if (fast) TG_TRY(tg_cyc_correct(hist, L, g4c.p, g4k.p, s));
         TG_TRY_CUDA(cudaEventRecord(g_last.ev[5], s));
         g_last.edges = (uint64_t)count;
