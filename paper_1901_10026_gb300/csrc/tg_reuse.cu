@@ -131,9 +131,10 @@ __device__ __forceinline__ uint32_t word_bits(int lo, int hi) {
     return up & ~((1u << lo) - 1u);
 }
 
-constexpr int kTauUnroll = 4;
+constexpr int kTauUnroll = 8;       // chunks of 32 entries in flight per warp
+constexpr int kTauThreads = 1024;   // one CTA per SM holds the bitmap: 32 warps share it
 
-__global__ void __launch_bounds__(512) k_tau(const int64_t *rowptr, const uint32_t *adj,
+__global__ void __launch_bounds__(kTauThreads) k_tau(const int64_t *rowptr, const uint32_t *adj,
                                              const int32_t *toff, const uint8_t *ntype,
                                              const int2 *edges,
                                              const uint32_t *order, const uint32_t *ustart,
@@ -1014,12 +1015,12 @@ int tg_reuse_count(const tg_graph *g, int k, int level, const uint32_t *full_ord
             const size_t smem = ((((size_t)((nbits + 31) >> 5)) * 4 + 15) & ~(size_t)15) + 16;
             TG_TRY(tg_allow_max_smem((const void *)k_tau));
             int per_sm = 0;
-            TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tau, 512, smem));
+            TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tau, kTauThreads, smem));
             if (per_sm < 1) per_sm = 1;
             int64_t grid = (int64_t)tg_num_sms() * per_sm;
             if (grid > (int64_t)un.nheavy) grid = un.nheavy;
             if (grid < 1) grid = 1;
-            k_tau<<<(unsigned)grid, 512, smem, s>>>(g->rowptr, g->adj, g->toff, g->ntype, g->edges, ord,
+            k_tau<<<(unsigned)grid, kTauThreads, smem, s>>>(g->rowptr, g->adj, g->toff, g->ntype, g->edges, ord,
                                                     un.ustart.p, un.heavy.p, un.nheavy, L, nbits,
                                                     q.p, tau.p); tg_note_launch();
             TG_TRY_CUDA(cudaGetLastError());
