@@ -41,6 +41,7 @@ struct EdgeParams {
     uint32_t nunits;
     const uint32_t *tau;       // per edge id, L counts
     const uint32_t *tau_adj;   // per adjacency entry: tau of its edge (L counts)
+    const uint32_t *tdeg;      // L = 8: typed degrees, 8 per node (NULL otherwise)
     const uint32_t *theta;
     const uint32_t *dsum;
     const unsigned long long *c4e;
@@ -302,13 +303,41 @@ __device__ void edge_finish(const EdgeParams &p, unsigned long long *shist, int6
 // find(w, pjy) tells whether the entry w of Gamma_i lies in Gamma_j, and gives
 // the adjacency entry of the edge (j, w).  Triangle counts are read per
 // adjacency entry: tau_iy at Gamma_i's own entry (along the scan) and tau_jy
-// at that entry (Gamma_j's rows stay in L2 while its unit runs).  The T
-// members of a chunk (all of type a) go to lane groups of 8 (L <= 8) or 16
-// lanes; lane b of a group reads tau_jy[b], tau_iy[b] and d_y^b (three
-// coalesced rows), the groups' values are added across the warp and the
-// first group adds them to B, C, DT.  Called by all
+// at that entry (Gamma_j's rows stay in L2 while its unit runs).  A chunk
+// with at least kLaneGather T members (all of type a) has each member lane
+// load its own three rows at once (16-byte loads of 32-byte rows when L = 8,
+// the typed degrees from a per-node row array) and sums each row over the
+// warp with one reduce-scatter; a sparser chunk gives its members to lane
+// groups of 8 (L <= 8) or 16 lanes, lane b of a group reading tau_jy[b],
+// tau_iy[b] and d_y^b (three coalesced rows), the groups' values added
+// across the warp and added to B, C, DT by the first group.  Called by all
 // 32 lanes; adds the entries of Gamma_i it read to *read and the T members to
 // *nt (lane-uniform values).
+constexpr int kLaneGather = 6;  // members per chunk from which each member lane gathers its own rows
+
+// Sum of v[0..7] over the 32 lanes, scattered: lane x ends with the total of
+// index ((x >> 4) & 1) * 4 + ((x >> 3) & 1) * 2 + ((x >> 2) & 1) (nine
+// shuffles instead of eight full reductions); returns that index via *idx.
+__device__ __forceinline__ uint32_t warp_sum8_scatter(uint32_t (&v)[8], int lane, int *idx) {
+    const bool h4 = (lane >> 4) & 1, h3 = (lane >> 3) & 1, h2 = (lane >> 2) & 1;
+    uint32_t a[4], b2[2];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t keep = h4 ? v[k + 4] : v[k], give = h4 ? v[k] : v[k + 4];
+        a[k] = keep + __shfl_xor_sync(kFull, give, 16);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const uint32_t keep = h3 ? a[k + 2] : a[k], give = h3 ? a[k] : a[k + 2];
+        b2[k] = keep + __shfl_xor_sync(kFull, give, 8);
+    }
+    uint32_t c = (h2 ? b2[1] : b2[0]) + __shfl_xor_sync(kFull, h2 ? b2[0] : b2[1], 4);
+    c += __shfl_xor_sync(kFull, c, 2);
+    c += __shfl_xor_sync(kFull, c, 1);
+    *idx = (h4 ? 4 : 0) + (h3 ? 2 : 0) + (h2 ? 1 : 0);
+    return c;
+}
+
 template <class Find>
 __device__ __forceinline__ void tsum_edge(const EdgeParams &p, int64_t e, int64_t bi,
                                           const int32_t *toi, Find find, unsigned long long *Bm,
@@ -333,6 +362,62 @@ __device__ __forceinline__ void tsum_edge(const EdgeParams &p, int64_t e, int64_
             found += __popc(tb);
             read += (unsigned long long)min(32, r1 - c0);
             nt += (unsigned long long)__popc(tb);
+            if (p.tdeg && __popc(tb) >= kLaneGather) {
+                // L = 8 and many members in this chunk: each member lane
+                // loads its own three 32-byte rows (two 16-byte loads each, all
+                // in flight at once), then one reduce-scatter per row
+                uint4 r[6];
+                if (isT) {
+                    const uint4 *rb = reinterpret_cast<const uint4 *>(p.tau_adj + (int64_t)ejy * 8);
+                    const uint4 *rc = reinterpret_cast<const uint4 *>(p.tau_adj + (bi + x) * 8);
+                    const uint4 *rd = reinterpret_cast<const uint4 *>(p.tdeg + (int64_t)(w & TG_IDMASK) * 8);
+                    r[0] = __ldg(rb);
+                    r[1] = __ldg(rb + 1);
+                    r[2] = __ldg(rc);
+                    r[3] = __ldg(rc + 1);
+                    r[4] = __ldg(rd);
+                    r[5] = __ldg(rd + 1);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) r[q] = make_uint4(0u, 0u, 0u, 0u);
+                }
+                unsigned long long *dst[3] = {Bm, Cm, Dm};
+#pragma unroll
+                for (int row = 0; row < 3; ++row) {
+                    uint32_t v[8] = {r[2 * row].x, r[2 * row].y, r[2 * row].z, r[2 * row].w,
+                                     r[2 * row + 1].x, r[2 * row + 1].y, r[2 * row + 1].z, r[2 * row + 1].w};
+                    int bidx = 0;
+                    const uint32_t sum = warp_sum8_scatter(v, lane, &bidx);
+                    if ((lane & 3) == 0) dst[row][a * 8 + bidx] += sum;
+                }
+                continue;
+            }
+            if (L < 8 && __popc(tb) >= kLaneGather) {
+                // the same with scalar loads (rows of L < 8 counts)
+                uint32_t v[8];
+                int bidx = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = (isT && q < L) ? __ldg(p.tau_adj + (int64_t)ejy * L + q) : 0u;
+                uint32_t sum = warp_sum8_scatter(v, lane, &bidx);
+                if ((lane & 3) == 0 && bidx < L) Bm[a * L + bidx] += sum;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = (isT && q < L) ? __ldg(p.tau_adj + (bi + x) * L + q) : 0u;
+                sum = warp_sum8_scatter(v, lane, &bidx);
+                if ((lane & 3) == 0 && bidx < L) Cm[a * L + bidx] += sum;
+                {
+                    const int32_t *ty = p.toff + (int64_t)(w & TG_IDMASK) * (L + 1);
+                    int32_t prev = isT ? __ldg(ty) : 0;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int32_t nx = (isT && q < L) ? __ldg(ty + q + 1) : prev;
+                        v[q] = (uint32_t)(nx - prev);
+                        prev = nx;
+                    }
+                }
+                sum = warp_sum8_scatter(v, lane, &bidx);
+                if ((lane & 3) == 0 && bidx < L) Dm[a * L + bidx] += sum;
+                continue;
+            }
             while (tb) {
                 // group grp takes the grp-th remaining member
                 unsigned m = tb;
@@ -604,6 +689,18 @@ int smem_optin_e() {
 
 }  // namespace
 
+namespace {
+// tdeg[v 8 + t] = d_v^t (L = 8), rows of 32 bytes for 16-byte loads
+__global__ void k_typed_degrees(const int32_t *toff, int64_t n, uint32_t *tdeg) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n * 8;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = x >> 3;
+        const int t = (int)(x & 7);
+        tdeg[x] = (uint32_t)(toff[v * 9 + t + 1] - toff[v * 9 + t]);
+    }
+}
+}  // namespace
+
 int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int64_t count,
                  const tg_units &un, uint64_t *rows, int64_t width,
                  unsigned long long *hist, const uint32_t *tau, const uint32_t *tau_adj,
@@ -625,6 +722,13 @@ int tg_cyc_edges(const tg_graph *g, int k, int level, const uint32_t *order, int
     p.ustart = un.ustart.p;
     p.tau = tau;
     p.tau_adj = tau_adj;
+    DevBuf<uint32_t> tdeg;
+    if (L == 8 && k == 4 && tdeg.alloc((size_t)g->n * 8, s)) {
+        k_typed_degrees<<<(unsigned)std::min<int64_t>((g->n * 8 + 255) / 256, 65535LL * 16), 256, 0, s>>>(
+            g->toff, g->n, tdeg.p); tg_note_launch();
+        TG_TRY_CUDA(cudaGetLastError());
+        p.tdeg = tdeg.p;
+    }
     p.theta = theta;
     p.dsum = dsum;
     p.c4e = c4e;
