@@ -316,14 +316,18 @@ def recorded_oracle2(workload_name):
     """The second oracle's time for the whole graph, as recorded in the header
     of the committed golden histogram (not re-measured by this run)."""
     path = os.path.join(ROOT, "tests", "golden", f"{workload_name}_o2_global.txt")
+    M = None
     try:
         for line in open(path):
             if not line.startswith("#"):
                 break
+            if "M = " in line:
+                M = int(line.split("M = ")[1].split()[0])
             if "from oracle.o2 alone" in line:
                 sec = float(line.split("(")[1].split(" s on ")[0])
                 thr = int(line.split(" s on ")[1].split()[0])
-                return {"seconds": sec, "cores": thr, "edges_per_s": None,
+                return {"seconds": sec, "cores": thr, "edges_per_s": (M / sec) if M else None,
+                        "what": "whole-graph global count by the second oracle",
                         "where": "build host (x86_64), recorded when the golden file was written",
                         "source": f"tests/golden/{workload_name}_o2_global.txt"}
     except (OSError, ValueError, IndexError):
