@@ -253,17 +253,7 @@ __global__ void k_batch_warp(BatchParams bp) {
                 const uint64_t g10 = (uint64_t)(int64_t)cnt[B10 * P + pr];
                 const uint64_t g12 = (uint64_t)(int64_t)cnt[B12 * P + pr];
                 uint64_t g4, g5, g9, g11;
-                if (t == u) {
-                    g4 = sit * sjt - g6;
-                    g5 = c2(sit) + c2(sjt) - g7;
-                    g9 = tt * (sit + sjt) - g10;
-                    g11 = c2(tt) - g12;
-                } else {
-                    g4 = sit * sju + siu * sjt - g6;
-                    g5 = sit * siu + sjt * sju - g7;
-                    g9 = tt * (siu + sju) + tu * (sit + sjt) - g10;
-                    g11 = tt * tu - g12;
-                }
+                closed_forms(t == u, sit, siu, sjt, sju, tt, tu, g6, g7, g10, g12, g4, g5, g9, g11);
                 if (!bp.global) {
                     uint64_t *row = G.rows + e * G.width + 2 * L;
                     if (bp.level == TG_ORBIT) {

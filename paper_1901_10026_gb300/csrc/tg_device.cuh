@@ -31,6 +31,28 @@ __device__ __forceinline__ void unpair(int L, int p, int &t, int &u) {
 
 __device__ __forceinline__ uint64_t c2(uint64_t x) { return x < 2 ? 0 : x * (x - 1) / 2; }
 
+// The closed forms of Sec. "Combinatorial Relationships" for the type pair
+// (t, u) of an edge: g4 (4-path centre), g5 (4-star), g9 (tailed-triangle
+// edge at the degree-3 node) and g11 (chordal-cycle chord) from the typed
+// set sizes |S_i^t|, |S_i^u|, |S_j^t|, |S_j^u|, |T^t|, |T^u| and the
+// enumerated g6, g7, g10, g12 of the same pair (mod 2^64).
+__device__ __forceinline__ void closed_forms(bool same, uint64_t sit, uint64_t siu, uint64_t sjt,
+                                             uint64_t sju, uint64_t tt, uint64_t tu, uint64_t g6,
+                                             uint64_t g7, uint64_t g10, uint64_t g12, uint64_t &g4,
+                                             uint64_t &g5, uint64_t &g9, uint64_t &g11) {
+    if (same) {
+        g4 = sit * sjt - g6;
+        g5 = c2(sit) + c2(sjt) - g7;
+        g9 = tt * (sit + sjt) - g10;
+        g11 = c2(tt) - g12;
+    } else {
+        g4 = sit * sju + siu * sjt - g6;
+        g5 = sit * siu + sjt * sju - g7;
+        g9 = tt * (siu + sju) + tu * (sit + sjt) - g10;
+        g11 = tt * tu - g12;
+    }
+}
+
 __device__ __forceinline__ int64_t colex3(int a, int b, int c) {
     // a <= b <= c
     return (int64_t)a + (int64_t)(b + 1) * b / 2 + (int64_t)(c + 2) * (c + 1) * c / 6;

@@ -165,17 +165,7 @@ __device__ __forceinline__ void pair_orbits_tab(const long long *xt, int L, int 
     const uint64_t g3 = (uint64_t)(t == u ? y_tu : y_tu + y_ut);
     const uint64_t g8 = (uint64_t)sym(XT_Z);
     uint64_t g4, g5, g9, g11;
-    if (t == u) {
-        g4 = sit * sjt - g6;
-        g5 = c2(sit) + c2(sjt) - g7;
-        g9 = tt * (sit + sjt) - g10;
-        g11 = c2(tt) - g12;
-    } else {
-        g4 = sit * sju + siu * sjt - g6;
-        g5 = sit * siu + sjt * sju - g7;
-        g9 = tt * (siu + sju) + tu * (sit + sjt) - g10;
-        g11 = tt * tu - g12;
-    }
+    closed_forms(t == u, sit, siu, sjt, sju, tt, tu, g6, g7, g10, g12, g4, g5, g9, g11);
     g[0] = g3;
     g[1] = g4;
     g[2] = g5;

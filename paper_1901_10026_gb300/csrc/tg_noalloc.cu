@@ -161,17 +161,7 @@ __global__ void __launch_bounds__(kNaBlock) k_noalloc_count(NaParams p) {
                 const uint64_t g7 = (uint64_t)cnt[C7 * P + pr], g8 = (uint64_t)cnt[C8 * P + pr];
                 const uint64_t g10 = (uint64_t)cnt[C10 * P + pr], g12 = (uint64_t)cnt[C12 * P + pr];
                 uint64_t g4, g5, g9, g11;
-                if (t == u) {
-                    g4 = sit * sjt - g6;
-                    g5 = c2(sit) + c2(sjt) - g7;
-                    g9 = tt * (sit + sjt) - g10;
-                    g11 = c2(tt) - g12;
-                } else {
-                    g4 = sit * sju + siu * sjt - g6;
-                    g5 = sit * siu + sjt * sju - g7;
-                    g9 = tt * (siu + sju) + tu * (sit + sjt) - g10;
-                    g11 = tt * tu - g12;
-                }
+                closed_forms(t == u, sit, siu, sjt, sju, tt, tu, g6, g7, g10, g12, g4, g5, g9, g11);
                 const uint64_t h[6] = {g3 + g4, g5, g6, g7 + g8 + g9, g10 + g11, g12};
                 int a = ti, b = tj, c = t, d = u;
                 sort2(a, b);
