@@ -951,18 +951,17 @@ __global__ void __launch_bounds__(kC4WalkWarps * 32) k_c4_bin_walk(C4Bin p) {
 // neighbours, else 32-bit counts); the first entry of a far end puts it on a
 // list (a bit per far end keeps it there once).  Then one thread per listed
 // far end reads its counts, clears them, and for the types it has (usually
-// few) adds C(c_t, 2) and c_t c_t' to its warp's table acc[type of b][pair]
+// few) adds C(c_t, 2) and c_t c_t' to the CTA's table acc[type of b][pair]
 // in shared memory (atomic adds), which goes into the histogram under
-// {ta, tb, t, t'} when the anchor changes.  Types beyond kBinAccL use c4_add
+// {ta, tb, t, t'} when the anchor changes.  1024-thread CTAs, two per SM.  Types beyond kBinAccL use c4_add
 // straight into a shared histogram instead.
-constexpr int kBinPairThreads = 512;
+constexpr int kBinPairThreads = 1024;
 constexpr int kBinRun = 16;
 constexpr int kBinAccL = 8;
 
 __device__ __forceinline__ void bin_flush(unsigned long long *acc, unsigned long long *h4, int L,
                                           int P, int ta) {
-    const int lane = threadIdx.x & 31;
-    for (int k = lane; k < L * P; k += 32) {
+    for (int k = threadIdx.x; k < L * P; k += blockDim.x) {
         const unsigned long long v = acc[k];
         if (!v) continue;
         acc[k] = 0ull;
@@ -974,14 +973,14 @@ __device__ __forceinline__ void bin_flush(unsigned long long *acc, unsigned long
 
 __global__ void __launch_bounds__(kBinPairThreads) k_c4_bin_pairs(C4Bin p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NW = kBinPairThreads / 32;
+    const int tid = threadIdx.x;
     const int L = p.L, Lp = L + (L & 1), P = L * (L + 1) / 2;
     const bool acc_mode = L <= kBinAccL;
     const int nfar = 1 << p.wlg;
     unsigned long long *h4 = reinterpret_cast<unsigned long long *>(smem);
     size_t off = ((size_t)p.n4 * 8 + 15) & ~(size_t)15;
-    unsigned long long *acc = reinterpret_cast<unsigned long long *>(smem + off) + (size_t)warp * L * P;
-    if (acc_mode) off += (size_t)NW * L * P * 8;
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(smem + off);  // one per CTA
+    if (acc_mode) off += ((size_t)L * P * 8 + 15) & ~(size_t)15;
     uint32_t *tab = reinterpret_cast<uint32_t *>(smem + off);
     const int twords = p.half ? nfar * (Lp >> 1) : nfar * L;
     uint32_t *tbits = tab + twords;                                      // nfar / 32 words
@@ -991,7 +990,7 @@ __global__ void __launch_bounds__(kBinPairThreads) k_c4_bin_pairs(C4Bin p) {
     __shared__ uint32_t s_nl;
     for (int64_t q = tid; q < p.n4; q += blockDim.x) h4[q] = 0ull;
     if (acc_mode)
-        for (int q = lane; q < L * P; q += 32) acc[q] = 0ull;
+        for (int q = tid; q < L * P; q += blockDim.x) acc[q] = 0ull;
     for (int q = tid; q < twords + nfar / 32; q += blockDim.x) tab[q] = 0u;
     if (tid == 0) s_nl = 0u;
     const uint32_t wmask = (uint32_t)nfar - 1u;
@@ -2346,7 +2345,7 @@ int c4_bin_waves(const tg_graph *g, const uint32_t *list, int64_t na,
         const size_t nfar = (size_t)1 << pw.wlg;
         const int P = L * (L + 1) / 2;
         const size_t psmem = (((size_t)n4 * 8 + 15) & ~(size_t)15) +
-                             (L <= kBinAccL ? (size_t)(kBinPairThreads / 32) * L * P * 8 : 0) +
+                             (L <= kBinAccL ? (((size_t)L * P * 8 + 15) & ~(size_t)15) : 0) +
                              (pw.half ? nfar * (Lp >> 1) : nfar * L) * 4 + nfar / 32 * 4 + nfar * 2;
         int pper = 0;
         TG_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pper, k_c4_bin_pairs,
