@@ -818,7 +818,7 @@ struct C4Bin {
     unsigned long long *work;  // [4]: wedges
 };
 
-constexpr int kBinUnroll = 4;
+constexpr int kBinUnroll = 2;
 constexpr int kBinFill = 32;            // default: binned when a walk averages this many wedges per window
 constexpr size_t kBinTable = 64 * 1024;  // bytes of the dense far-end table
 
