@@ -66,6 +66,12 @@ def test_directed_rmat14():
     _check(G)
 
 
+@pytest.mark.parametrize("L", [1, 16])
+def test_type_count_extremes(L):
+    # L = 1 (untyped census) and the largest L (the widest shared histogram)
+    _check(synth.er_directed(600, 5000, 0.3, L, seed=11 + L))
+
+
 @pytest.mark.parametrize("n", [3, 50, 300])
 def test_stars_and_cliques(n):
     star = [(0, v) for v in range(1, n)] + [(v, 0) for v in range(1, n, 3)]
