@@ -789,7 +789,8 @@ __device__ __forceinline__ void k4_hist_add(unsigned long long *h4, int a, int b
 // (anchor, b >> wlg).  A count pass sizes the buckets and a fill pass writes
 // them, each with one counter add per distinct bucket among a warp's 32
 // wedges (a member's list is sorted by (type, id), so neighbouring wedges
-// mostly share a window).  k_c4_bin_pairs then gives each bucket to a CTA,
+// mostly share a window; a run of equal buckets among consecutive lanes takes
+// its slots with one add).  k_c4_bin_pairs then gives each bucket to a CTA,
 // which counts its entries by (b, t) in a dense shared-memory table of the
 // window's 2^wlg far ends and adds each far end's cycle pairs to the
 // type-multiset histogram (c4_add).  DRAM sees the walk twice and 2 bytes
@@ -846,7 +847,6 @@ __device__ __forceinline__ int64_t c4_chunk_bin(const C4Bin &p, uint32_t a, uint
     for (IT b0 = lo; b0 < hi; b0 += 32 * kBinUnroll) {
         uint32_t bv[kBinUnroll], base[kBinUnroll];
         int tv[kBinUnroll];
-        unsigned mm[kBinUnroll];
         bool ok[kBinUnroll];
 #pragma unroll
         for (int q = 0; q < kBinUnroll; ++q) {
@@ -872,24 +872,34 @@ __device__ __forceinline__ int64_t c4_chunk_bin(const C4Bin &p, uint32_t a, uint
                 }
             }
         }
+        // runs of equal buckets among consecutive lanes (a member's list is
+        // sorted by (type, id), so consecutive wedges mostly share a window):
+        // the first lane of a run takes the run's slots with one add
+        int rs[kBinUnroll];
 #pragma unroll
         for (int q = 0; q < kBinUnroll; ++q) {
             const int key = ok[q] ? (int)(bv[q] >> p.wlg) : -1;
-            mm[q] = __match_any_sync(kFull, key);
+            const int prev = __shfl_up_sync(kFull, key, 1);
+            const unsigned heads = __ballot_sync(kFull, lane == 0 || key != prev);
+            const unsigned upto = heads & ((2u << lane) - 1u);  // heads at or below this lane
+            rs[q] = 31 - __clz(upto);
+            const unsigned above = heads & ~((2u << lane) - 1u);
+            const int re = above ? __ffs(above) - 1 : 32;
             base[q] = 0u;
-            if (ok[q] && lane == __ffs(mm[q]) - 1) {
+            mm[q] = 0u;
+            if (key >= 0 && rs[q] == lane) {
                 if (kFill)
-                    base[q] = atomicAdd(cb + key, (uint32_t)__popc(mm[q]));
+                    base[q] = atomicAdd(cb + key, (uint32_t)(re - lane));
                 else
-                    atomicAdd(cb + key, (uint32_t)__popc(mm[q]));
+                    atomicAdd(cb + key, (uint32_t)(re - lane));
             }
         }
 #pragma unroll
         for (int q = 0; q < kBinUnroll; ++q) {
             if (kFill) {
-                const uint32_t bb = __shfl_sync(kFull, base[q], __ffs(mm[q]) - 1);
+                const uint32_t bb = __shfl_sync(kFull, base[q], rs[q]);
                 if (ok[q])
-                    p.bins[bb + (uint32_t)__popc(mm[q] & ((1u << lane) - 1u))] =
+                    p.bins[bb + (uint32_t)(lane - rs[q])] =
                         (uint16_t)((bv[q] & wmask) | ((uint32_t)tv[q] << p.wlg));
             } else if (ok[q]) {
                 ++wk;
