@@ -886,7 +886,6 @@ __device__ __forceinline__ int64_t c4_chunk_bin(const C4Bin &p, uint32_t a, uint
             const unsigned above = heads & ~((2u << lane) - 1u);
             const int re = above ? __ffs(above) - 1 : 32;
             base[q] = 0u;
-            mm[q] = 0u;
             if (key >= 0 && rs[q] == lane) {
                 if (kFill)
                     base[q] = atomicAdd(cb + key, (uint32_t)(re - lane));
