@@ -97,3 +97,95 @@ def counts(n, src, dst, types, L):
                 w = (set(tri) - {x, y}).pop()
                 rows[eidx[(min(x, y), max(x, y))]][c * L + int(types[w])] += 1
     return und, rows, glob
+
+
+# ---------------------------------------------------------------- 4 nodes --
+# Directed typed 4-node graphlets: every 4-node subset whose underlying graph
+# is connected, classified by the smallest code over the 24 relabellings (the
+# code of a digraph on positions 0..3 is the sum of 2^(4a + b) over its arcs
+# a -> b); class c is the c-th smallest such code among the connected
+# digraphs (199 of them).
+
+_PERMS4 = list(itertools.permutations(range(4)))
+
+
+def _code4(nodes, arcs):
+    c = 0
+    for a, x in enumerate(nodes):
+        for b, y in enumerate(nodes):
+            if a != b and (x, y) in arcs:
+                c |= 1 << (4 * a + b)
+    return c
+
+
+def _canon4(code):
+    best = None
+    for pm in _PERMS4:
+        c = 0
+        for a in range(4):
+            for b in range(4):
+                if a != b and (code >> (4 * a + b)) & 1:
+                    c |= 1 << (4 * pm[a] + pm[b])
+        best = c if best is None or c < best else best
+    return best
+
+
+def _connected4(code):
+    adj = [set() for _ in range(4)]
+    for a in range(4):
+        for b in range(4):
+            if a != b and (code >> (4 * a + b)) & 1:
+                adj[a].add(b)
+                adj[b].add(a)
+    seen, stack = {0}, [0]
+    while stack:
+        v = stack.pop()
+        for w in adj[v]:
+            if w not in seen:
+                seen.add(w)
+                stack.append(w)
+    return len(seen) == 4
+
+
+_CLASS4 = None
+
+
+def class_table4():
+    """Sorted canonical codes of the connected 4-node digraphs."""
+    global _CLASS4
+    if _CLASS4 is None:
+        codes = set()
+        for code in range(1 << 16):
+            if code & 0x8421 or not _connected4(code):
+                continue
+            codes.add(_canon4(code))
+        _CLASS4 = sorted(codes)
+    return _CLASS4
+
+
+def counts4(n, src, dst, types, L):
+    """(canonical edges, per-edge rows as lists of 199 P, global counts list)."""
+    table = {c: q for q, c in enumerate(class_table4())}
+    arcs = arc_set(src, dst)
+    und = sorted({(min(a, b), max(a, b)) for a, b in arcs})
+    eidx = {e: q for q, e in enumerate(und)}
+    P = L * (L + 1) // 2
+    rows = [[0] * (199 * P) for _ in und]
+    n4 = (L + 3) * (L + 2) * (L + 1) * L // 24
+
+    def colex4(t):
+        a, b, c, d = sorted(t)
+        return a + (b + 1) * b // 2 + (c + 2) * (c + 1) * c // 6 + (d + 3) * (d + 2) * (d + 1) * d // 24
+
+    glob = [0] * (199 * n4)
+    for quad in itertools.combinations(range(n), 4):
+        code = _code4(quad, arcs)
+        if not _connected4(code):
+            continue
+        c = table[_canon4(code)]
+        glob[c * n4 + colex4([int(types[v]) for v in quad])] += 1
+        for x, y in itertools.combinations(quad, 2):
+            if (min(x, y), max(x, y)) in eidx:
+                t, u = sorted(int(types[v]) for v in quad if v not in (x, y))
+                rows[eidx[(min(x, y), max(x, y))]][c * P + t * L - t * (t - 1) // 2 + (u - t)] += 1
+    return und, rows, glob
