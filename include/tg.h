@@ -318,6 +318,31 @@ int64_t tg_dir_global_len(int32_t L);
 int tg_count_directed_per_edge(const tg_graph *g, uint64_t *rows, void *stream);
 int tg_count_directed_global(const tg_graph *g, uint64_t *out, void *stream);
 
+/*
+ * Directed typed 4-node graphlets (same section; the paper lists no directed
+ * 4-node motifs).  A directed 4-node graphlet is a connected induced subgraph
+ * on four nodes with its arcs, keyed by its isomorphism class and the sorted
+ * multiset of its node types.  There are 199 classes, numbered by canonical
+ * code: the code of a digraph on positions 0..3 is the sum of 2^(4a + b) over
+ * its arcs a -> b, its canonical code the smallest over the 24 relabellings,
+ * and class c has the c-th smallest canonical code among the connected ones.
+ * Per-edge rows: M rows of tg_dir4_slots(L) = 199 P uint64 (P = L(L+1)/2),
+ * slot c P + pair(t, u) for the types t <= u of the two other nodes
+ * (pair(a, b) = a L - a(a-1)/2 + (b - a)).  Global counts:
+ * tg_dir4_global_len(L) = 199 C(L+3, 4), class c's block at c C(L+3, 4),
+ * inside it the colex rank of the sorted type multiset; each the per-edge sum
+ * divided by the class's number of underlying edges (3 to 6).  One warp per
+ * edge enumerates the candidate sets {i, j, w, r} (w a neighbour of i or j, r
+ * a later such neighbour or a neighbour of w): work grows with the square of
+ * the endpoint degrees, so this form suits graphs of moderate degree.
+ * Arguments, ownership and errors as tg_count_directed_*.
+ */
+#define TG_TETRAD_CLASSES 199
+int64_t tg_dir4_slots(int32_t L);
+int64_t tg_dir4_global_len(int32_t L);
+int tg_count_directed4_per_edge(const tg_graph *g, uint64_t *rows, void *stream);
+int tg_count_directed4_global(const tg_graph *g, uint64_t *out, void *stream);
+
 /* ----------------------------------------------------- no allocation ---- */
 /*
  * The paper has no counterpart to this call; it exists for callers that

@@ -23,7 +23,8 @@ from . import build as _build
 __all__ = [
     "TGError", "Graph", "lib", "tg_build_csr", "tg_free_graph", "tg_graph_info", "tg_edge_list",
     "tg_count_global", "tg_count_global_noalloc", "tg_count_directed_global",
-    "tg_count_directed_per_edge", "tg_dir_slots", "tg_dir_global_len", "TRIAD_NAMES", "tg_count_per_edge", "tg_count_shard", "tg_count_per_edge_sparse", "tg_sparse_ids", "tg_sparse_id", "Batch", "tg_count_batch", "Server", "tg_count_range", "tg_global_finalize",
+    "tg_count_directed_per_edge", "tg_dir_slots", "tg_dir_global_len", "TRIAD_NAMES",
+    "tg_count_directed4_global", "tg_count_directed4_per_edge", "tg_dir4_slots", "tg_dir4_global_len", "tg_count_per_edge", "tg_count_shard", "tg_count_per_edge_sparse", "tg_sparse_ids", "tg_sparse_id", "Batch", "tg_count_batch", "Server", "tg_count_range", "tg_global_finalize",
     "tg_work_model", "tg_slots", "tg_global_len", "tg_config_count", "tg_config_rank",
     "tg_config_unrank", "tg_paper_hash", "tg_slot_config", "tg_strerror", "tg_version",
     "tg_debug_fail_alloc", "tg_set_tune", "tg_get_tune", "tg_autotune", "tg_autotune_reset", "tg_launch_count", "tg_last_timing",
@@ -146,6 +147,10 @@ def lib():
             "tg_dir_global_len": (i64, [i32]),
             "tg_count_directed_global": (ctypes.c_int, [vp, vp, vp]),
             "tg_count_directed_per_edge": (ctypes.c_int, [vp, vp, vp]),
+            "tg_dir4_slots": (i64, [i32]),
+            "tg_dir4_global_len": (i64, [i32]),
+            "tg_count_directed4_global": (ctypes.c_int, [vp, vp, vp]),
+            "tg_count_directed4_per_edge": (ctypes.c_int, [vp, vp, vp]),
             "tg_count_per_edge": (ctypes.c_int, [vp, i32, i32, vp, vp]),
             "tg_count_range": (ctypes.c_int, [vp, i32, i64, i64, vp, vp]),
             "tg_count_shard": (ctypes.c_int, [vp, i32, i32, i32, vp, vp]),
@@ -372,6 +377,33 @@ def tg_count_directed_per_edge(g: Graph, rows=None, stream=None):
         rows = np.zeros((g.M, tg_dir_slots(g.L)), np.uint64)
     _check(lib().tg_count_directed_per_edge(g.handle, _ptr(rows), _stream(stream)),
            "tg_count_directed_per_edge")
+    return rows
+
+
+def tg_dir4_slots(L: int) -> int:
+    return int(lib().tg_dir4_slots(L))
+
+
+def tg_dir4_global_len(L: int) -> int:
+    return int(lib().tg_dir4_global_len(L))
+
+
+def tg_count_directed4_global(g: Graph, out=None, stream=None):
+    """Directed typed 4-node graphlet counts of a graph built with ``directed=True``:
+    199 classes x C(L+3, 4) type multisets."""
+    if out is None:
+        out = np.zeros(tg_dir4_global_len(g.L), np.uint64)
+    _check(lib().tg_count_directed4_global(g.handle, _ptr(out), _stream(stream)),
+           "tg_count_directed4_global")
+    return out
+
+
+def tg_count_directed4_per_edge(g: Graph, rows=None, stream=None):
+    """Per-edge directed typed 4-node rows (M x 199 P)."""
+    if rows is None:
+        rows = np.zeros((g.M, tg_dir4_slots(g.L)), np.uint64)
+    _check(lib().tg_count_directed4_per_edge(g.handle, _ptr(rows), _stream(stream)),
+           "tg_count_directed4_per_edge")
     return rows
 
 
