@@ -553,9 +553,8 @@ __global__ void k_dir4_finalize(const unsigned long long *sums, uint64_t *out, i
 }
 
 // Per-edge rows (rows != nullptr, zeroed here) or undivided global sums (zeroed by the caller).
-int dir4_count(const tg_graph *g, unsigned long long *rows, unsigned long long *sums,
-               const int32_t *d_edges_unused, unsigned *err, cudaStream_t s) {
-    (void)d_edges_unused;
+int dir4_count(const tg_graph *g, unsigned long long *rows, unsigned long long *sums, unsigned *err,
+               cudaStream_t s) {
     const Dir4Table &tt = dir4_table();
     if (!tt.ok) return TG_EINTERNAL;
     const int L = g->L;
@@ -711,7 +710,7 @@ extern "C" int tg_count_directed4_per_edge(const tg_graph *g, uint64_t *rows, vo
         if (!tmp.alloc((size_t)g->M * width, s)) return TG_ENOMEM;
         dst = tmp.p;
     }
-    TG_TRY(dir4_count(g, reinterpret_cast<unsigned long long *>(dst), nullptr, nullptr, err.p, s));
+    TG_TRY(dir4_count(g, reinterpret_cast<unsigned long long *>(dst), nullptr, err.p, s));
     unsigned herr = 0;
     TG_TRY_CUDA(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, s));
     if (!dev_out)
@@ -734,7 +733,7 @@ extern "C" int tg_count_directed4_global(const tg_graph *g, uint64_t *out, void 
     TG_TRY_CUDA(cudaMemsetAsync(sums.p, 0, len * 8, s));
     TG_TRY_CUDA(cudaMemsetAsync(err.p, 0, 4, s));
     TG_TRY_CUDA(cudaMemcpyAsync(ce.p, tt.edges, kDir4Classes * 4, cudaMemcpyHostToDevice, s));
-    TG_TRY(dir4_count(g, nullptr, sums.p, nullptr, err.p, s));
+    TG_TRY(dir4_count(g, nullptr, sums.p, err.p, s));
     const bool dev_out = tg_is_device_ptr(out);
     DevBuf<uint64_t> tmp;
     uint64_t *dst = out;
